@@ -1,0 +1,299 @@
+"""Pins of the CPU FP64 oracle against things other than itself.
+
+The paper prints no worked numeric example, so each oracle function is pinned by
+brute force on tiny inputs, by explicit matrices built from first principles, by closed
+forms and limits stated in Sec. 3, and by finite differences.  Each pin is chosen so that a
+plausible slip (a dropped term, a wrong sign, swapped W/H, a missing renormalisation)
+fails at least one test.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import emfuse_oracle as O
+
+RNG = np.random.default_rng(1234)
+
+
+# ----------------------------------------------------------------------------- helpers
+def neighbours(ny, nx):
+    """4-neighbour edges of an ny x nx pixel grid (each undirected edge once)."""
+    edges = []
+    for y in range(ny):
+        for x in range(nx):
+            if x + 1 < nx:
+                edges.append(((y, x), (y, x + 1)))
+            if y + 1 < ny:
+                edges.append(((y, x), (y + 1, x)))
+    return edges
+
+
+def energy_minimiser(s, o, alpha):
+    """Brute force: the discrete energy of Sec. 3 "Screened-Poisson Blending",
+    E(f) = alpha sum_p (f_p - s_p)^2 + sum_edges ((f_p - f_q) - (o_p - o_q))^2,
+    minimised as a dense linear least-squares problem (no Euler-Lagrange step, no DCT)."""
+    ny, nx = s.shape
+    n = ny * nx
+    idx = lambda y, x: y * nx + x
+    rows, rhs = [], []
+    sa = math.sqrt(alpha)
+    for y in range(ny):
+        for x in range(nx):
+            r = np.zeros(n); r[idx(y, x)] = sa
+            rows.append(r); rhs.append(sa * s[y, x])
+    for (p, q) in neighbours(ny, nx):
+        r = np.zeros(n); r[idx(*p)] = 1.0; r[idx(*q)] = -1.0
+        rows.append(r); rhs.append(o[p] - o[q])
+    f, *_ = np.linalg.lstsq(np.array(rows), np.array(rhs), rcond=None)
+    return f.reshape(ny, nx)
+
+
+def dense_A(ny, nx, alpha):
+    """alpha I + graph Laplacian of the 4-neighbour grid, assembled edge by edge."""
+    n = ny * nx
+    A = alpha * np.eye(n)
+    for (p, q) in neighbours(ny, nx):
+        i, j = p[0] * nx + p[1], q[0] * nx + q[1]
+        A[i, i] += 1; A[j, j] += 1; A[i, j] -= 1; A[j, i] -= 1
+    return A
+
+
+def cosine_matrix(n):
+    """Orthonormal DCT-II matrix from its definition C[k, x] = c_k cos(pi k (x + 1/2) / n)."""
+    C = np.zeros((n, n))
+    for k in range(n):
+        ck = math.sqrt(1.0 / n) if k == 0 else math.sqrt(2.0 / n)
+        for x in range(n):
+            C[k, x] = ck * math.cos(math.pi * k * (x + 0.5) / n)
+    return C
+
+
+# ----------------------------------------------------------------------------- DCT / spectrum
+@pytest.mark.parametrize("n", [1, 2, 5, 8])
+def test_dct_matches_cosine_matrix(n):
+    import scipy.fft as sfft
+    x = RNG.normal(size=n)
+    assert np.allclose(sfft.dct(x, type=2, norm="ortho"), cosine_matrix(n) @ x, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 16])
+def test_neumann_eigenpairs(n):
+    """cos(pi k (x+1/2)/n) is an eigenvector of the 1-D Neumann graph Laplacian."""
+    A = dense_A(1, n, 0.0)
+    lam = O.neumann_eigenvalues(n)
+    C = cosine_matrix(n)
+    for k in range(n):
+        v = C[k]
+        assert np.allclose(A @ v, lam[k] * v, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- Eq. (1)
+@pytest.mark.parametrize("shape", [(8, 8), (7, 5), (5, 7), (1, 9), (1, 1), (2, 3), (6, 1)])
+@pytest.mark.parametrize("alpha", [1e-3, 0.01, 0.1, 2.0])
+def test_solve_equals_energy_minimiser(shape, alpha):
+    s = RNG.uniform(0, 255, size=shape)
+    o = RNG.uniform(0, 255, size=shape)
+    f = O.solve_dct(s, o, alpha)
+    ref = energy_minimiser(s, o, alpha)
+    assert np.max(np.abs(f - ref)) <= 1e-8 * 255 / min(1.0, alpha) * 10
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (7, 5), (1, 6)])
+def test_operator_is_the_dense_euler_lagrange_system(shape):
+    alpha = 0.37
+    u = RNG.normal(size=shape)
+    A = dense_A(*shape, alpha)
+    assert np.allclose(O.apply_A(u, alpha).ravel(), A @ u.ravel(), atol=1e-12)
+    s = RNG.normal(size=shape); o = RNG.normal(size=shape)
+    b = O.screened_rhs(s, o, alpha)
+    assert np.allclose(b.ravel(), alpha * s.ravel() + dense_A(*shape, 0.0) @ o.ravel(), atol=1e-12)
+    x = np.linalg.solve(A, b.ravel()).reshape(shape)
+    assert np.allclose(O.solve_dct(s, o, alpha), x, atol=1e-10)
+
+
+def test_operator_symmetric_positive_definite():
+    ny, nx, alpha = 6, 5, 0.01
+    u = RNG.normal(size=(ny, nx)); v = RNG.normal(size=(ny, nx))
+    assert abs(np.sum(O.apply_A(u, alpha) * v) - np.sum(u * O.apply_A(v, alpha))) < 1e-10
+    ev = np.linalg.eigvalsh(dense_A(ny, nx, alpha))
+    assert ev.min() == pytest.approx(alpha, rel=1e-9)  # the constant mode: A 1 = alpha 1
+
+
+def test_constant_is_fixed_point():
+    c = 93.25
+    s = np.full((9, 11), c); o = np.full((9, 11), c)
+    assert np.allclose(O.solve_dct(s, o, 1e-3), c, atol=1e-10)
+    stack = np.full((5, 6, 7), c)
+    assert np.allclose(O.smooth_stack(stack, 1.0, 3.0), c, atol=1e-12)
+
+
+def test_limits_of_alpha():
+    """Sec. 3: large alpha interpolates I1 (f -> s); small alpha keeps the gradients of I0,
+    with the DC term from s (f -> o - mean(o) + mean(s))."""
+    s = RNG.uniform(0, 255, size=(12, 10)); o = RNG.uniform(0, 255, size=(12, 10))
+    assert np.max(np.abs(O.solve_dct(s, o, 1e12) - s)) < 1e-6
+    f0 = O.solve_dct(s, o, 1e-10)
+    assert np.max(np.abs(f0 - (o - o.mean() + s.mean()))) < 1e-4
+
+
+def test_mean_preserved_from_s():
+    s = RNG.uniform(0, 255, size=(13, 17)); o = RNG.uniform(0, 255, size=(13, 17))
+    for alpha in (1e-3, 0.1, 10.0):
+        assert O.solve_dct(s, o, alpha).mean() == pytest.approx(s.mean(), abs=1e-9)
+
+
+@pytest.mark.parametrize("kl", [(0, 1), (3, 2), (4, 0)])
+def test_single_cosine_mode_gain(kl):
+    """Frequency-space blend (Sec. 3): one mode of s is scaled by alpha/(alpha+lam) and the
+    same mode of o by lam/(alpha+lam), with lam the eigenvalue found by brute force."""
+    ny, nx, alpha = 9, 7, 0.05
+    l, k = kl
+    mode = np.outer(cosine_matrix(ny)[l], cosine_matrix(nx)[k])
+    lam = (mode.ravel() @ (dense_A(ny, nx, 0.0) @ mode.ravel())) / (mode.ravel() @ mode.ravel())
+    f = O.solve_dct(mode, np.zeros_like(mode), alpha)
+    assert np.allclose(f, alpha / (alpha + lam) * mode, atol=1e-12)
+    f = O.solve_dct(np.zeros_like(mode), mode, alpha)
+    assert np.allclose(f, lam / (alpha + lam) * mode, atol=1e-12)
+
+
+def test_linearity():
+    shape = (10, 8); alpha = 0.02
+    s1, s2, o1, o2 = (RNG.normal(size=shape) for _ in range(4))
+    a, b = 0.3, -1.7
+    lhs = O.solve_dct(a * s1 + b * s2, a * o1 + b * o2, alpha)
+    rhs = a * O.solve_dct(s1, o1, alpha) + b * O.solve_dct(s2, o2, alpha)
+    assert np.allclose(lhs, rhs, atol=1e-10)
+
+
+def test_residual_of_exact_solution_is_zero_and_detects_error():
+    s = RNG.uniform(0, 255, size=(32, 24)); o = RNG.uniform(0, 255, size=(32, 24))
+    f = O.solve_dct(s, o, 1e-3)
+    assert O.relative_residual(f, s, o, 1e-3) < 1e-12
+    assert O.relative_residual(f + 1e-3, s, o, 1e-3) > 1e-9
+
+
+def test_alpha_must_be_positive():
+    with pytest.raises(ValueError):
+        O.solve_dct(np.ones((2, 2)), np.ones((2, 2)), 0.0)
+
+
+# ----------------------------------------------------------------------------- smoothing
+def test_truncation_rule():
+    """Sec. 3 "Implementation": weight zero beyond three standard deviations."""
+    assert len(O.gaussian_taps(1.0)) == 7       # |d| <= 3
+    assert len(O.gaussian_taps(3.0)) == 19      # |d| <= 9
+    assert len(O.gaussian_taps(0.5)) == 3       # floor(1.5) = 1
+    w = O.gaussian_taps(3.0)
+    assert w[0] == pytest.approx(math.exp(-4.5))
+    assert len(O.gaussian_taps(0.0)) == 1
+
+
+def brute_force_3d(vol, sxy, sz):
+    """Direct renormalised 3-D sum with the paper's anisotropic Gaussian G (constant
+    prefactor included) over the truncated support |dx|,|dy| <= 3 sxy, |dz| <= 3 sz."""
+    nz, ny, nx = vol.shape
+    Rxy, Rz = int(math.floor(3 * sxy)), int(math.floor(3 * sz))
+    norm = 1.0 / (sxy * sxy * sz * (2 * math.pi) ** 1.5)
+    out = np.zeros_like(vol, dtype=np.float64)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                num = den = 0.0
+                for dz in range(-Rz, Rz + 1):
+                    for dy in range(-Rxy, Rxy + 1):
+                        for dx in range(-Rxy, Rxy + 1):
+                            zz, yy, xx = z + dz, y + dy, x + dx
+                            if 0 <= zz < nz and 0 <= yy < ny and 0 <= xx < nx:
+                                g = norm * math.exp(-(dx * dx + dy * dy) / (2 * sxy * sxy)) \
+                                    * math.exp(-(dz * dz) / (2 * sz * sz))
+                                num += g * vol[zz, yy, xx]; den += g
+                out[z, y, x] = num / den
+    return out
+
+
+@pytest.mark.parametrize("sig", [(1.0, 3.0), (0.7, 1.4), (1.0, 0.0)])
+def test_separable_equals_brute_force_3d(sig):
+    vol = RNG.uniform(0, 255, size=(5, 6, 7))
+    sxy, sz = sig
+    if sz == 0.0:
+        ref = np.stack([brute_force_3d(vol[j:j + 1], sxy, 1e-9)[0] for j in range(vol.shape[0])])
+    else:
+        ref = brute_force_3d(vol, sxy, sz)
+    assert np.allclose(O.smooth_stack(vol, sxy, sz), ref, atol=1e-9)
+
+
+def test_z_ramp_preserved_away_from_ends():
+    nz = 30
+    vol = np.broadcast_to(np.arange(nz, dtype=float)[:, None, None] * 2.5 + 7, (nz, 4, 5)).copy()
+    out = O.smooth_stack(vol, 1.0, 3.0)
+    assert np.allclose(out[9:nz - 9], vol[9:nz - 9], atol=1e-10)
+    # renormalisation at the ends pulls the ramp inwards (not a fixed point there)
+    assert out[0, 0, 0] > vol[0, 0, 0] + 1.0
+
+
+def test_smooth_transpose_dot_product():
+    x = RNG.normal(size=(11, 6, 5)); y = RNG.normal(size=(11, 6, 5))
+    lhs = np.sum(O.smooth_stack(x, 1.0, 2.0) * y)
+    rhs = np.sum(x * O.smooth_transpose(y, 1.0, 2.0))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_dsmooth_dsigma_z_matches_finite_difference():
+    vol = RNG.uniform(0, 255, size=(12, 4, 5))
+    sz, h, R = 2.2, 1e-5, 6
+    fd = (O.smooth_stack(vol, 1.0, sz + h, radius_z=R) - O.smooth_stack(vol, 1.0, sz - h, radius_z=R)) / (2 * h)
+    assert np.allclose(O.dsmooth_dsigma_z(vol, 1.0, sz, radius_z=R), fd, atol=1e-5)
+
+
+# ----------------------------------------------------------------------------- adjoint
+def test_backward_slice_matches_dense_jacobians():
+    ny, nx, alpha = 5, 4, 0.3
+    n = ny * nx
+    s = RNG.uniform(0, 255, size=(ny, nx)); o = RNG.uniform(0, 255, size=(ny, nx))
+    g = RNG.normal(size=(ny, nx))
+    A = dense_A(ny, nx, alpha); Lm = dense_A(ny, nx, 0.0)
+    # f = A^{-1}(alpha s + L o): Jacobians by dense inverse, written out directly
+    Ainv = np.linalg.inv(A)
+    f = (Ainv @ (alpha * s.ravel() + Lm @ o.ravel())).reshape(ny, nx)
+    ds, do, da = O.backward_slice(g, s, o, f, alpha)
+    assert np.allclose(ds.ravel(), (alpha * Ainv).T @ g.ravel(), atol=1e-10)
+    assert np.allclose(do.ravel(), (Ainv @ Lm).T @ g.ravel(), atol=1e-10)
+    # d f / d alpha = A^{-1}(s - f) (differentiate A f = alpha s + L o)
+    assert da == pytest.approx(g.ravel() @ (Ainv @ (s - f).ravel()), rel=1e-10)
+
+
+def test_backward_stack_matches_finite_differences():
+    """Central differences in FP64: in log(alpha) (alpha - h would be singular at small
+    alpha) and in sigma_z with the support radius frozen."""
+    nz, ny, nx = 6, 5, 4
+    I0 = RNG.uniform(0, 255, size=(nz, ny, nx))
+    g = RNG.normal(size=(nz, ny, nx))
+    sxy, sz, alpha, R = 1.0, 1.3, 0.05, 3
+
+    def loss(I, a, s_z):
+        s = O.smooth_stack(I, sxy, s_z, radius_z=R)
+        f = np.stack([O.solve_dct(s[j], I[j], a) for j in range(nz)])
+        return float(np.sum(g * f))
+
+    dI0, dalpha, dsig = O.backward_stack(g, I0, sxy, sz, alpha, radius_z=R)
+    h = 1e-3
+    fd_alpha = (loss(I0, alpha * math.exp(h), sz) - loss(I0, alpha * math.exp(-h), sz)) / (2 * h) / alpha
+    assert dalpha == pytest.approx(fd_alpha, rel=1e-5)
+    fd_sig = (loss(I0, alpha, sz + h) - loss(I0, alpha, sz - h)) / (2 * h)
+    assert dsig == pytest.approx(fd_sig, rel=1e-5)
+    for idx in [(0, 0, 0), (3, 2, 1), (5, 4, 3)]:
+        e = np.zeros_like(I0); e[idx] = 1.0
+        fd = (loss(I0 + h * e, alpha, sz) - loss(I0 - h * e, alpha, sz)) / (2 * h)
+        assert dI0[idx] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_correct_stack_shapes_and_continuity():
+    """End-to-end on a tiny stack with per-slice gain: the corrected stack has smaller
+    inter-slice jumps than the input (the purpose stated in Sec. 1)."""
+    from paper_1506_02079_gb300.synthetic import make_stack
+    I0 = make_stack(12, 32, 32, seed=7).double().numpy()
+    I1, I2 = O.correct_stack(I0, 1.0, 3.0, 1e-3)
+    assert I2.shape == I0.shape
+    jump = lambda v: float(np.mean((v[1:] - v[:-1]) ** 2))
+    assert jump(I2) < 0.5 * jump(I0)
