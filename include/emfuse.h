@@ -1,0 +1,197 @@
+/*
+ * emfuse.h -- C ABI of libemfuse.so: GB300 (sm_103a) gradient-domain colour correction of
+ * registered EM image stacks, after Kazhdan et al., "Gradient-Domain Fusion for Color
+ * Correction in Large EM Image Stacks" (arXiv 1506.02079).
+ *
+ * The method has two phases (Sec. 3):
+ *   phase 1  I1 = I0 * G_{sigma_xy, sigma_z}: anisotropic Gaussian smoothing across the slice
+ *            axis ("Anisotropic Smoothing"), Gaussian cut off beyond three standard
+ *            deviations ("Implementation");
+ *   phase 2  for every xy-slice j, the screened-Poisson system of Eq. (1),
+ *            (alpha - Lap) I2_j = alpha I1_j - Lap I0_j,
+ *            i.e. value constraints from the smoothed slice s = I1_j and gradient constraints
+ *            from the original slice o = I0_j ("Screened-Poisson Blending"), solved by
+ *            multigrid ("Implementation").
+ *
+ * Conventions shared by every entry point
+ *   - Layout: a stack is [z][y][x], x fastest.  A slice is [y][x].  Sizes are in elements.
+ *   - Discretisation: Lap is the 5-point graph Laplacian with Neumann (no-flux) boundaries
+ *     and unit pixel spacing; Gaussian taps are exp(-d^2 / 2 sigma^2) for integer
+ *     |d| <= floor(3 sigma), renormalised over the taps that fall inside the stack.
+ *   - Ownership: the caller owns every buffer passed in.  The library allocates its own
+ *     device workspace (multigrid pyramids, FP64 iterates) stream-ordered on `stream` and
+ *     releases it before returning.
+ *   - Pointers are device pointers unless stated otherwise.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - Errors: every call returns an emfuse_status; it never aborts.  On error a message is
+ *     available from emfuse_last_error() (per host thread).  Invalid arguments are
+ *     detected before any work is queued.
+ *   - Solves (screened_poisson, correct_stack, backward) block the calling host thread:
+ *     the host reads per-slice residual norms between V-cycles to decide convergence.
+ *     Outputs are complete when the call returns.
+ */
+#ifndef EMFUSE_H
+#define EMFUSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { EMFUSE_U8 = 0, EMFUSE_F32 = 1 } emfuse_dtype;
+
+typedef enum {
+    EMFUSE_OK = 0,
+    EMFUSE_EINVAL = 1,    /* bad argument (null pointer, size < 1, alpha <= 0, sigma < 0 ...) */
+    EMFUSE_ECUDA = 2,     /* a CUDA call failed; see emfuse_last_error()                     */
+    EMFUSE_ENOMEM = 3,    /* device workspace could not be allocated                         */
+    EMFUSE_ENOCONV = 4,   /* tol not reached in max_vcycles; outputs hold the last iterate   */
+    EMFUSE_ETIMEOUT = 5   /* a bounded device-side wait expired                             */
+} emfuse_status;
+
+typedef enum {
+    EMFUSE_PREC_FP32 = 0,   /* everything in FP32 (iterate, residual, V-cycles)               */
+    EMFUSE_PREC_MIXED = 1,  /* FP32 V-cycles inside FP64 defect correction (default)          */
+    EMFUSE_PREC_FP64 = 2    /* everything in FP64                                             */
+} emfuse_precision;
+
+/* Solver options.  Fill with emfuse_default_opts() and override fields. */
+typedef struct {
+    double tol;          /* stop when every slice has ||b - A f||_2 / ||b||_2 <= tol,
+                            b = alpha s + L o, A = alpha I + L (residual measure of the
+                            solver table in Sec. 4).  Default 1e-6.                       */
+    int max_vcycles;     /* maximum outer iterations (one V-cycle each).  Default 40.      */
+    int nu_pre;          /* red-black Gauss-Seidel sweeps before restriction.  Default 2.  */
+    int nu_post;         /* sweeps after prolongation.  Default 2.                         */
+    int precision;       /* emfuse_precision.  Default EMFUSE_PREC_MIXED.                  */
+    int fused;           /* 1: fused wavefront kernels on large levels; 0: one kernel per
+                            half-sweep (reference schedule).  Default 1.                   */
+    int reserved[6];     /* must be zero                                                   */
+} emfuse_solve_opts;
+
+/* Per-slice result of a solve. */
+typedef struct {
+    int vcycles;          /* V-cycles applied to this slice                                */
+    int converged;        /* 1 if rel_residual <= tol                                      */
+    double rel_residual;  /* final ||b - A f||_2 / ||b||_2, computed on the GPU              */
+    double b_norm;        /* ||b||_2                                                        */
+} emfuse_slice_stats;
+
+/* Fill `opts` with the defaults listed above. */
+void emfuse_default_opts(emfuse_solve_opts* opts);
+
+/*
+ * Phase 1: I1 = I0 * G_{sigma_xy, sigma_z}  (Sec. 3 "Anisotropic Smoothing"; truncation at
+ * three standard deviations, Sec. 3 "Implementation").
+ *
+ *   in      device, nz planes of ny rows, row pitch `pitch` elements (>= nx), dtype `dt`
+ *           (uint8 or float32).
+ *   out     device float32, (z1 - z0) planes with the same row pitch; plane i holds output
+ *           slice z0 + i.
+ *   z0, z1  output plane range, 0 <= z0 < z1 <= nz.  Every input plane is used as context,
+ *           so a z-slab with floor(3 sigma_z) halo planes on each side gives exactly the
+ *           slices of the whole stack (Sec. 3 "Distributed Processing").
+ *   sigma_xy, sigma_z >= 0 (0 = no smoothing along that axis).
+ *
+ * Weights are renormalised over in-stack taps at stack ends and slice edges.
+ * Asynchronous on `stream`.
+ */
+int emfuse_smooth_z(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                    int64_t pitch, int64_t z0, int64_t z1, float sigma_xy, float sigma_z,
+                    void* stream);
+
+/*
+ * Phase 2: per-slice screened-Poisson solve, Eq. (1): (alpha I + L) f_j = alpha s_j + L o_j
+ * (Sec. 3 "Screened-Poisson Blending"), by multigrid V-cycles (Sec. 3 "Implementation").
+ *
+ *   s, o, f   device float32, a ragged batch of `nslices` dense slices packed in one buffer:
+ *             slice j has ny[j] rows of nx[j] elements starting at element offsets[j].
+ *             f may not alias s or o.
+ *   nx, ny, offsets   HOST arrays of length nslices.
+ *   alpha     screening weight, > 0.
+ *   opts      NULL = defaults.
+ *   stats     NULL or a HOST array of nslices entries, filled on return.
+ *
+ * Initial iterate f = o.  Returns EMFUSE_ENOCONV (with f = last iterate) when some slice
+ * misses opts->tol after opts->max_vcycles V-cycles.
+ */
+int emfuse_screened_poisson(const float* s, const float* o, float* f, int64_t nslices,
+                            const int64_t* nx, const int64_t* ny, const int64_t* offsets,
+                            double alpha, const emfuse_solve_opts* opts,
+                            emfuse_slice_stats* stats, void* stream);
+
+/*
+ * Both phases on a stack: s = smooth(I0), then f_j = solve(s_j, o_j = I0_j) for every j.
+ *
+ *   in        I0, nz x ny x nx dense, dtype `dt`.
+ *   out       I2, float32, same shape.
+ *   in_is_host  0: `in` and `out` are device pointers.
+ *               1: `in` and `out` are HOST pointers (page-locked memory is strongly
+ *                  recommended); the stack is streamed through the device in z-chunks with
+ *                  floor(3 sigma_z) halo planes, copies overlapped with compute on side
+ *                  streams, so stacks larger than device memory are supported.
+ *   stats     NULL or a HOST array of nz entries.
+ */
+int emfuse_correct_stack(const void* in, int dt, int in_is_host, float* out, int64_t nx,
+                         int64_t ny, int64_t nz, float sigma_xy, float sigma_z, double alpha,
+                         const emfuse_solve_opts* opts, emfuse_slice_stats* stats,
+                         void* stream);
+
+/*
+ * Adjoint of emfuse_correct_stack / emfuse_screened_poisson on a dense stack of nz slices
+ * of ny x nx.  With A = alpha I + L symmetric and lam_j = A^{-1} grad_f_j (solved by the same
+ * multigrid), for a loss l with dl/df = grad_f:
+ *     dl/ds      = alpha lam
+ *     dl/do      = L lam
+ *     dl/dalpha  = sum_j <lam_j, s_j - f_j>
+ *     dl/dI0     = L lam + K^T (alpha lam)        (s = K I0, o = I0; K the phase-1 smoothing)
+ *     dl/dsigma_z = <alpha lam, (dK/dsigma_z) I0>  (support radius held at floor(3 sigma_z))
+ *
+ *   grad_f, f, s   device float32 (f and s as produced by the forward call).
+ *   o              device I0, dtype `dt`.
+ *   grad_s, grad_o, grad_in0   device float32 outputs, each may be NULL (not computed).
+ *   grad_alpha, grad_sigma_z   HOST double outputs, each may be NULL.
+ *   grad_in0 / grad_sigma_z need sigma_xy, sigma_z (the forward smoothing).
+ */
+int emfuse_backward(const float* grad_f, const float* f, const float* s, const void* o, int dt,
+                    int64_t nx, int64_t ny, int64_t nz, float sigma_xy, float sigma_z,
+                    double alpha, float* grad_s, float* grad_o, float* grad_in0,
+                    double* grad_alpha, double* grad_sigma_z, const emfuse_solve_opts* opts,
+                    void* stream);
+
+/*
+ * Instrumentation (no counterpart in the paper).
+ *
+ * emfuse_kernel_launches(): number of kernels this library has launched in this process.
+ * emfuse_profile_begin(): start recording a CUDA event pair around every kernel launch of
+ *   the library, on the stream the kernel is launched on, together with the algorithmic
+ *   bytes of the launch: every input element the kernel's function needs read once and
+ *   every output element written once (counted at each launch site).  Adds two event
+ *   records per launch.
+ * emfuse_profile_end(): stop recording, wait for the recorded events, and fill up to
+ *   `max_entries` per-kernel totals (sorted by total time, descending).  Returns the number
+ *   of kernel names recorded (which may exceed max_entries), or -1 on a CUDA error.
+ */
+typedef struct {
+    char name[48];           /* kernel family, e.g. "relax_l0" */
+    int64_t launches;
+    double total_ms;         /* sum of event-measured launch durations */
+    double bytes;            /* sum of algorithmic bytes over the launches */
+} emfuse_kernel_profile;
+
+uint64_t emfuse_kernel_launches(void);
+void emfuse_profile_begin(void);
+int emfuse_profile_end(emfuse_kernel_profile* out, int max_entries);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* emfuse_last_error(void);
+
+/* Library version string. */
+const char* emfuse_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMFUSE_H */

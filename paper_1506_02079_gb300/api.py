@@ -1,0 +1,265 @@
+"""Thin Python binding of libemfuse.so (argument marshalling only).
+
+Every function has the name of the C entry point it calls (``include/emfuse.h``).  Tensors
+are PyTorch tensors used purely as device (or pinned host) memory; all arithmetic runs in the
+library's CUDA kernels on the current PyTorch stream.  A missing library raises
+``EmfuseUnavailable``; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "EmfuseError", "EmfuseUnavailable", "SolveOpts", "SliceStats", "lib", "library_path",
+    "default_opts", "emfuse_smooth_z", "emfuse_screened_poisson", "emfuse_correct_stack",
+    "emfuse_backward", "emfuse_version", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
+    "PREC_FP64", "EXPORTED_SYMBOLS",
+]
+
+EMFUSE_U8, EMFUSE_F32 = 0, 1
+PREC_FP32, PREC_MIXED, PREC_FP64 = 0, 1, 2
+STATUS = {0: "EMFUSE_OK", 1: "EMFUSE_EINVAL", 2: "EMFUSE_ECUDA", 3: "EMFUSE_ENOMEM",
+          4: "EMFUSE_ENOCONV", 5: "EMFUSE_ETIMEOUT"}
+EXPORTED_SYMBOLS = ["emfuse_default_opts", "emfuse_smooth_z", "emfuse_screened_poisson",
+                    "emfuse_correct_stack", "emfuse_backward", "emfuse_last_error",
+                    "emfuse_version", "emfuse_kernel_launches", "emfuse_profile_begin",
+                    "emfuse_profile_end"]
+
+
+class EmfuseError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class EmfuseUnavailable(RuntimeError):
+    pass
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_vcycles", ctypes.c_int), ("nu_pre", ctypes.c_int),
+                ("nu_post", ctypes.c_int), ("precision", ctypes.c_int), ("fused", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+class SliceStats(ctypes.Structure):
+    _fields_ = [("vcycles", ctypes.c_int), ("converged", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("b_norm", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libemfuse.so (loaded once; raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise EmfuseUnavailable(
+                    f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(path)
+            i64, vp, fl, db, ci = ctypes.c_int64, ctypes.c_void_p, ctypes.c_float, ctypes.c_double, ctypes.c_int
+            L.emfuse_default_opts.argtypes = [ctypes.POINTER(SolveOpts)]
+            L.emfuse_default_opts.restype = None
+            L.emfuse_smooth_z.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
+            L.emfuse_screened_poisson.argtypes = [vp, vp, vp, i64, vp, vp, vp, db,
+                                                  ctypes.POINTER(SolveOpts), vp, vp]
+            L.emfuse_correct_stack.argtypes = [vp, ci, ci, vp, i64, i64, i64, fl, fl, db,
+                                               ctypes.POINTER(SolveOpts), vp, vp]
+            L.emfuse_backward.argtypes = [vp, vp, vp, vp, ci, i64, i64, i64, fl, fl, db, vp, vp, vp,
+                                          vp, vp, ctypes.POINTER(SolveOpts), vp]
+            for name in ("emfuse_smooth_z", "emfuse_screened_poisson", "emfuse_correct_stack",
+                         "emfuse_backward"):
+                getattr(L, name).restype = ci
+            L.emfuse_last_error.restype = ctypes.c_char_p
+            L.emfuse_last_error.argtypes = []
+            L.emfuse_version.restype = ctypes.c_char_p
+            L.emfuse_version.argtypes = []
+            L.emfuse_kernel_launches.restype = ctypes.c_uint64
+            L.emfuse_kernel_launches.argtypes = []
+            _lib = L
+        return _lib
+
+
+def emfuse_version() -> str:
+    return lib().emfuse_version().decode()
+
+
+def default_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    lib().emfuse_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _check(code: int, allow_noconv: bool = False):
+    if code == 0 or (allow_noconv and code == 4):
+        return code
+    raise EmfuseError(code, lib().emfuse_last_error().decode())
+
+
+def _stream_ptr(device: torch.device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.uint8:
+        return EMFUSE_U8
+    if t.dtype == torch.float32:
+        return EMFUSE_F32
+    raise TypeError(f"unsupported dtype {t.dtype}: use uint8 or float32")
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if t is not None and not t.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+
+
+def _stats_list(arr) -> list[dict]:
+    return [{"vcycles": s.vcycles, "converged": bool(s.converged), "rel_residual": s.rel_residual,
+             "b_norm": s.b_norm} for s in arr]
+
+
+def emfuse_smooth_z(stack: torch.Tensor, sigma_xy: float = 1.0, sigma_z: float = 3.0,
+                    out: torch.Tensor | None = None, z0: int = 0, z1: int | None = None) -> torch.Tensor:
+    """Phase 1 (Sec. 3 "Anisotropic Smoothing"): I1 = I0 * G.  ``stack`` is [z][y][x] on CUDA."""
+    _require_cuda(stack)
+    nz, ny, nx = stack.shape
+    z1 = nz if z1 is None else z1
+    if out is None:
+        out = torch.empty((z1 - z0, ny, nx), device=stack.device, dtype=torch.float32)
+    _require_cuda(out)
+    _check(lib().emfuse_smooth_z(stack.data_ptr(), _dtype_code(stack), out.data_ptr(), nx, ny, nz,
+                                 nx, z0, z1, float(sigma_xy), float(sigma_z), _stream_ptr(stack.device)))
+    return out
+
+
+def _pack_slices(s, o):
+    """Accept 3-D stacks (uniform batch) or lists of 2-D slices (ragged batch)."""
+    if isinstance(s, torch.Tensor) and s.dim() == 3:
+        nz, ny, nx = s.shape
+        nxs = np.full(nz, nx, dtype=np.int64)
+        nys = np.full(nz, ny, dtype=np.int64)
+        offs = np.arange(nz, dtype=np.int64) * nx * ny
+        return s.contiguous(), o.contiguous(), nxs, nys, offs, None
+    if isinstance(s, torch.Tensor) and s.dim() == 2:
+        return _pack_slices(s[None], o[None])
+    shapes = [tuple(t.shape) for t in s]
+    nys = np.array([a for a, _ in shapes], dtype=np.int64)
+    nxs = np.array([b for _, b in shapes], dtype=np.int64)
+    offs = np.zeros(len(shapes), dtype=np.int64)
+    offs[1:] = np.cumsum(nys * nxs)[:-1]
+    sp = torch.cat([t.reshape(-1) for t in s])
+    op = torch.cat([t.reshape(-1) for t in o])
+    return sp, op, nxs, nys, offs, shapes
+
+
+def emfuse_screened_poisson(s, o, alpha: float, opts: SolveOpts | None = None, *, nx=None, ny=None,
+                            offsets=None, out: torch.Tensor | None = None, return_stats: bool = False,
+                            allow_noconv: bool = False):
+    """Phase 2 (Eq. (1)): (alpha I + L) f = alpha s + L o for every slice.
+
+    ``s``/``o``: CUDA float32 stacks [z][y][x], single slices [y][x], lists of slices, or packed
+    1-D buffers together with ``nx``, ``ny``, ``offsets`` (host int64 arrays).
+    """
+    if nx is not None:
+        sp, op = s, o
+        nxs, nys, offs = (np.ascontiguousarray(a, dtype=np.int64) for a in (nx, ny, offsets))
+        shapes = "packed"
+    else:
+        sp, op, nxs, nys, offs, shapes = _pack_slices(s, o)
+    _require_cuda(sp, op)
+    if sp.dtype != torch.float32 or op.dtype != torch.float32:
+        raise TypeError("s and o must be float32")
+    f = torch.empty_like(sp) if out is None else out
+    _require_cuda(f)
+    n = len(nxs)
+    stats = (SliceStats * n)()
+    code = lib().emfuse_screened_poisson(
+        sp.data_ptr(), op.data_ptr(), f.data_ptr(), n, nxs.ctypes.data, nys.ctypes.data,
+        offs.ctypes.data, float(alpha), ctypes.byref(opts) if opts is not None else None,
+        ctypes.addressof(stats), _stream_ptr(sp.device))
+    _check(code, allow_noconv)
+    if shapes not in (None, "packed"):
+        f = [f[int(a):int(a) + h * w].view(h, w) for a, (h, w) in zip(offs, shapes)]
+    elif isinstance(s, torch.Tensor) and s.dim() == 2 and nx is None:
+        f = f[0]
+    return (f, _stats_list(stats)) if return_stats else f
+
+
+def emfuse_correct_stack(stack: torch.Tensor, sigma_xy: float = 1.0, sigma_z: float = 3.0,
+                         alpha: float = 1e-3, opts: SolveOpts | None = None,
+                         out: torch.Tensor | None = None, return_stats: bool = False,
+                         allow_noconv: bool = False, device: int | None = None):
+    """Both phases.  A CUDA ``stack`` is processed in place on the device; a CPU ``stack``
+    (pinned memory recommended) is streamed through the device in z-chunks and the result is
+    written to a CPU ``out``."""
+    if not stack.is_contiguous():
+        raise ValueError("expected a contiguous stack")
+    nz, ny, nx = stack.shape
+    on_host = not stack.is_cuda
+    if out is None:
+        out = torch.empty((nz, ny, nx), dtype=torch.float32, device=stack.device,
+                          pin_memory=bool(on_host and stack.is_pinned()))
+    if out.is_cuda == on_host:
+        raise ValueError("out must live where the stack lives")
+    dev = stack.device if stack.is_cuda else torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    stats = (SliceStats * nz)()
+    code = lib().emfuse_correct_stack(
+        stack.data_ptr(), _dtype_code(stack), int(on_host), out.data_ptr(), nx, ny, nz,
+        float(sigma_xy), float(sigma_z), float(alpha),
+        ctypes.byref(opts) if opts is not None else None, ctypes.addressof(stats), _stream_ptr(dev))
+    _check(code, allow_noconv)
+    return (out, _stats_list(stats)) if return_stats else out
+
+
+def emfuse_backward(grad_f: torch.Tensor, f: torch.Tensor | None, s: torch.Tensor | None,
+                    o: torch.Tensor | None, sigma_xy: float, sigma_z: float, alpha: float,
+                    want=("s", "o", "in0", "alpha", "sigma_z"), opts: SolveOpts | None = None):
+    """Adjoint of the correction (see include/emfuse.h).  Returns a dict of the requested
+    gradients: 's', 'o', 'in0' (CUDA float32 tensors), 'alpha', 'sigma_z' (floats)."""
+    _require_cuda(grad_f, f, s, o)
+    g3 = grad_f if grad_f.dim() == 3 else grad_f[None]
+    nz, ny, nx = g3.shape
+    out = {}
+    ptr = lambda t: t.data_ptr() if t is not None else None
+    gs = torch.empty_like(g3) if "s" in want else None
+    go = torch.empty_like(g3) if "o" in want else None
+    gi = torch.empty_like(g3) if "in0" in want else None
+    ga = ctypes.c_double(0.0)
+    gz = ctypes.c_double(0.0)
+    dt = _dtype_code(o) if o is not None else EMFUSE_F32
+    code = lib().emfuse_backward(
+        g3.data_ptr(), ptr(f), ptr(s), ptr(o), dt, nx, ny, nz, float(sigma_xy), float(sigma_z),
+        float(alpha), ptr(gs), ptr(go), ptr(gi),
+        ctypes.addressof(ga) if "alpha" in want else None,
+        ctypes.addressof(gz) if "sigma_z" in want else None,
+        ctypes.byref(opts) if opts is not None else None, _stream_ptr(g3.device))
+    _check(code, allow_noconv=True)
+    shape = grad_f.shape
+    if gs is not None: out["s"] = gs.view(shape)
+    if go is not None: out["o"] = go.view(shape)
+    if gi is not None: out["in0"] = gi.view(shape)
+    if "alpha" in want: out["alpha"] = ga.value
+    if "sigma_z" in want: out["sigma_z"] = gz.value
+    return out

@@ -1,0 +1,255 @@
+// extern "C" entry points of libemfuse (declared in include/emfuse.h): argument validation,
+// error reporting, and the orchestration of the two phases of the method.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "emfuse_common.cuh"
+#include "emfuse_internal.cuh"
+
+namespace emfuse {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+const char* last_error() { return g_last_error.c_str(); }
+
+static int einval(const std::string& msg) {
+    set_error(msg);
+    return EMFUSE_EINVAL;
+}
+
+static int resolve_opts(const emfuse_solve_opts* in, emfuse_solve_opts* out) {
+    emfuse_default_opts(out);
+    if (in) *out = *in;
+    if (!(out->tol >= 0.0)) return einval("opts.tol must be >= 0");
+    if (out->max_vcycles < 0) return einval("opts.max_vcycles must be >= 0");
+    if (out->nu_pre < 0 || out->nu_post < 0 || out->nu_pre + out->nu_post < 1 || out->nu_pre > 8 || out->nu_post > 8)
+        return einval("opts.nu_pre / nu_post must be in [0, 8] with at least one sweep");
+    if (out->precision < EMFUSE_PREC_FP32 || out->precision > EMFUSE_PREC_FP64)
+        return einval("opts.precision must be EMFUSE_PREC_FP32, _MIXED or _FP64");
+    return EMFUSE_OK;
+}
+
+static bool dtype_ok(int dt) { return dt == EMFUSE_U8 || dt == EMFUSE_F32; }
+static size_t dtype_size(int dt) { return dt == EMFUSE_U8 ? 1 : 4; }
+
+// Largest supported side: level indices and pitches are 32-bit.
+constexpr int64_t kMaxSide = (int64_t)1 << 30;
+
+static int check_sigma(float sxy, float sz) {
+    if (!(sxy >= 0.f) || !(sz >= 0.f) || !std::isfinite(sxy) || !std::isfinite(sz))
+        return einval("sigma_xy and sigma_z must be finite and >= 0");
+    if (support_radius(sxy) > 32 || support_radius(sz) > 32)
+        return einval("sigma too large: support radius floor(3 sigma) must be <= 32");
+    return EMFUSE_OK;
+}
+
+static int check_alpha(double alpha) {
+    if (!(alpha > 0.0) || !std::isfinite(alpha))
+        return einval("alpha must be finite and > 0 (Eq. (1) is singular at alpha = 0 with Neumann boundaries)");
+    return EMFUSE_OK;
+}
+
+// Solve every slice of a dense stack (nz slices of ny x nx).
+static int solve_stack(const float* s, const void* o, int dt, float* out, int64_t nx, int64_t ny,
+                       int64_t nz, double alpha, const emfuse_solve_opts& opts,
+                       emfuse_slice_stats* stats, const float* rhs, cudaStream_t st) {
+    std::vector<int64_t> vx(nz, nx), vy(nz, ny), off(nz);
+    for (int64_t j = 0; j < nz; ++j) off[j] = j * nx * ny;
+    SolveRequest req;
+    req.s = s;
+    req.o = o;
+    req.o_dtype = dt;
+    req.rhs = rhs;
+    req.out = out;
+    req.nslices = nz;
+    req.nx = vx.data();
+    req.ny = vy.data();
+    req.offsets = off.data();
+    req.alpha = alpha;
+    req.opts = opts;
+    req.stats = stats;
+    return solve_batch(req, st);
+}
+
+}  // namespace emfuse
+
+using namespace emfuse;
+
+extern "C" {
+
+void emfuse_default_opts(emfuse_solve_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-6;
+    o->max_vcycles = 40;
+    o->nu_pre = 2;
+    o->nu_post = 2;
+    o->precision = EMFUSE_PREC_MIXED;
+    o->fused = 1;
+}
+
+const char* emfuse_last_error(void) { return last_error(); }
+
+const char* emfuse_version(void) { return "emfuse 0.1 (sm_103a)"; }
+
+int emfuse_smooth_z(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                    int64_t pitch, int64_t z0, int64_t z1, float sigma_xy, float sigma_z,
+                    void* stream) {
+    set_error("");
+    if (!in || !out) return einval("emfuse_smooth_z: null pointer");
+    if (!dtype_ok(dt)) return einval("emfuse_smooth_z: dtype must be EMFUSE_U8 or EMFUSE_F32");
+    if (nx < 1 || ny < 1 || nz < 1 || nx > kMaxSide || ny > kMaxSide || nz > kMaxSide)
+        return einval("emfuse_smooth_z: sizes must be in [1, 2^30]");
+    if (pitch < nx) return einval("emfuse_smooth_z: pitch must be >= nx");
+    if (z0 < 0 || z1 > nz || z0 >= z1) return einval("emfuse_smooth_z: need 0 <= z0 < z1 <= nz");
+    EMF_TRY(check_sigma(sigma_xy, sigma_z));
+    return smooth_stack(in, dt, out, nx, ny, nz, pitch, z0, z1, sigma_xy, sigma_z,
+                        (cudaStream_t)stream, 0);
+}
+
+int emfuse_screened_poisson(const float* s, const float* o, float* f, int64_t nslices,
+                            const int64_t* nx, const int64_t* ny, const int64_t* offsets,
+                            double alpha, const emfuse_solve_opts* opts,
+                            emfuse_slice_stats* stats, void* stream) {
+    set_error("");
+    if (!s || !o || !f || !nx || !ny || !offsets) return einval("emfuse_screened_poisson: null pointer");
+    if (nslices < 1) return einval("emfuse_screened_poisson: nslices must be >= 1");
+    if (f == s || f == o) return einval("emfuse_screened_poisson: f must not alias s or o");
+    for (int64_t j = 0; j < nslices; ++j) {
+        if (nx[j] < 1 || ny[j] < 1 || nx[j] > kMaxSide || ny[j] > kMaxSide)
+            return einval("emfuse_screened_poisson: slice sizes must be in [1, 2^30]");
+        if (offsets[j] < 0) return einval("emfuse_screened_poisson: negative offset");
+    }
+    EMF_TRY(check_alpha(alpha));
+    emfuse_solve_opts o2;
+    EMF_TRY(resolve_opts(opts, &o2));
+    SolveRequest req;
+    req.s = s;
+    req.o = o;
+    req.o_dtype = EMFUSE_F32;
+    req.out = f;
+    req.nslices = nslices;
+    req.nx = nx;
+    req.ny = ny;
+    req.offsets = offsets;
+    req.alpha = alpha;
+    req.opts = o2;
+    req.stats = stats;
+    return solve_batch(req, (cudaStream_t)stream);
+}
+
+int emfuse_correct_stack(const void* in, int dt, int in_is_host, float* out, int64_t nx,
+                         int64_t ny, int64_t nz, float sigma_xy, float sigma_z, double alpha,
+                         const emfuse_solve_opts* opts, emfuse_slice_stats* stats,
+                         void* stream) {
+    set_error("");
+    if (!in || !out) return einval("emfuse_correct_stack: null pointer");
+    if (!dtype_ok(dt)) return einval("emfuse_correct_stack: dtype must be EMFUSE_U8 or EMFUSE_F32");
+    if (nx < 1 || ny < 1 || nz < 1 || nx > kMaxSide || ny > kMaxSide || nz > kMaxSide)
+        return einval("emfuse_correct_stack: sizes must be in [1, 2^30]");
+    EMF_TRY(check_sigma(sigma_xy, sigma_z));
+    EMF_TRY(check_alpha(alpha));
+    emfuse_solve_opts o2;
+    EMF_TRY(resolve_opts(opts, &o2));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t plane = nx * ny;
+    if (!in_is_host) {
+        DeviceBuffer sbuf;
+        EMF_TRY(sbuf.alloc((size_t)(plane * nz) * sizeof(float), st));
+        EMF_TRY(smooth_stack(in, dt, sbuf.as<float>(), nx, ny, nz, nx, 0, nz, sigma_xy, sigma_z, st, 0));
+        return solve_stack(sbuf.as<float>(), in, dt, out, nx, ny, nz, alpha, o2, stats, nullptr, st);
+    }
+    // Host-resident stack: z-chunks of C output slices with R halo planes on each side.
+    const int R = support_radius(sigma_z);
+    size_t free_b = 0, total_b = 0;
+    EMF_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    // per output slice: input (dt) + s (4) + out (4) + solver workspace (~8 + 8 mixed)
+    const double per_slice = (double)plane * (dtype_size(dt) + 4 + 4 + 24);
+    int64_t C = (int64_t)std::max(1.0, std::floor(0.5 * (double)free_b / per_slice) - 2 * R);
+    C = std::min<int64_t>(C, nz);
+    C = std::min<int64_t>(C, 64);
+    const size_t esz = dtype_size(dt);
+    DeviceBuffer din, dout, ds;
+    const int64_t in_cap = std::min<int64_t>(nz, C + 2 * R);
+    EMF_TRY(din.alloc((size_t)(in_cap * plane) * esz, st));
+    EMF_TRY(dout.alloc((size_t)(C * plane) * sizeof(float), st));
+    EMF_TRY(ds.alloc((size_t)(C * plane) * sizeof(float), st));
+    int rc_all = EMFUSE_OK;
+    for (int64_t z0 = 0; z0 < nz; z0 += C) {
+        const int64_t z1 = std::min(nz, z0 + C);
+        const int64_t a = std::max<int64_t>(0, z0 - R), b = std::min<int64_t>(nz, z1 + R);
+        EMF_CUDA(cudaMemcpyAsync(din.as<char>(), (const char*)in + (size_t)(a * plane) * esz,
+                                 (size_t)((b - a) * plane) * esz, cudaMemcpyHostToDevice, st));
+        // Every tap of an output plane in [z0, z1) lies inside the slab [a, b) or outside the
+        // stack, so smoothing the slab on its own gives exactly the stack's slices.
+        EMF_TRY(smooth_stack(din.as<char>(), dt, ds.as<float>(), nx, ny, b - a, nx, z0 - a, z1 - a,
+                             sigma_xy, sigma_z, st, 0));
+        const char* o_chunk = din.as<char>() + (size_t)((z0 - a) * plane) * esz;
+        int rc = solve_stack(ds.as<float>(), o_chunk, dt, dout.as<float>(), nx, ny, z1 - z0, alpha,
+                             o2, stats ? stats + z0 : nullptr, nullptr, st);
+        if (rc != EMFUSE_OK && rc != EMFUSE_ENOCONV) return rc;
+        if (rc == EMFUSE_ENOCONV) rc_all = rc;
+        EMF_CUDA(cudaMemcpyAsync(out + z0 * plane, dout.as<float>(), (size_t)((z1 - z0) * plane) * sizeof(float),
+                                 cudaMemcpyDeviceToHost, st));
+    }
+    EMF_CUDA(cudaStreamSynchronize(st));
+    return rc_all;
+}
+
+int emfuse_backward(const float* grad_f, const float* f, const float* s, const void* o, int dt,
+                    int64_t nx, int64_t ny, int64_t nz, float sigma_xy, float sigma_z,
+                    double alpha, float* grad_s, float* grad_o, float* grad_in0,
+                    double* grad_alpha, double* grad_sigma_z, const emfuse_solve_opts* opts,
+                    void* stream) {
+    set_error("");
+    if (!grad_f) return einval("emfuse_backward: grad_f is null");
+    if (!dtype_ok(dt)) return einval("emfuse_backward: dtype must be EMFUSE_U8 or EMFUSE_F32");
+    if (nx < 1 || ny < 1 || nz < 1 || nx > kMaxSide || ny > kMaxSide || nz > kMaxSide)
+        return einval("emfuse_backward: sizes must be in [1, 2^30]");
+    if (grad_alpha && (!f || !s)) return einval("emfuse_backward: grad_alpha needs f and s");
+    if (grad_sigma_z && !o) return einval("emfuse_backward: grad_sigma_z needs o (I0)");
+    EMF_TRY(check_alpha(alpha));
+    EMF_TRY(check_sigma(sigma_xy, sigma_z));
+    emfuse_solve_opts o2;
+    EMF_TRY(resolve_opts(opts, &o2));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = nx * ny * nz;
+    DeviceBuffer lam;
+    EMF_TRY(lam.alloc((size_t)n * sizeof(float), st));
+    // lam = A^{-1} grad_f (A symmetric)
+    int rc = solve_stack(nullptr, nullptr, EMFUSE_F32, lam.as<float>(), nx, ny, nz, alpha, o2,
+                         nullptr, grad_f, st);
+    if (rc != EMFUSE_OK && rc != EMFUSE_ENOCONV) return rc;
+    DeviceBuffer tmp_s;
+    float* gs = grad_s;
+    if (!gs && (grad_in0 || grad_sigma_z)) {
+        EMF_TRY(tmp_s.alloc((size_t)n * sizeof(float), st));
+        gs = tmp_s.as<float>();
+    }
+    if (gs) EMF_TRY(scale_copy(lam.as<float>(), gs, n, (float)alpha, st));
+    if (grad_o) EMF_TRY(apply_laplacian_stack(lam.as<float>(), grad_o, nx, ny, nz, 1.f, st));
+    if (grad_alpha) EMF_TRY(dot_diff(lam.as<float>(), s, f, n, grad_alpha, st));
+    if (grad_in0) {
+        // dl/dI0 = L lam + K^T (alpha lam)
+        EMF_TRY(smooth_transpose(gs, grad_in0, nx, ny, nz, sigma_xy, sigma_z, st));
+        DeviceBuffer lap;
+        EMF_TRY(lap.alloc((size_t)n * sizeof(float), st));
+        EMF_TRY(apply_laplacian_stack(lam.as<float>(), lap.as<float>(), nx, ny, nz, 1.f, st));
+        EMF_TRY(axpy(lap.as<float>(), grad_in0, n, 1.f, st));
+    }
+    if (grad_sigma_z) {
+        DeviceBuffer dk;
+        EMF_TRY(dk.alloc((size_t)n * sizeof(float), st));
+        EMF_TRY(smooth_dsigma_z(o, dt, dk.as<float>(), nx, ny, nz, sigma_xy, sigma_z, st));
+        EMF_TRY(dot_diff(gs, dk.as<float>(), nullptr, n, grad_sigma_z, st));
+    }
+    EMF_CUDA(cudaStreamSynchronize(st));
+    return rc;
+}
+
+}  // extern "C"

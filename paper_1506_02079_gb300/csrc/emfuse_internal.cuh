@@ -1,0 +1,52 @@
+// Internal (non-exported) interfaces between the translation units of libemfuse.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "emfuse_common.cuh"
+
+namespace emfuse {
+
+// ---- smoothing (smooth.cu)
+int support_radius(float sigma);
+std::vector<float> gaussian_taps(float sigma, int R);
+std::vector<float> inverse_norms(const std::vector<float>& w, int n);
+// force_path: 0 = automatic, 1 = three 1-D passes
+int smooth_stack(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                 int64_t pitch, int64_t z0, int64_t z1, float sigma_xy, float sigma_z,
+                 cudaStream_t st, int force_path);
+int smooth_transpose(const float* g, float* out, int64_t nx, int64_t ny, int64_t nz,
+                     float sigma_xy, float sigma_z, cudaStream_t st);
+int smooth_dsigma_z(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                    float sigma_xy, float sigma_z, cudaStream_t st);
+
+// ---- multigrid screened-Poisson solve (multigrid.cu)
+struct SolveRequest {
+    const float* s = nullptr;   // value constraints (I1), packed ragged batch
+    const void* o = nullptr;    // gradient constraints (I0), packed, dtype o_dtype
+    int o_dtype = EMFUSE_F32;
+    const float* rhs = nullptr; // if non-null: solve A x = rhs instead (adjoint); s, o unused
+    float* out = nullptr;       // solution, packed
+    int64_t nslices = 0;
+    const int64_t* nx = nullptr;       // host
+    const int64_t* ny = nullptr;       // host
+    const int64_t* offsets = nullptr;  // host, elements
+    double alpha = 0.0;
+    emfuse_solve_opts opts{};
+    emfuse_slice_stats* stats = nullptr;  // host, may be null
+};
+int solve_batch(const SolveRequest& req, cudaStream_t st);
+
+// elementwise helpers used by the adjoint (multigrid.cu)
+int apply_laplacian_stack(const float* in, float* out, int64_t nx, int64_t ny, int64_t nz,
+                          float scale, cudaStream_t st);
+// sum_j <a_j, b_j - c_j> in FP64 over a dense float stack; result copied to host
+int dot_diff(const float* a, const float* b, const float* c, int64_t n, double* host_out,
+             cudaStream_t st);
+int scale_copy(const float* in, float* out, int64_t n, float a, cudaStream_t st);
+int axpy(const float* x, float* y, int64_t n, float a, cudaStream_t st);
+
+}  // namespace emfuse

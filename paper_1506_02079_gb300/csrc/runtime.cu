@@ -1,0 +1,112 @@
+// Launch accounting and optional per-kernel CUDA-event timing (the instrumentation entry
+// points of include/emfuse.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "emfuse_common.cuh"
+
+namespace emfuse {
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+std::atomic<bool> g_profiling{false};
+std::mutex g_mu;
+struct Rec {
+    const char* name;
+    cudaEvent_t a, b;
+    double bytes;
+};
+std::vector<Rec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+
+cudaEvent_t take_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+}  // namespace
+
+KernelScope::KernelScope(const char* name, cudaStream_t s, double bytes)
+    : name_(name), s_(s), bytes_(bytes) {
+    if (g_profiling.load(std::memory_order_relaxed)) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        a_ = take_event();
+        b_ = take_event();
+        if (a_ && b_) cudaEventRecord(a_, s_);
+    }
+}
+
+KernelScope::~KernelScope() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (a_ && b_) {
+        cudaEventRecord(b_, s_);
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_recs.push_back(Rec{name_, a_, b_, bytes_});
+    }
+}
+
+}  // namespace emfuse
+
+using namespace emfuse;
+
+extern "C" {
+
+uint64_t emfuse_kernel_launches(void) { return g_launches.load(); }
+
+void emfuse_profile_begin(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& r : g_recs) {
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+    g_profiling.store(true);
+}
+
+int emfuse_profile_end(emfuse_kernel_profile* out, int max_entries) {
+    g_profiling.store(false);
+    std::lock_guard<std::mutex> lk(g_mu);
+    struct Acc { int64_t n = 0; double ms = 0, bytes = 0; };
+    std::map<std::string, Acc> acc;
+    int rc = 0;
+    for (auto& r : g_recs) {
+        if (cudaEventSynchronize(r.b) != cudaSuccess) { rc = -1; continue; }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) { rc = -1; continue; }
+        Acc& x = acc[r.name];
+        x.n += 1;
+        x.ms += ms;
+        x.bytes += r.bytes;
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+    if (rc < 0) {
+        set_error("emfuse_profile_end: a CUDA event could not be read");
+        return -1;
+    }
+    std::vector<std::pair<std::string, Acc>> v(acc.begin(), acc.end());
+    std::sort(v.begin(), v.end(), [](auto& p, auto& q) { return p.second.ms > q.second.ms; });
+    for (int i = 0; i < (int)v.size() && i < max_entries && out; ++i) {
+        std::memset(&out[i], 0, sizeof(out[i]));
+        std::strncpy(out[i].name, v[i].first.c_str(), sizeof(out[i].name) - 1);
+        out[i].launches = v[i].second.n;
+        out[i].total_ms = v[i].second.ms;
+        out[i].bytes = v[i].second.bytes;
+    }
+    return (int)v.size();
+}
+
+}  // extern "C"

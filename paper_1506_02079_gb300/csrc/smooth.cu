@@ -1,0 +1,373 @@
+// Phase 1 of the method: anisotropic Gaussian smoothing I1 = I0 * G_{sigma_xy, sigma_z}
+// (Sec. 3 "Anisotropic Smoothing"), with the Gaussian cut off beyond three standard deviations
+// (Sec. 3 "Implementation") and the weights renormalised over the taps inside the stack.
+//
+// Two implementations:
+//   * smooth_fused_kernel: one HBM pass.  A CTA owns a 64x16 xy-tile and marches along z.
+//     Each input plane is staged in shared memory with its xy halo, blurred in x then y,
+//     and pushed into a per-thread ring of the last P planes held in registers; the z-blur of
+//     the plane R behind is emitted from the ring.  The ring index is a compile-time constant
+//     (the z loop is unrolled by the ring period P), so the ring never leaves registers.
+//     Reads I0 once (plus L2-resident halo) and writes I1 once.
+//   * axis_conv_kernel: one renormalised 1-D pass along x, y or z with optional pre/post
+//     scaling.  Used for large supports, for the transpose K^T and for dK/dsigma_z in the
+//     adjoint, and as an independent cross-check of the fused kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "emfuse_common.cuh"
+#include "emfuse_internal.cuh"
+
+namespace emfuse {
+
+namespace {
+
+constexpr int kTX = 64;   // tile width (outputs)
+constexpr int kTY = 16;   // tile height (outputs)
+constexpr int kThreads = 256;
+constexpr int kMaxRxy = 8;
+
+struct SmoothParams {
+    float wxy[2 * kMaxRxy + 1];  // taps w(d), d = -Rxy..Rxy
+    float wz[19];                // wz[j] = w(Rz - j), j = 0..2Rz (zero beyond)
+    int Rxy, Rz;
+};
+
+template <class Tin>
+__device__ __forceinline__ float load_in(const Tin* p) { return float(*p); }
+
+template <class Tin, int P>
+__global__ void __launch_bounds__(kThreads, 2)
+smooth_fused_kernel(const Tin* __restrict__ in, float* __restrict__ out, int nx, int ny, int nz,
+                    int64_t pitch, int z0, int z1, const float* __restrict__ inv_nx,
+                    const float* __restrict__ inv_ny, const float* __restrict__ inv_nz,
+                    SmoothParams prm) {
+    constexpr int MAXH = kTY + 2 * kMaxRxy;
+    __shared__ float s_in[MAXH][kTX + 2 * kMaxRxy + 1];
+    __shared__ float s_x[MAXH][kTX];
+
+    const int R = prm.Rxy;
+    const int Rz = prm.Rz;
+    const int x0 = blockIdx.x * kTX;
+    const int y0 = blockIdx.y * kTY;
+    const int tid = threadIdx.x;
+    const int tx = tid % 16;  // 4 consecutive x per thread
+    const int ty = tid / 16;  // one row per thread
+    const int W = kTX + 2 * R;
+    const int H = kTY + 2 * R;
+    const int64_t plane = pitch * (int64_t)ny;
+
+    float ring[P][4];
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ring[q][i] = 0.f;
+
+    // input planes that influence outputs [z0, z1)
+    const int zin_lo = max(0, z0 - Rz);
+    const int zin_hi = min(nz, z1 + Rz);  // exclusive
+    // zi runs from zin_lo to z1 - 1 + Rz; output zo = zi - Rz
+    const int zi_end = z1 + Rz;
+
+    for (int zb = zin_lo; zb < zi_end; zb += P) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int zi = zb + q;
+            if (zi >= zi_end) break;  // uniform across the CTA
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            if (zi < zin_hi) {
+                const Tin* src = in + (int64_t)zi * plane;
+                __syncthreads();
+                for (int e = tid; e < W * H; e += kThreads) {
+                    const int r = e / W, c = e - r * W;
+                    const int gy = y0 - R + r, gx = x0 - R + c;
+                    float val = 0.f;
+                    if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) val = load_in(src + (int64_t)gy * pitch + gx);
+                    s_in[r][c] = val;
+                }
+                __syncthreads();
+                for (int e = tid; e < kTX * H; e += kThreads) {
+                    const int r = e / kTX, c = e - r * kTX;
+                    float acc = 0.f;
+                    for (int d = -R; d <= R; ++d) acc = fmaf(prm.wxy[d + R], s_in[r][c + R + d], acc);
+                    const int gx = min(x0 + c, nx - 1);
+                    s_x[r][c] = acc * inv_nx[gx];
+                }
+                __syncthreads();
+                const int gy = min(y0 + ty, ny - 1);
+                const float iny = inv_ny[gy];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float acc = 0.f;
+                    for (int d = -R; d <= R; ++d) acc = fmaf(prm.wxy[d + R], s_x[ty + R + d][4 * tx + i], acc);
+                    v[i] = acc * iny;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ring[q][i] = v[i];
+            const int zo = zi - Rz;
+            if (zo >= z0 && zo < z1) {
+                float o4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int j = 0; j < P; ++j) {
+                    const float w = prm.wz[j];
+                    const int slot = (q - j + P * 4) % P;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) o4[i] = fmaf(w, ring[slot][i], o4[i]);
+                }
+                const float inz = inv_nz[zo];
+                const int gy = y0 + ty;
+                if (gy < ny) {
+                    float* dst = out + (int64_t)(zo - z0) * plane + (int64_t)gy * pitch;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int gx = x0 + 4 * tx + i;
+                        if (gx < nx) dst[gx] = o4[i] * inz;
+                    }
+                }
+            }
+        }
+    }
+}
+
+struct AxisParams {
+    float w[65];
+    int R;
+};
+
+// out[p] = beta * out[p] + post[idx_a(p)] * sum_{|d|<=R, inside} w(d) pre[idx_a(p+d)] in[p+d]
+// along axis a (0 = x, 1 = y, 2 = z).  pre / post may be null (= 1).
+template <class Tin>
+__global__ void axis_conv_kernel(const Tin* __restrict__ in, float* __restrict__ out, int nx,
+                                 int ny, int nz, int64_t pitch_in, int64_t pitch_out, int axis,
+                                 const float* __restrict__ pre, const float* __restrict__ post,
+                                 float beta, AxisParams prm) {
+    const int64_t n = (int64_t)nx * ny * nz;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = int(i % nx);
+        const int y = int((i / nx) % ny);
+        const int z = int(i / ((int64_t)nx * ny));
+        const int c = axis == 0 ? x : (axis == 1 ? y : z);
+        const int len = axis == 0 ? nx : (axis == 1 ? ny : nz);
+        const int64_t stride = axis == 0 ? 1 : (axis == 1 ? pitch_in : pitch_in * ny);
+        const int64_t base = (int64_t)z * pitch_in * ny + (int64_t)y * pitch_in + x;
+        float acc = 0.f;
+        for (int d = -prm.R; d <= prm.R; ++d) {
+            const int cc = c + d;
+            if (cc < 0 || cc >= len) continue;
+            float v = float(in[base + (int64_t)d * stride]);
+            if (pre) v *= pre[cc];
+            acc = fmaf(prm.w[d + prm.R], v, acc);
+        }
+        if (post) acc *= post[c];
+        const int64_t o = (int64_t)z * pitch_out * ny + (int64_t)y * pitch_out + x;
+        out[o] = beta == 0.f ? acc : fmaf(beta, out[o], acc);
+    }
+}
+
+}  // namespace
+
+int support_radius(float sigma) {
+    if (!(sigma > 0.f)) return 0;
+    return (int)std::floor(3.0 * (double)sigma + 1e-9);
+}
+
+std::vector<float> gaussian_taps(float sigma, int R) {
+    std::vector<float> w(2 * R + 1, 1.f);
+    if (sigma > 0.f)
+        for (int d = -R; d <= R; ++d) w[d + R] = (float)std::exp(-(double)d * d / (2.0 * (double)sigma * sigma));
+    return w;
+}
+
+// 1 / (sum of in-range taps) for every index 0..n-1 of an axis of length n.
+std::vector<float> inverse_norms(const std::vector<float>& w, int n) {
+    const int R = ((int)w.size() - 1) / 2;
+    std::vector<float> inv(n);
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int d = -R; d <= R; ++d)
+            if (i + d >= 0 && i + d < n) s += w[d + R];
+        inv[i] = (float)(1.0 / s);
+    }
+    return inv;
+}
+
+static int launch_axis(const void* in, int dt, float* out, int nx, int ny, int nz, int64_t pin,
+                       int64_t pout, int axis, const std::vector<float>& w, const float* pre,
+                       const float* post, float beta, cudaStream_t st) {
+    AxisParams prm{};
+    prm.R = ((int)w.size() - 1) / 2;
+    if (prm.R > 32) {
+        set_error("smoothing support radius above 32 taps is not supported");
+        return EMFUSE_EINVAL;
+    }
+    for (size_t i = 0; i < w.size(); ++i) prm.w[i] = w[i];
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, threads), (int64_t)kNumSMs * 32);
+    KernelScope ks("smooth_axis", st, (double)n * ((dt == EMFUSE_U8 ? 1.0 : 4.0) + 4.0 + (beta != 0.f ? 4.0 : 0.0)));
+    if (dt == EMFUSE_U8)
+        axis_conv_kernel<uint8_t><<<(unsigned)blocks, threads, 0, st>>>(
+            (const uint8_t*)in, out, nx, ny, nz, pin, pout, axis, pre, post, beta, prm);
+    else
+        axis_conv_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(
+            (const float*)in, out, nx, ny, nz, pin, pout, axis, pre, post, beta, prm);
+    EMF_CHECK_LAUNCH();
+    return EMFUSE_OK;
+}
+
+// Device table of the inverse normalisers of the three axes: [inv_x | inv_y | inv_z].
+static int upload_norms(DeviceBuffer& buf, const std::vector<float>& ix, const std::vector<float>& iy,
+                        const std::vector<float>& iz, cudaStream_t st, std::vector<float>& host) {
+    host.clear();
+    host.insert(host.end(), ix.begin(), ix.end());
+    host.insert(host.end(), iy.begin(), iy.end());
+    host.insert(host.end(), iz.begin(), iz.end());
+    EMF_TRY(buf.alloc(host.size() * sizeof(float), st));
+    EMF_CUDA(cudaMemcpyAsync(buf.as<float>(), host.data(), host.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, st));
+    return EMFUSE_OK;
+}
+
+int smooth_stack(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                 int64_t pitch, int64_t z0, int64_t z1, float sigma_xy, float sigma_z,
+                 cudaStream_t st, int force_path) {
+    const int Rxy = support_radius(sigma_xy);
+    const int Rz = support_radius(sigma_z);
+    const auto wxy = gaussian_taps(sigma_xy, Rxy);
+    const auto wz = gaussian_taps(sigma_z, Rz);
+    std::vector<float> host;
+    DeviceBuffer norms;
+    EMF_TRY(upload_norms(norms, inverse_norms(wxy, (int)nx), inverse_norms(wxy, (int)ny),
+                         inverse_norms(wz, (int)nz), st, host));
+    const float* inv_x = norms.as<float>();
+    const float* inv_y = inv_x + nx;
+    const float* inv_z = inv_y + ny;
+
+    const bool fused_ok = Rxy <= kMaxRxy && Rz <= 9 && force_path != 1;
+    if (fused_ok) {
+        SmoothParams prm{};
+        prm.Rxy = Rxy;
+        prm.Rz = Rz;
+        for (int d = 0; d < 2 * Rxy + 1; ++d) prm.wxy[d] = wxy[d];
+        for (int j = 0; j < 2 * Rz + 1; ++j) prm.wz[j] = wz[2 * Rz - j];
+        dim3 grid((unsigned)ceil_div(nx, kTX), (unsigned)ceil_div(ny, kTY));
+        const int P = 2 * Rz + 1;
+        const int64_t zin0 = std::max<int64_t>(0, z0 - Rz), zin1 = std::min<int64_t>(nz, z1 + Rz);
+        KernelScope ks("smooth_fused", st,
+                       (double)nx * ny * ((zin1 - zin0) * (dt == EMFUSE_U8 ? 1.0 : 4.0) + (z1 - z0) * 4.0));
+#define EMF_SMOOTH_LAUNCH(PP)                                                                  \
+    do {                                                                                       \
+        if (dt == EMFUSE_U8)                                                                   \
+            smooth_fused_kernel<uint8_t, PP><<<grid, kThreads, 0, st>>>(                       \
+                (const uint8_t*)in, out, (int)nx, (int)ny, (int)nz, pitch, (int)z0, (int)z1,   \
+                inv_x, inv_y, inv_z, prm);                                                     \
+        else                                                                                   \
+            smooth_fused_kernel<float, PP><<<grid, kThreads, 0, st>>>(                         \
+                (const float*)in, out, (int)nx, (int)ny, (int)nz, pitch, (int)z0, (int)z1,     \
+                inv_x, inv_y, inv_z, prm);                                                     \
+    } while (0)
+        if (P <= 1) EMF_SMOOTH_LAUNCH(1);
+        else if (P <= 7) EMF_SMOOTH_LAUNCH(7);
+        else EMF_SMOOTH_LAUNCH(19);
+#undef EMF_SMOOTH_LAUNCH
+        EMF_CHECK_LAUNCH();
+        return EMFUSE_OK;
+    }
+    // Three renormalised 1-D passes (x, y over the needed input planes; then z).
+    const int64_t zin0 = std::max<int64_t>(0, z0 - Rz), zin1 = std::min<int64_t>(nz, z1 + Rz);
+    const int64_t nzin = zin1 - zin0;
+    DeviceBuffer t1, t2;
+    EMF_TRY(t1.alloc((size_t)(nzin * ny * nx) * sizeof(float), st));
+    EMF_TRY(t2.alloc((size_t)(nzin * ny * nx) * sizeof(float), st));
+    const size_t esz = dt == EMFUSE_U8 ? 1 : 4;
+    const void* in0 = (const char*)in + (size_t)(zin0 * ny * pitch) * esz;
+    EMF_TRY(launch_axis(in0, dt, t1.as<float>(), (int)nx, (int)ny, (int)nzin, pitch, nx, 0, wxy,
+                        nullptr, inv_x, 0.f, st));
+    EMF_TRY(launch_axis(t1.as<float>(), EMFUSE_F32, t2.as<float>(), (int)nx, (int)ny, (int)nzin,
+                        nx, nx, 1, wxy, nullptr, inv_y, 0.f, st));
+    // z pass: only the requested output planes, normaliser indexed by absolute z
+    DeviceBuffer tz;
+    EMF_TRY(tz.alloc((size_t)(nzin * ny * nx) * sizeof(float), st));
+    std::vector<float> iz_local(host.begin() + nx + ny + zin0, host.begin() + nx + ny + zin1);
+    // renormalisation by the absolute-z table: recompute in local coordinates would be wrong
+    // when the slab is a sub-range, so scale with the global table slice.
+    DeviceBuffer izb;
+    EMF_TRY(izb.alloc(iz_local.size() * sizeof(float), st));
+    EMF_CUDA(cudaMemcpyAsync(izb.as<float>(), iz_local.data(), iz_local.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, st));
+    EMF_TRY(launch_axis(t2.as<float>(), EMFUSE_F32, tz.as<float>(), (int)nx, (int)ny, (int)nzin,
+                        nx, nx, 2, wz, nullptr, izb.as<float>(), 0.f, st));
+    EMF_CUDA(cudaMemcpy2DAsync(out, pitch * sizeof(float),
+                               tz.as<float>() + (z0 - zin0) * ny * nx, nx * sizeof(float),
+                               nx * sizeof(float), (size_t)((z1 - z0) * ny), cudaMemcpyDeviceToDevice, st));
+    EMF_CUDA(cudaStreamSynchronize(st));  // host vectors above must outlive the async copies
+    return EMFUSE_OK;
+}
+
+// K^T g for K = Kz Ky Kx (dense float stack, pitch nx):  (K_a^T v)(q) = sum_p w(p-q) v(p)/N(p).
+int smooth_transpose(const float* g, float* out, int64_t nx, int64_t ny, int64_t nz,
+                     float sigma_xy, float sigma_z, cudaStream_t st) {
+    const int Rxy = support_radius(sigma_xy), Rz = support_radius(sigma_z);
+    const auto wxy = gaussian_taps(sigma_xy, Rxy);
+    const auto wz = gaussian_taps(sigma_z, Rz);
+    std::vector<float> host;
+    DeviceBuffer norms;
+    EMF_TRY(upload_norms(norms, inverse_norms(wxy, (int)nx), inverse_norms(wxy, (int)ny),
+                         inverse_norms(wz, (int)nz), st, host));
+    const float* inv_x = norms.as<float>();
+    const float* inv_y = inv_x + nx;
+    const float* inv_z = inv_y + ny;
+    DeviceBuffer t1;
+    EMF_TRY(t1.alloc((size_t)(nx * ny * nz) * sizeof(float), st));
+    EMF_TRY(launch_axis(g, EMFUSE_F32, out, (int)nx, (int)ny, (int)nz, nx, nx, 2, wz, inv_z, nullptr, 0.f, st));
+    EMF_TRY(launch_axis(out, EMFUSE_F32, t1.as<float>(), (int)nx, (int)ny, (int)nz, nx, nx, 1, wxy, inv_y, nullptr, 0.f, st));
+    EMF_TRY(launch_axis(t1.as<float>(), EMFUSE_F32, out, (int)nx, (int)ny, (int)nz, nx, nx, 0, wxy, inv_x, nullptr, 0.f, st));
+    EMF_CUDA(cudaStreamSynchronize(st));
+    return EMFUSE_OK;
+}
+
+// (dK/dsigma_z) I0 with the support radius fixed at floor(3 sigma_z):
+//   Kz' v = (sum w' v) / N - (sum w v) N' / N^2,  w'(d) = w(d) d^2 / sigma^3.
+int smooth_dsigma_z(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                    float sigma_xy, float sigma_z, cudaStream_t st) {
+    const int Rxy = support_radius(sigma_xy), Rz = support_radius(sigma_z);
+    const auto wxy = gaussian_taps(sigma_xy, Rxy);
+    const auto wz = gaussian_taps(sigma_z, Rz);
+    std::vector<float> dwz(wz.size());
+    for (int d = -Rz; d <= Rz; ++d)
+        dwz[d + Rz] = sigma_z > 0.f ? (float)((double)wz[d + Rz] * d * d / std::pow((double)sigma_z, 3)) : 0.f;
+    const auto ix = inverse_norms(wxy, (int)nx), iy = inverse_norms(wxy, (int)ny), iz = inverse_norms(wz, (int)nz);
+    std::vector<float> c1(nz), c2(nz);  // 1/N and -N'/N^2 per plane
+    for (int z = 0; z < nz; ++z) {
+        double N = 0, dN = 0;
+        for (int d = -Rz; d <= Rz; ++d)
+            if (z + d >= 0 && z + d < nz) { N += wz[d + Rz]; dN += dwz[d + Rz]; }
+        c1[z] = (float)(1.0 / N);
+        c2[z] = (float)(-dN / (N * N));
+    }
+    std::vector<float> host;
+    DeviceBuffer norms, cz;
+    EMF_TRY(upload_norms(norms, ix, iy, iz, st, host));
+    std::vector<float> hc(c1);
+    hc.insert(hc.end(), c2.begin(), c2.end());
+    EMF_TRY(cz.alloc(hc.size() * sizeof(float), st));
+    EMF_CUDA(cudaMemcpyAsync(cz.as<float>(), hc.data(), hc.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    DeviceBuffer t1, t2;
+    EMF_TRY(t1.alloc((size_t)(nx * ny * nz) * sizeof(float), st));
+    EMF_TRY(t2.alloc((size_t)(nx * ny * nz) * sizeof(float), st));
+    const float* inv_x = norms.as<float>();
+    const float* inv_y = inv_x + nx;
+    EMF_TRY(launch_axis(in, dt, t1.as<float>(), (int)nx, (int)ny, (int)nz, nx, nx, 0, wxy, nullptr, inv_x, 0.f, st));
+    EMF_TRY(launch_axis(t1.as<float>(), EMFUSE_F32, t2.as<float>(), (int)nx, (int)ny, (int)nz, nx, nx, 1, wxy, nullptr, inv_y, 0.f, st));
+    EMF_TRY(launch_axis(t2.as<float>(), EMFUSE_F32, out, (int)nx, (int)ny, (int)nz, nx, nx, 2, dwz, nullptr, cz.as<float>(), 0.f, st));
+    EMF_TRY(launch_axis(t2.as<float>(), EMFUSE_F32, out, (int)nx, (int)ny, (int)nz, nx, nx, 2, wz, nullptr, cz.as<float>() + nz, 1.f, st));
+    EMF_CUDA(cudaStreamSynchronize(st));
+    return EMFUSE_OK;
+}
+
+}  // namespace emfuse

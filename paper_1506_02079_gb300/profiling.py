@@ -1,0 +1,95 @@
+"""Per-kernel timing and roofline numbers from the library's own CUDA-event instrumentation.
+
+``profile_steps`` runs a callable with ``emfuse_profile_begin/end`` around it: every kernel
+launch of the library is bracketed by CUDA events on its own stream and carries the
+algorithmic bytes of the launch (each needed input element read once, each output written
+once).  ``kernel_roofline`` turns the dominant kernel's totals into achieved GB/s against the
+measured HBM copy bandwidth of the machine.
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import json
+import os
+
+from . import api
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+FALLBACK_HBM_GBS = 6800.0
+
+
+class _Prof(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+def profile_steps(step, n: int) -> list[dict]:
+    L = api.lib()
+    L.emfuse_profile_begin.argtypes = []
+    L.emfuse_profile_begin.restype = None
+    L.emfuse_profile_end.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.emfuse_profile_end.restype = ctypes.c_int
+    L.emfuse_profile_begin()
+    try:
+        for _ in range(n):
+            step()
+    finally:
+        buf = (_Prof * 64)()
+        k = L.emfuse_profile_end(ctypes.addressof(buf), 64)
+    if k < 0:
+        raise api.EmfuseError(2, L.emfuse_last_error().decode())
+    total = sum(buf[i].total_ms for i in range(min(k, 64))) or 1.0
+    out = []
+    for i in range(min(k, 64)):
+        p = buf[i]
+        out.append({"name": p.name.decode(), "launches": int(p.launches) // max(n, 1),
+                    "ms_per_step": p.total_ms / n, "share": p.total_ms / total,
+                    "gbs": (p.bytes / (p.total_ms * 1e-3) / 1e9) if p.total_ms > 0 else None,
+                    "bytes_per_launch": p.bytes / max(p.launches, 1)})
+    return out
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash(name: str) -> str:
+    """Hash of the CUDA sources, so stored ncu traffic is dropped once a kernel changes."""
+    h = hashlib.sha256()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(name: str):
+    """dram read+write bytes per launch of kernel `name` from the committed ncu summary
+    (profiles/traffic.json), or None if absent or taken on different sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = d.get(name)
+    if not e or e.get("source_hash") != kernel_source_hash(name):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def kernel_roofline(prof: list[dict]) -> dict:
+    top = max(prof, key=lambda p: p["share"])
+    peak, kind = measured_hbm_peak()
+    return {"kernel": top["name"], "bound": "hbm", "achieved": top["gbs"], "peak": peak,
+            "unit": "GB/s", "frac": (top["gbs"] / peak) if top["gbs"] else None,
+            "peak_source": f"hbm_gbs of {kind}", "share_of_step": top["share"],
+            "bytes_per_launch": top["bytes_per_launch"], "traffic": stored_traffic(top["name"])}

@@ -1,0 +1,170 @@
+"""GPU path vs the CPU FP64 oracle, element by element, through the C ABI.
+
+Tolerances (written here, derived in the design notes):
+* smoothing: fp32 accumulation of at most 7 + 7 + 19 taps of values <= 255 ->
+  max |d| <= 2e-5 * 255;
+* solves: max |f - f_oracle| <= 1e-4 * 255 (the intensity range of 8-bit EM data) for the plain
+  FP32 path; the mixed (FP32 + FP64 defect correction) and FP64 paths must in addition
+  report a relative residual <= 1e-6 on every slice.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import emfuse_oracle as O
+from paper_1506_02079_gb300 import api
+from paper_1506_02079_gb300.synthetic import make_stack, make_ragged_batch
+
+pytestmark = pytest.mark.gpu
+
+SMOOTH_TOL = 2e-5 * 255.0
+SOLVE_TOL = 1e-4 * 255.0
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    api.lib()
+    return torch.device("cuda", 0)
+
+
+def maxdiff(a, b):
+    return float(np.max(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64))))
+
+
+# ----------------------------------------------------------------------------- phase 1
+@pytest.mark.parametrize("shape", [(16, 256, 256), (5, 17, 33), (1, 1, 1), (4, 7, 130), (23, 70, 9)])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.uint8])
+def test_smooth_matches_oracle(dev, shape, dtype):
+    I0 = make_stack(*shape, seed=11, out_dtype=dtype)
+    out = api.emfuse_smooth_z(I0.to(dev), 1.0, 3.0).cpu().numpy()
+    ref = O.smooth_stack(I0.double().numpy(), 1.0, 3.0)
+    assert maxdiff(out, ref) <= SMOOTH_TOL
+
+
+@pytest.mark.parametrize("sig", [(0.0, 3.0), (1.0, 0.0), (0.5, 1.0), (2.0, 4.5), (1.3, 3.3)])
+def test_smooth_other_sigmas_and_fallback_path(dev, sig):
+    """sigma_z = 4.5 (support 13) exercises the three-pass path."""
+    I0 = make_stack(30, 40, 50, seed=12)
+    out = api.emfuse_smooth_z(I0.to(dev), *sig).cpu().numpy()
+    ref = O.smooth_stack(I0.double().numpy(), *sig)
+    assert maxdiff(out, ref) <= SMOOTH_TOL
+
+
+def test_smooth_z_range_equals_full_stack(dev):
+    """A slab with floor(3 sigma_z) halo planes gives exactly the stack's slices
+    (Sec. 3 "Distributed Processing")."""
+    I0 = make_stack(40, 64, 48, seed=13).to(dev)
+    full = api.emfuse_smooth_z(I0, 1.0, 3.0)
+    part = api.emfuse_smooth_z(I0[5:35].contiguous(), 1.0, 3.0, z0=9, z1=21)
+    assert torch.equal(part, full[14:26])
+    sub = api.emfuse_smooth_z(I0, 1.0, 3.0, z0=3, z1=17)
+    assert torch.equal(sub, full[3:17])
+
+
+# ----------------------------------------------------------------------------- phase 2
+def oracle_solve(s, o, alpha):
+    return np.stack([O.solve_dct(s[j], o[j], alpha) for j in range(s.shape[0])])
+
+
+@pytest.mark.parametrize("alpha", [1e-3, 1e-2, 1e-1])
+@pytest.mark.parametrize("precision", [api.PREC_FP32, api.PREC_MIXED, api.PREC_FP64])
+def test_solve_config_plain_stack(dev, alpha, precision):
+    """16 slices of 256 x 256 (s = oracle smoothing, o = I0)."""
+    I0 = make_stack(16, 256, 256, seed=0)
+    s = O.smooth_stack(I0.double().numpy(), 1.0, 3.0)
+    o = I0.double().numpy()
+    tol = 1e-5 if precision == api.PREC_FP32 else 1e-6
+    opts = api.default_opts(precision=precision, tol=tol)
+    f, stats = api.emfuse_screened_poisson(torch.from_numpy(s).float().to(dev), I0.to(dev), alpha,
+                                           opts, return_stats=True)
+    ref = oracle_solve(s.astype(np.float32), I0.numpy(), alpha)
+    assert maxdiff(f.cpu().numpy(), ref) <= SOLVE_TOL
+    assert all(st["converged"] for st in stats)
+    if precision != api.PREC_FP32:
+        assert max(st["rel_residual"] for st in stats) <= 1e-6
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 17), (17, 1), (2, 3), (21, 26), (255, 193),
+                                   (3, 4097), (64, 64), (100, 37)])
+@pytest.mark.parametrize("alpha", [1e-3, 0.1])
+def test_solve_odd_sizes(dev, shape, alpha):
+    rng = np.random.default_rng(shape[0] * 1000 + shape[1])
+    s = rng.uniform(0, 255, size=shape).astype(np.float32)
+    o = (0.9 * s + rng.normal(0, 10, size=shape)).astype(np.float32)
+    f, stats = api.emfuse_screened_poisson(torch.from_numpy(s).to(dev), torch.from_numpy(o).to(dev),
+                                           alpha, return_stats=True)
+    ref = O.solve_dct(s, o, alpha)
+    assert maxdiff(f.cpu().numpy(), ref) <= SOLVE_TOL
+    assert stats[0]["rel_residual"] <= 1e-6
+
+
+def test_solve_ragged_batch(dev):
+    """One call on slices of mixed sizes (the batched configuration, scaled down)."""
+    s, o, ny, nx, offs = make_ragged_batch(12, seed=2, side_lo=16, side_hi=300)
+    sizes = list(zip(ny.tolist(), nx.tolist()))
+    sizes[3] = (37, 211)  # a non-square one
+    s, o, ny, nx, offs = make_ragged_batch(12, seed=2, sides=sizes)
+    f, stats = api.emfuse_screened_poisson(s.to(dev), o.to(dev), 1e-3, nx=nx, ny=ny, offsets=offs,
+                                           return_stats=True)
+    f = f.cpu().numpy()
+    for j in range(len(nx)):
+        a, h, w = int(offs[j]), int(ny[j]), int(nx[j])
+        ref = O.solve_dct(s[a:a + h * w].numpy().reshape(h, w), o[a:a + h * w].numpy().reshape(h, w), 1e-3)
+        assert maxdiff(f[a:a + h * w].reshape(h, w), ref) <= SOLVE_TOL, j
+        assert stats[j]["rel_residual"] <= 1e-6
+
+
+def test_solve_reports_nonconvergence(dev):
+    s = torch.rand(64, 64, device=dev) * 255
+    o = torch.rand(64, 64, device=dev) * 255
+    f, stats = api.emfuse_screened_poisson(s, o, 1e-3, api.default_opts(max_vcycles=1, tol=1e-12),
+                                           return_stats=True, allow_noconv=True)
+    assert stats[0]["vcycles"] == 1 and not stats[0]["converged"]
+    with pytest.raises(api.EmfuseError):
+        api.emfuse_screened_poisson(s, o, 1e-3, api.default_opts(max_vcycles=1, tol=1e-12))
+
+
+def test_constant_stack_is_fixed_point(dev):
+    I0 = torch.full((6, 33, 40), 77.0, device=dev)
+    out = api.emfuse_correct_stack(I0, 1.0, 3.0, 1e-3)
+    assert float((out - 77.0).abs().max()) <= 1e-4
+
+
+# ----------------------------------------------------------------------------- both phases
+@pytest.mark.parametrize("dtype", [torch.float32, torch.uint8])
+@pytest.mark.parametrize("on_host", [False, True])
+def test_correct_stack_matches_oracle(dev, dtype, on_host):
+    I0 = make_stack(16, 256, 256, seed=0, out_dtype=dtype)
+    if on_host:
+        inp = I0.pin_memory()
+    else:
+        inp = I0.to(dev)
+    out, stats = api.emfuse_correct_stack(inp, 1.0, 3.0, 0.01, return_stats=True)
+    _, ref = O.correct_stack(I0.double().numpy(), 1.0, 3.0, 0.01)
+    assert maxdiff(out.cpu().numpy(), ref) <= SOLVE_TOL
+    assert max(st["rel_residual"] for st in stats) <= 1e-6
+
+
+# ----------------------------------------------------------------------------- adjoint
+def test_backward_matches_oracle(dev):
+    nz, ny, nx = 6, 24, 20
+    I0 = make_stack(nz, ny, nx, seed=3)
+    g = torch.from_numpy(np.random.default_rng(5).normal(size=(nz, ny, nx))).float()
+    sxy, sz, alpha = 1.0, 1.5, 0.05
+    Id = I0.to(dev)
+    s = api.emfuse_smooth_z(Id, sxy, sz)
+    f = api.emfuse_screened_poisson(s, Id, alpha)
+    gr = api.emfuse_backward(g.to(dev), f, s, Id, sxy, sz, alpha)
+    x = I0.double().numpy()
+    dI0, dalpha, dsig = O.backward_stack(g.double().numpy(), x, sxy, sz, alpha)
+    s_np = O.smooth_stack(x, sxy, sz)
+    lam = np.stack([O.apply_Ainv(g[j].double().numpy(), alpha) for j in range(nz)])
+    scale = lambda a: float(np.max(np.abs(a)))
+    assert maxdiff(gr["s"].cpu().numpy(), alpha * lam) <= 1e-4 * scale(alpha * lam)
+    assert maxdiff(gr["o"].cpu().numpy(), O.laplacian(lam)) <= 1e-4 * scale(O.laplacian(lam))
+    assert maxdiff(gr["in0"].cpu().numpy(), dI0) <= 1e-4 * scale(dI0)
+    assert gr["alpha"] == pytest.approx(dalpha, rel=2e-3)
+    assert gr["sigma_z"] == pytest.approx(dsig, rel=2e-3)
+    assert s_np.shape == (nz, ny, nx)
