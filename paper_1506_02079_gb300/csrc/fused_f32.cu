@@ -1,0 +1,49 @@
+// FP32 instantiations of the fused multigrid schedule (kernels in fused_impl.cuh).
+#include "fused_impl.cuh"
+
+namespace emfuse {
+using fused_detail::kWaveWarps;
+
+template <class T>
+static int launch_wave_impl(const WaveArgs<T>& a, int S, bool zero_init, bool up, cudaStream_t st, double bytes) {
+    if (a.nitems == 0) return EMFUSE_OK;
+    const unsigned grid = (unsigned)ceil_div(a.nitems, kWaveWarps);
+    const char* name = up ? (a.k == 0 ? "wave_up_l0" : "wave_up_coarse")
+                          : (a.k == 0 ? "wave_down_l0" : "wave_down_coarse");
+    KernelScope ks(name, st, bytes);
+#define EMF_WAVE(SS)                                                                         \
+    do {                                                                                     \
+        if (up) fused_detail::k_wave<T, SS, false, true><<<grid, kWaveWarps * 32, 0, st>>>(a);             \
+        else if (zero_init) fused_detail::k_wave<T, SS, true, false><<<grid, kWaveWarps * 32, 0, st>>>(a); \
+        else fused_detail::k_wave<T, SS, false, false><<<grid, kWaveWarps * 32, 0, st>>>(a);              \
+    } while (0)
+    switch (S) {
+        case 2: EMF_WAVE(2); break;
+        case 4: EMF_WAVE(4); break;
+        case 6: EMF_WAVE(6); break;
+        default: set_error("wavefront kernel: unsupported sweep count"); return EMFUSE_EINVAL;
+    }
+#undef EMF_WAVE
+    EMF_CHECK_LAUNCH();
+    return EMFUSE_OK;
+}
+
+template <class T>
+static int launch_tail_impl(const TailArgs<T>& a, cudaStream_t st, double bytes) {
+    if (a.nslices == 0) return EMFUSE_OK;
+    KernelScope ks("coarse_tail", st, bytes);
+    fused_detail::k_tail<T><<<(unsigned)a.nslices, 512, 0, st>>>(a);
+    EMF_CHECK_LAUNCH();
+    return EMFUSE_OK;
+}
+
+template <>
+int launch_wave<float>(const WaveArgs<float>& a, int S, bool zero_init, bool up, cudaStream_t st, double bytes) {
+    return launch_wave_impl<float>(a, S, zero_init, up, st, bytes);
+}
+template <>
+int launch_tail<float>(const TailArgs<float>& a, cudaStream_t st, double bytes) {
+    return launch_tail_impl<float>(a, st, bytes);
+}
+
+}  // namespace emfuse

@@ -1,7 +1,8 @@
-// Device-side pieces of the multigrid shared by the reference (one kernel per half-sweep)
-// and the fused kernels: the level descriptor, the finite-volume stencil of a level, the
-// Gauss-Seidel update, the residual and the prolongation weights.  Both schedules call the
-// same inline functions with explicit fma ordering, so they produce bit-identical iterates.
+// Device-side pieces of the multigrid shared by the reference schedule (one kernel per
+// half-sweep) and the fused schedule (wavefront kernels + coarse tail): the level
+// descriptor, the finite-volume stencil of a level, the Gauss-Seidel update, the residual and
+// the prolongation weights.  Both schedules call the same inline functions with explicit
+// fma ordering, so they produce bit-identical iterates.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -11,53 +12,89 @@
 
 namespace emfuse {
 
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float div_t(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_t(double a, double b) { return __ddiv_rn(a, b); }
+
 // One slice at one multigrid level (device-visible).
 template <class T>
 struct LSlice {
     T* u;              // iterate, `pitch` elements per row
     T* b;              // right-hand side
     int nx, ny, pitch;
-    const T* uc;       // level k+1 iterate (null at the coarsest level of this slice)
+    T* uc;             // level k+1 iterate and rhs (null at the coarsest level of this slice)
+    T* bc;
     int ncx, ncy, pitchc;
-    const T* uf;       // level k-1 iterate and rhs (null at k = 0)
-    const T* bf;
+    T* uf;             // level k-1 iterate and rhs (null at k = 0)
+    T* bf;
     int nfx, nfy, pitchf;
     int n0x, n0y;      // finest-level size (fixes the cell geometry of every level)
     int slice;         // index of the slice in the caller's batch
     int tiles_x;       // reference-kernel tiles along x
+    int fstrips;       // wavefront-kernel strips along x
 };
+
+// Per-axis geometry of a cell: its width (level units) and the face coefficients
+// 2 / (w_i + w_{i+-1}) to its lower / upper neighbour (0 at the slice boundary).
+template <class T>
+struct AxisCoef {
+    T w, gm, gp;
+};
+
+template <class T>
+__device__ __forceinline__ AxisCoef<T> axis_coef(int i, int n, int n0, int k) {
+    AxisCoef<T> a;
+    if (k == 0) {
+        a.w = T(1);
+        a.gm = i > 0 ? T(1) : T(0);
+        a.gp = i + 1 < n ? T(1) : T(0);
+        return a;
+    }
+    if (i >= 1 && i + 2 < n) {  // cells i-1, i, i+1 are all full: every coefficient is 1
+        a.w = T(1);
+        a.gm = T(1);
+        a.gp = T(1);
+        return a;
+    }
+    a.w = cell_width<T>(i, n0, k);
+    a.gm = face_coeff<T>(i - 1, n, n0, k);
+    a.gp = face_coeff<T>(i, n, n0, k);
+    return a;
+}
 
 template <class T>
 struct Coef {
     T cw, ce, cn, cs, D;
 };
 
-// Finite-volume stencil of level k at cell (x, y) (interior: alpha + L/4^k).
+// Finite-volume stencil of level k at a cell (interior cells: alpha + L/4^k).
 template <class T>
-__device__ __forceinline__ Coef<T> coef_at(int x, int y, int nx, int ny, int n0x, int n0y, int k,
-                                           T alpha, T sk) {
+__device__ __forceinline__ Coef<T> make_coef(const AxisCoef<T>& ax, const AxisCoef<T>& ay, int k,
+                                             T alpha, T sk) {
     Coef<T> c;
     if (k == 0) {
-        c.cw = x > 0 ? T(1) : T(0);
-        c.ce = x + 1 < nx ? T(1) : T(0);
-        c.cn = y > 0 ? T(1) : T(0);
-        c.cs = y + 1 < ny ? T(1) : T(0);
+        c.cw = ax.gm;
+        c.ce = ax.gp;
+        c.cn = ay.gm;
+        c.cs = ay.gp;
         c.D = alpha + (((c.cw + c.ce) + c.cn) + c.cs);
         return c;
     }
-    const T wx = cell_width<T>(x, n0x, k), wy = cell_width<T>(y, n0y, k);
-    c.cw = sk * (wy * face_coeff<T>(x - 1, nx, n0x, k));
-    c.ce = sk * (wy * face_coeff<T>(x, nx, n0x, k));
-    c.cn = sk * (wx * face_coeff<T>(y - 1, ny, n0y, k));
-    c.cs = sk * (wx * face_coeff<T>(y, ny, n0y, k));
-    c.D = alpha * (wx * wy) + (((c.cw + c.ce) + c.cn) + c.cs);
+    c.cw = sk * (ay.w * ax.gm);
+    c.ce = sk * (ay.w * ax.gp);
+    c.cn = sk * (ax.w * ay.gm);
+    c.cs = sk * (ax.w * ay.gp);
+    c.D = fma_t(alpha, ax.w * ay.w, ((c.cw + c.ce) + c.cn) + c.cs);
     return c;
 }
 
-__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ float div_t(float a, float b) { return __fdiv_rn(a, b); }
-__device__ __forceinline__ double div_t(double a, double b) { return __ddiv_rn(a, b); }
+template <class T>
+__device__ __forceinline__ Coef<T> coef_at(int x, int y, int nx, int ny, int n0x, int n0y, int k,
+                                           T alpha, T sk) {
+    return make_coef<T>(axis_coef<T>(x, nx, n0x, k), axis_coef<T>(y, ny, n0y, k), k, alpha, sk);
+}
+
 
 // Gauss-Seidel update u_p = (b_p + sum_q c_pq u_q) / D_p.
 template <class T>
@@ -79,8 +116,8 @@ __device__ __forceinline__ T residual_at(const Coef<T>& c, T b, T u, T uw, T ue,
     return fma_t(-c.D, u, acc);
 }
 
-// Linear interpolation weight along one axis from level k+1 (coarse) to level k (fine):
-// fine cell x lies between coarse centres I = x/2 and J; returns J and its weight.
+// Linear interpolation along one axis from level k+1 (coarse) to level k (fine): fine cell x
+// lies between coarse centres I = x/2 and J; returns J and its weight (0 if J = I).
 template <class T>
 __device__ __forceinline__ void interp_axis(int x, int n0, int k, int nc, int& I, int& J, T& wJ) {
     I = x >> 1;
@@ -100,7 +137,15 @@ __device__ __forceinline__ void interp_axis(int x, int n0, int k, int nc, int& I
     wJ = T(cf2 > cc2 ? cf2 - cc2 : cc2 - cf2) / T(cj2 > cc2 ? cj2 - cc2 : cc2 - cj2);
 }
 
-// Bilinear correction at fine cell (x, y) of level k from the level k+1 iterate.
+// Bilinear combination of the four coarse values around a fine cell.
+template <class T>
+__device__ __forceinline__ T bilinear(T r0I, T r0J, T r1I, T r1J, T wx, T wy) {
+    const T a = fma_t(wx, r0J - r0I, r0I);
+    const T b = fma_t(wx, r1J - r1I, r1I);
+    return fma_t(wy, b - a, a);
+}
+
+// Correction at fine cell (x, y) of level k interpolated from the level k+1 iterate.
 template <class T>
 __device__ __forceinline__ T prolong_at(const T* __restrict__ uc, int pitchc, int x, int y, int ncx,
                                         int ncy, int n0x, int n0y, int k) {
@@ -110,9 +155,52 @@ __device__ __forceinline__ T prolong_at(const T* __restrict__ uc, int pitchc, in
     interp_axis<T>(y, n0y, k, ncy, Iy, Jy, wy);
     const T* r0 = uc + (int64_t)Iy * pitchc;
     const T* r1 = uc + (int64_t)Jy * pitchc;
-    const T a = fma_t(wx, r0[Jx] - r0[Ix], r0[Ix]);
-    const T b = fma_t(wx, r1[Jx] - r1[Ix], r1[Ix]);
-    return fma_t(wy, b - a, a);
+    return bilinear<T>(r0[Ix], r0[Jx], r1[Ix], r1[Jx], wx, wy);
 }
+
+__device__ __forceinline__ int find_item(const int64_t* __restrict__ ts, int n, int64_t t) {
+    int lo = 0, hi = n;  // ts[0] = 0 <= t < ts[n]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (ts[mid] <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- fused schedule (fused.cu)
+constexpr int kWaveHalo = 8;                      // x halo of a strip (cells, multiple of 4)
+constexpr int kWaveWidth = 128;                   // strip width: 32 lanes x 4 cells
+constexpr int kWaveIW = kWaveWidth - 2 * kWaveHalo;  // interior cells per strip
+constexpr int kTailMax = 64;                      // levels with max side <= this go to the tail
+
+template <class T>
+struct WaveArgs {
+    const LSlice<T>* sl;         // slices that use the wavefront kernel at this level
+    const int64_t* item_start;   // warp work items per slice, prefix sums (nsl + 1)
+    int nsl;
+    int64_t nitems;
+    int k;
+    int ch;                      // rows per work item (even)
+    T alpha;
+    T sk;
+    const int* active;
+};
+
+template <class T>
+struct TailArgs {
+    const LSlice<T>* table;      // all levels of all slices
+    const int* level_off;        // first table entry of each slice
+    const int* nlev;             // levels of each slice
+    const int* kc;               // first level handled by the tail, per slice
+    int nslices;
+    T alpha;
+    int nu_pre, nu_post;
+    const int* active;
+};
+
+template <class T>
+int launch_wave(const WaveArgs<T>& a, int S, bool zero_init, bool up, cudaStream_t st, double bytes);
+template <class T>
+int launch_tail(const TailArgs<T>& a, cudaStream_t st, double bytes);
 
 }  // namespace emfuse

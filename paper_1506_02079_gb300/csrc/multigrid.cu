@@ -39,14 +39,6 @@ namespace {
 constexpr int kBX = 32;
 constexpr int kBY = 8;
 
-__device__ __forceinline__ int find_slice(const int64_t* __restrict__ ts, int n, int64_t t) {
-    int lo = 0, hi = n;  // ts[0] = 0 <= t < ts[n]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (ts[mid] <= t) lo = mid; else hi = mid;
-    }
-    return lo;
-}
 
 template <class T>
 struct LevelArgs {
@@ -63,7 +55,7 @@ struct LevelArgs {
 template <class T>
 __global__ void __launch_bounds__(kBX* kBY) k_relax(LevelArgs<T> a, int color) {
     const int64_t t = blockIdx.x;
-    const int j = find_slice(a.tile_start, a.nsl, t);
+    const int j = find_item(a.tile_start, a.nsl, t);
     const LSlice<T> S = a.sl[j];
     if (a.active && !a.active[S.slice]) return;
     const int lt = int(t - a.tile_start[j]);
@@ -84,7 +76,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_relax(LevelArgs<T> a, int color) {
 template <class T>
 __global__ void __launch_bounds__(kBX* kBY) k_residual_restrict(LevelArgs<T> a, T sk_fine) {
     const int64_t t = blockIdx.x;
-    const int j = find_slice(a.tile_start, a.nsl, t);
+    const int j = find_item(a.tile_start, a.nsl, t);
     const LSlice<T> S = a.sl[j];
     if (a.active && !a.active[S.slice]) return;
     const int lt = int(t - a.tile_start[j]);
@@ -117,9 +109,9 @@ __global__ void __launch_bounds__(kBX* kBY) k_residual_restrict(LevelArgs<T> a, 
 template <class T>
 __global__ void __launch_bounds__(kBX* kBY) k_prolong_add(LevelArgs<T> a) {
     const int64_t t = blockIdx.x;
-    const int j = find_slice(a.tile_start, a.nsl, t);
+    const int j = find_item(a.tile_start, a.nsl, t);
     const LSlice<T> S = a.sl[j];
-    if (!S.uc) return;
+    if (!S.uc) return;  // coarsest level of this slice
     if (a.active && !a.active[S.slice]) return;
     const int lt = int(t - a.tile_start[j]);
     const int x = (lt % S.tiles_x) * kBX + threadIdx.x;
@@ -129,95 +121,127 @@ __global__ void __launch_bounds__(kBX* kBY) k_prolong_add(LevelArgs<T> a) {
 }
 
 // ---------------------------------------------------------------- finest-level kernels
+// The iterate is kept in correction form f = o + d (d = 0 initially), so the residual
+//     r = b - A f = alpha (s - o) - A d
+// never subtracts the large L o and L f from each other.  In the adjoint (rhs) mode the
+// system is A x = rhs with x = d and o = 0.
 struct TopSlice {
-    int64_t off;   // element offset of the slice in the packed s / o / f / out buffers
+    int64_t off;   // element offset of the slice in the packed s / o / d / out buffers
     int nx, ny;
+    int tiles_x;   // 64 x 16 tiles of the residual kernel
+    int pitch0;    // level-0 row pitch
+    void* u0;      // level-0 iterate of the V-cycle (the correction e)
+    void* b0;      // level-0 right-hand side (the residual r)
 };
 
-template <class TF, class TV, class To>
-__global__ void __launch_bounds__(kBX* kBY)
-k_residual_top(LevelArgs<TV> a, const TopSlice* __restrict__ top, const float* __restrict__ s,
-               const To* __restrict__ o, const float* __restrict__ rhs, const TF* __restrict__ f,
-               double alpha, double* __restrict__ norms) {
+constexpr int kTopTX = 64;
+constexpr int kTopTY = 16;
+
+// MODE 0: d = 0, r = alpha (s - o) (first residual; also accumulates ||b||^2)
+// MODE 1: d = e                    (first correction)
+// MODE 2: d = d + e                (later corrections)
+// Arithmetic on d and r in TF (FP64 when mixed); the FP64 work per cell is the update of d,
+// its 5-point operator and the squared residual.
+template <class TF, class TV, class To, int MODE>
+__global__ void __launch_bounds__(256)
+k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, int nslices,
+      const int* __restrict__ active, const float* __restrict__ s, const To* __restrict__ o,
+      const float* __restrict__ rhs, TF* __restrict__ d, double alpha, double* __restrict__ norms) {
     const int64_t t = blockIdx.x;
-    const int j = find_slice(a.tile_start, a.nsl, t);
-    const LSlice<TV> S = a.sl[j];
-    if (a.active && !a.active[S.slice]) return;
-    const TopSlice G = top[S.slice];
-    const int lt = int(t - a.tile_start[j]);
-    const int x = (lt % S.tiles_x) * kBX + threadIdx.x;
-    const int y = (lt / S.tiles_x) * kBY + threadIdx.y;
+    const int j = find_item(tile_start, nslices, t);
+    if (active && !active[j]) return;
+    const TopSlice G = top[j];
+    const int lt = int(t - tile_start[j]);
+    const int tx0 = (lt % G.tiles_x) * kTopTX;
+    const int ty0 = (lt / G.tiles_x) * kTopTY;
+    const int tid = threadIdx.x;
+    const TV* e = static_cast<const TV*>(G.u0);
+    TV* r0 = static_cast<TV*>(G.b0);
+    __shared__ TF dsm[kTopTY + 2][kTopTX + 2];
+    if (MODE >= 1) {
+        for (int q = tid; q < (kTopTY + 2) * (kTopTX + 2); q += 256) {
+            const int rr = q / (kTopTX + 2), cc = q - rr * (kTopTX + 2);
+            const int gx = tx0 - 1 + cc, gy = ty0 - 1 + rr;
+            TF v = TF(0);
+            if (gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny) {
+                const TF ev = TF(e[(int64_t)gy * G.pitch0 + gx]);
+                v = MODE == 1 ? ev : d[G.off + (int64_t)gy * G.nx + gx] + ev;
+            }
+            dsm[rr][cc] = v;
+        }
+        __syncthreads();
+    }
+    const float af = float(alpha);
+    // alpha + deg for deg = 1..4, selected without indexing (deg 0 only for 1 x 1 slices)
+    const TF ad1 = TF(alpha) + TF(1), ad2 = TF(alpha) + TF(2), ad3 = TF(alpha) + TF(3), ad4 = TF(alpha) + TF(4);
     double rr = 0.0, bb = 0.0;
-    if (x < S.nx && y < S.ny) {
+    const int ly = tid / 16;
+    const int y = ty0 + ly;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int lx = 4 * (tid % 16) + i;
+        const int x = tx0 + lx;
+        if (x >= G.nx || y >= G.ny) continue;
         const int64_t p = G.off + (int64_t)y * G.nx + x;
         const bool hw = x > 0, he = x + 1 < G.nx, hn = y > 0, hs = y + 1 < G.ny;
-        const TF deg = TF(int(hw) + int(he) + int(hn) + int(hs));
-        TF b;
+        float bc;
         if (rhs) {
-            b = TF(rhs[p]);
+            bc = rhs[p];
+            if (MODE == 0) bb = fma(double(bc), double(bc), bb);
         } else {
-            const TF oc = TF(o[p]);
-            TF Lo = deg * oc;
-            if (hw) Lo -= TF(o[p - 1]);
-            if (he) Lo -= TF(o[p + 1]);
-            if (hn) Lo -= TF(o[p - G.nx]);
-            if (hs) Lo -= TF(o[p + G.nx]);
-            b = TF(alpha) * TF(s[p]) + Lo;
+            const float sv = s[p], ov = float(o[p]);
+            bc = af * (sv - ov);
+            if (MODE == 0) {
+                // ||b||^2 with b = alpha s + L o, for the relative-residual denominator
+                float lo = 0.f;
+                if (hw) lo += ov - float(o[p - 1]);
+                if (he) lo += ov - float(o[p + 1]);
+                if (hn) lo += ov - float(o[p - G.nx]);
+                if (hs) lo += ov - float(o[p + G.nx]);
+                const float b = fmaf(af, sv, lo);
+                bb = fma(double(b), double(b), bb);
+            }
         }
-        const TF fc = f[p];
-        TF Lf = deg * fc;
-        if (hw) Lf -= f[p - 1];
-        if (he) Lf -= f[p + 1];
-        if (hn) Lf -= f[p - G.nx];
-        if (hs) Lf -= f[p + G.nx];
-        const TF r = b - (TF(alpha) * fc + Lf);
-        const int64_t q = (int64_t)y * S.pitch + x;
-        S.b[q] = TV(r);
-        S.u[q] = TV(0);
-        rr = double(r) * double(r);
-        bb = double(b) * double(b);
+        TF r;
+        if (MODE == 0) {
+            r = TF(bc);
+        } else {
+            const TF c = dsm[ly + 1][lx + 1];
+            const TF nsum = (dsm[ly + 1][lx] + dsm[ly + 1][lx + 2]) + (dsm[ly][lx + 1] + dsm[ly + 2][lx + 1]);
+            const int deg = int(hw) + int(he) + int(hn) + int(hs);
+            const TF adeg = deg == 4 ? ad4 : (deg == 3 ? ad3 : (deg == 2 ? ad2 : (deg == 1 ? ad1 : TF(alpha))));
+            const TF Ad = fma_t(adeg, c, -nsum);
+            r = TF(bc) - Ad;
+            d[p] = c;
+        }
+        r0[(int64_t)y * G.pitch0 + x] = TV(r);
+        const double rd = double(r);
+        rr = fma(rd, rd, rr);
     }
-    // block reduction in FP64: warp shuffles, then one atomic pair per block
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) {
         rr += __shfl_xor_sync(0xffffffffu, rr, m);
-        bb += __shfl_xor_sync(0xffffffffu, bb, m);
+        if (MODE == 0) bb += __shfl_xor_sync(0xffffffffu, bb, m);
     }
-    __shared__ double red[2][kBY];
-    if (threadIdx.x == 0) { red[0][threadIdx.y] = rr; red[1][threadIdx.y] = bb; }
+    __shared__ double red[2][8];
+    if ((tid & 31) == 0) { red[0][tid >> 5] = rr; red[1][tid >> 5] = bb; }
     __syncthreads();
-    if (threadIdx.y == 0 && threadIdx.x == 0) {
+    if (tid == 0) {
         double r2 = 0.0, b2 = 0.0;
-        for (int w = 0; w < kBY; ++w) { r2 += red[0][w]; b2 += red[1][w]; }
-        atomicAdd(&norms[2 * S.slice], r2);
-        atomicAdd(&norms[2 * S.slice + 1], b2);
+        for (int w = 0; w < 8; ++w) { r2 += red[0][w]; b2 += red[1][w]; }
+        atomicAdd(&norms[2 * j], r2);
+        if (MODE == 0) atomicAdd(&norms[2 * j + 1], b2);
     }
 }
 
-template <class TF, class TV>
-__global__ void __launch_bounds__(kBX* kBY)
-k_update_top(LevelArgs<TV> a, const TopSlice* __restrict__ top, TF* __restrict__ f) {
-    const int64_t t = blockIdx.x;
-    const int j = find_slice(a.tile_start, a.nsl, t);
-    const LSlice<TV> S = a.sl[j];
-    if (a.active && !a.active[S.slice]) return;
-    const TopSlice G = top[S.slice];
-    const int lt = int(t - a.tile_start[j]);
-    const int x = (lt % S.tiles_x) * kBX + threadIdx.x;
-    const int y = (lt / S.tiles_x) * kBY + threadIdx.y;
-    if (x >= S.nx || y >= S.ny) return;
-    f[G.off + (int64_t)y * G.nx + x] += TF(S.u[(int64_t)y * S.pitch + x]);
-}
-
-template <class TF, class To>
-__global__ void k_init_f(TF* __restrict__ f, const To* __restrict__ o, int64_t n, int zero) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        f[i] = zero ? TF(0) : TF(o[i]);
-}
-
-__global__ void k_store(const double* __restrict__ f, float* __restrict__ out, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = float(f[i]);
+// out = o + d (or d in the adjoint mode), one pass over the packed slices.
+template <class TF, class To, bool FULL64>
+__global__ void k_store(const TF* __restrict__ d, const To* __restrict__ o, float* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (!o) out[i] = float(d[i]);
+        else if (FULL64) out[i] = float(double(o[i]) + double(d[i]));
+        else out[i] = float(o[i]) + float(d[i]);
+    }
 }
 
 inline unsigned grid_for(int64_t n, int threads) {
@@ -227,13 +251,20 @@ inline unsigned grid_for(int64_t n, int threads) {
 // ---------------------------------------------------------------- host-side plan
 template <class T>
 struct LevelPlan {
-    std::vector<LSlice<T>> sl;
-    std::vector<int64_t> tile_start;   // size nsl + 1
+    std::vector<LSlice<T>> sl;          // every slice that has this level
+    std::vector<int64_t> tile_start;    // reference-kernel tiles, prefix sums (nsl + 1)
+    std::vector<LSlice<T>> wsl;         // slices that run the wavefront kernels here
+    std::vector<int64_t> item_start;    // wavefront work items, prefix sums
     LSlice<T>* d_sl = nullptr;
     int64_t* d_ts = nullptr;
+    LSlice<T>* d_wsl = nullptr;
+    int64_t* d_is = nullptr;
     int k = 0;
-    double cells = 0;   // cells of this level summed over its slices
+    int ch = 64;                        // wavefront rows per work item
+    double cells = 0;                   // cells of this level summed over its slices
+    double wcells = 0;                  // ... over the wavefront slices
     int64_t ntiles() const { return tile_start.empty() ? 0 : tile_start.back(); }
+    int64_t nitems() const { return item_start.empty() ? 0 : item_start.back(); }
 };
 
 inline int num_levels(int64_t nx, int64_t ny) {
@@ -242,27 +273,53 @@ inline int num_levels(int64_t nx, int64_t ny) {
     return K + 1;
 }
 
+// Small descriptor uploads: packs host vectors into one device blob.
+struct Blob {
+    std::vector<char> host;
+    template <class V>
+    size_t add(const std::vector<V>& v) {
+        const size_t pos = host.size();
+        host.resize(pos + round_up(std::max<size_t>(1, v.size() * sizeof(V)), 256));
+        if (!v.empty()) std::memcpy(host.data() + pos, v.data(), v.size() * sizeof(V));
+        return pos;
+    }
+};
+
 template <class TF, class TV>
 struct Solver {
     const SolveRequest& req;
     cudaStream_t st;
     std::vector<LevelPlan<TV>> levels;
-    DeviceBuffer ws_levels, ws_desc, ws_f, ws_norms, ws_active, ws_top;
-    std::vector<int> nlev;
-    int Kmax = 0;
-    TF* f = nullptr;
+    DeviceBuffer ws_levels, ws_desc, ws_f, ws_norms, ws_active;
+    std::vector<int> nlev, kc;
+    int Kmax = 0, Kw = 0;       // levels, and levels with wavefront work
+    TF* d = nullptr;
     double* d_norms = nullptr;
     int* d_active = nullptr;
     TopSlice* d_top = nullptr;
+    int64_t* d_top_ts = nullptr;
+    int64_t top_tiles = 0;
+    double top_cells = 0;
+    TailArgs<TV> tail{};
+    double tail_cells = 0;
+    bool fused = true;
 
     Solver(const SolveRequest& r, cudaStream_t s) : req(r), st(s) {}
 
+    static bool wave_ok(int nu) { return nu == 1 || nu == 2 || (nu == 3 && sizeof(TV) == 4); }
+
     int build() {
         const int64_t n = req.nslices;
+        fused = req.opts.fused != 0 && wave_ok(req.opts.nu_pre) && wave_ok(req.opts.nu_post);
         nlev.resize(n);
+        kc.resize(n);
         for (int64_t j = 0; j < n; ++j) {
             nlev[j] = num_levels(req.nx[j], req.ny[j]);
             Kmax = std::max(Kmax, nlev[j]);
+            int k = 0;  // first level small enough for the coarse tail
+            while (std::max(level_size((int)req.nx[j], k), level_size((int)req.ny[j], k)) > kTailMax) ++k;
+            kc[j] = fused ? k : nlev[j];
+            Kw = std::max(Kw, kc[j]);
         }
         // level arrays: u and b of every slice and level, rows padded to 128 bytes
         const int64_t align = 128 / (int64_t)sizeof(TV);
@@ -278,68 +335,119 @@ struct Solver {
         }
         EMF_TRY(ws_levels.alloc((size_t)total * sizeof(TV), st));
         TV* base = ws_levels.as<TV>();
+        auto make = [&](int64_t j, int k) {
+            LSlice<TV> S{};
+            const int n0x = (int)req.nx[j], n0y = (int)req.ny[j];
+            S.nx = level_size(n0x, k);
+            S.ny = level_size(n0y, k);
+            S.pitch = (int)round_up(S.nx, align);
+            S.u = base + off[j][k];
+            S.b = S.u + (int64_t)S.pitch * S.ny;
+            if (k + 1 < nlev[j]) {
+                S.ncx = level_size(n0x, k + 1);
+                S.ncy = level_size(n0y, k + 1);
+                S.pitchc = (int)round_up(S.ncx, align);
+                S.uc = base + off[j][k + 1];
+                S.bc = S.uc + (int64_t)S.pitchc * S.ncy;
+            }
+            if (k > 0) {
+                S.nfx = level_size(n0x, k - 1);
+                S.nfy = level_size(n0y, k - 1);
+                S.pitchf = (int)round_up(S.nfx, align);
+                S.uf = base + off[j][k - 1];
+                S.bf = S.uf + (int64_t)S.pitchf * S.nfy;
+            }
+            S.n0x = n0x;
+            S.n0y = n0y;
+            S.slice = (int)j;
+            S.tiles_x = (int)ceil_div(S.nx, kBX);
+            S.fstrips = (int)ceil_div(S.nx, kWaveIW);
+            return S;
+        };
         levels.resize(Kmax);
+        std::vector<LSlice<TV>> table;
+        std::vector<int> level_off(n);
+        for (int64_t j = 0; j < n; ++j) {
+            level_off[j] = (int)table.size();
+            for (int k = 0; k < nlev[j]; ++k) table.push_back(make(j, k));
+        }
         for (int k = 0; k < Kmax; ++k) {
             LevelPlan<TV>& L = levels[k];
             L.k = k;
             L.tile_start.push_back(0);
+            L.item_start.push_back(0);
+            int64_t want = 0;
             for (int64_t j = 0; j < n; ++j) {
                 if (nlev[j] <= k) continue;
-                LSlice<TV> S{};
-                const int n0x = (int)req.nx[j], n0y = (int)req.ny[j];
-                S.nx = level_size(n0x, k);
-                S.ny = level_size(n0y, k);
-                S.pitch = (int)round_up(S.nx, align);
-                S.u = base + off[j][k];
-                S.b = S.u + (int64_t)S.pitch * S.ny;
-                if (k + 1 < nlev[j]) {
-                    S.ncx = level_size(n0x, k + 1);
-                    S.ncy = level_size(n0y, k + 1);
-                    S.pitchc = (int)round_up(S.ncx, align);
-                    S.uc = base + off[j][k + 1];
-                }
-                if (k > 0) {
-                    S.nfx = level_size(n0x, k - 1);
-                    S.nfy = level_size(n0y, k - 1);
-                    S.pitchf = (int)round_up(S.nfx, align);
-                    S.uf = base + off[j][k - 1];
-                    S.bf = S.uf + (int64_t)S.pitchf * S.nfy;
-                }
-                S.n0x = n0x;
-                S.n0y = n0y;
-                S.slice = (int)j;
-                S.tiles_x = (int)ceil_div(S.nx, kBX);
-                const int64_t tiles = (int64_t)S.tiles_x * ceil_div(S.ny, kBY);
+                const LSlice<TV> S = make(j, k);
                 L.sl.push_back(S);
-                L.tile_start.push_back(L.tile_start.back() + tiles);
+                L.tile_start.push_back(L.tile_start.back() + (int64_t)S.tiles_x * ceil_div(S.ny, kBY));
                 L.cells += (double)S.nx * S.ny;
+                if (k < kc[j]) {
+                    L.wsl.push_back(S);
+                    L.wcells += (double)S.nx * S.ny;
+                    want += (int64_t)S.fstrips * S.ny;
+                }
             }
+            // rows per work item: as tall as possible while keeping ~4 waves of warps
+            L.ch = 128;
+            while (L.ch > 16 && want / L.ch < (int64_t)kNumSMs * 16 * 4) L.ch /= 2;
+            for (const auto& S : L.wsl)
+                L.item_start.push_back(L.item_start.back() + (int64_t)S.fstrips * ceil_div(S.ny, L.ch));
         }
-        // descriptors: one upload of all levels
-        size_t bytes = 0;
-        for (auto& L : levels) bytes += round_up(L.sl.size() * sizeof(LSlice<TV>), 256) + round_up(L.tile_start.size() * 8, 256);
-        std::vector<char> blob(bytes);
-        EMF_TRY(ws_desc.alloc(bytes, st));
-        size_t pos = 0;
-        for (auto& L : levels) {
-            std::memcpy(blob.data() + pos, L.sl.data(), L.sl.size() * sizeof(LSlice<TV>));
-            L.d_sl = reinterpret_cast<LSlice<TV>*>(ws_desc.as<char>() + pos);
-            pos += round_up(L.sl.size() * sizeof(LSlice<TV>), 256);
-            std::memcpy(blob.data() + pos, L.tile_start.data(), L.tile_start.size() * 8);
-            L.d_ts = reinterpret_cast<int64_t*>(ws_desc.as<char>() + pos);
-            pos += round_up(L.tile_start.size() * 8, 256);
-        }
-        EMF_CUDA(cudaMemcpyAsync(ws_desc.as<char>(), blob.data(), bytes, cudaMemcpyHostToDevice, st));
+        // finest-level (residual kernel) tiling
         std::vector<TopSlice> top(n);
-        for (int64_t j = 0; j < n; ++j) top[j] = TopSlice{req.offsets[j], (int)req.nx[j], (int)req.ny[j]};
-        EMF_TRY(ws_top.alloc(n * sizeof(TopSlice), st));
-        EMF_CUDA(cudaMemcpyAsync(ws_top.as<TopSlice>(), top.data(), n * sizeof(TopSlice), cudaMemcpyHostToDevice, st));
-        d_top = ws_top.as<TopSlice>();
+        std::vector<int64_t> top_ts(n + 1, 0);
+        for (int64_t j = 0; j < n; ++j) {
+            const LSlice<TV> S0 = table[level_off[j]];
+            top[j] = TopSlice{req.offsets[j], (int)req.nx[j], (int)req.ny[j],
+                              (int)ceil_div(req.nx[j], kTopTX), S0.pitch, S0.u, S0.b};
+            top_ts[j + 1] = top_ts[j] + (int64_t)top[j].tiles_x * ceil_div(req.ny[j], kTopTY);
+            top_cells += (double)req.nx[j] * req.ny[j];
+        }
+        top_tiles = top_ts[n];
+        std::vector<int> vkc(kc), vnlev(nlev);
+        for (int64_t j = 0; j < n; ++j)
+            for (int k = kc[j]; k < nlev[j]; ++k) {
+                const auto& S = table[level_off[j] + k];
+                tail_cells += (double)S.nx * S.ny;
+            }
+        Blob blob;
+        std::vector<size_t> pos_sl(Kmax), pos_ts(Kmax), pos_wsl(Kmax), pos_is(Kmax);
+        for (int k = 0; k < Kmax; ++k) {
+            pos_sl[k] = blob.add(levels[k].sl);
+            pos_ts[k] = blob.add(levels[k].tile_start);
+            pos_wsl[k] = blob.add(levels[k].wsl);
+            pos_is[k] = blob.add(levels[k].item_start);
+        }
+        const size_t pos_top = blob.add(top), pos_top_ts = blob.add(top_ts);
+        const size_t pos_table = blob.add(table), pos_loff = blob.add(level_off);
+        const size_t pos_nlev = blob.add(vnlev), pos_kc = blob.add(vkc);
+        EMF_TRY(ws_desc.alloc(blob.host.size(), st));
+        char* dbase = ws_desc.as<char>();
+        EMF_CUDA(cudaMemcpyAsync(dbase, blob.host.data(), blob.host.size(), cudaMemcpyHostToDevice, st));
+        for (int k = 0; k < Kmax; ++k) {
+            levels[k].d_sl = reinterpret_cast<LSlice<TV>*>(dbase + pos_sl[k]);
+            levels[k].d_ts = reinterpret_cast<int64_t*>(dbase + pos_ts[k]);
+            levels[k].d_wsl = reinterpret_cast<LSlice<TV>*>(dbase + pos_wsl[k]);
+            levels[k].d_is = reinterpret_cast<int64_t*>(dbase + pos_is[k]);
+        }
+        d_top = reinterpret_cast<TopSlice*>(dbase + pos_top);
+        d_top_ts = reinterpret_cast<int64_t*>(dbase + pos_top_ts);
         EMF_TRY(ws_norms.alloc(2 * n * sizeof(double), st));
         d_norms = ws_norms.as<double>();
         EMF_TRY(ws_active.alloc(n * sizeof(int), st));
         d_active = ws_active.as<int>();
-        EMF_CUDA(cudaStreamSynchronize(st));  // host staging vectors go out of scope
+        tail.table = reinterpret_cast<const LSlice<TV>*>(dbase + pos_table);
+        tail.level_off = reinterpret_cast<const int*>(dbase + pos_loff);
+        tail.nlev = reinterpret_cast<const int*>(dbase + pos_nlev);
+        tail.kc = reinterpret_cast<const int*>(dbase + pos_kc);
+        tail.nslices = (int)n;
+        tail.alpha = TV(req.alpha);
+        tail.nu_pre = req.opts.nu_pre;
+        tail.nu_post = req.opts.nu_post;
+        tail.active = d_active;
+        EMF_CUDA(cudaStreamSynchronize(st));  // the host staging blob goes out of scope
         return EMFUSE_OK;
     }
 
@@ -349,6 +457,20 @@ struct Solver {
         a.tile_start = levels[k].d_ts;
         a.nsl = (int)levels[k].sl.size();
         a.k = k;
+        a.alpha = TV(req.alpha);
+        a.sk = TV(std::ldexp(1.0, -2 * k));
+        a.active = d_active;
+        return a;
+    }
+
+    WaveArgs<TV> wargs(int k) const {
+        WaveArgs<TV> a;
+        a.sl = levels[k].d_wsl;
+        a.item_start = levels[k].d_is;
+        a.nsl = (int)levels[k].wsl.size();
+        a.nitems = levels[k].nitems();
+        a.k = k;
+        a.ch = levels[k].ch;
         a.alpha = TV(req.alpha);
         a.sk = TV(std::ldexp(1.0, -2 * k));
         a.active = d_active;
@@ -369,8 +491,12 @@ struct Solver {
         return EMFUSE_OK;
     }
 
-    int vcycle() {
+    // Reference schedule: one kernel per half-sweep, restriction and prolongation.
+    int vcycle_reference() {
         const int nu1 = req.opts.nu_pre, nu2 = req.opts.nu_post;
+        // level-0 iterate starts at zero
+        for (const auto& S : levels[0].sl)
+            EMF_CUDA(cudaMemsetAsync(S.u, 0, (size_t)S.pitch * S.ny * sizeof(TV), st));
         for (int k = 0; k < Kmax; ++k) {
             EMF_TRY(relax(k, nu1));
             if (k + 1 < Kmax) {
@@ -394,6 +520,37 @@ struct Solver {
         return EMFUSE_OK;
     }
 
+    // Fused schedule: wavefront DOWN on large levels, one coarse-tail kernel, wavefront UP.
+    int vcycle_fused() {
+        const int S1 = 2 * req.opts.nu_pre, S2 = 2 * req.opts.nu_post;
+        for (int k = 0; k < Kw; ++k) {
+            const auto& L = levels[k];
+            // reads b, writes u and the coarse rhs
+            const double bytes = sizeof(TV) * (2.0 * L.wcells + 0.25 * L.wcells);
+            EMF_TRY(launch_wave<TV>(wargs(k), S1, true, false, st, bytes));
+        }
+        EMF_TRY(launch_tail<TV>(tail, st, sizeof(TV) * 2.0 * tail_cells));
+        for (int k = Kw - 1; k >= 0; --k) {
+            const auto& L = levels[k];
+            // reads u, b and the coarse iterate, writes u
+            const double bytes = sizeof(TV) * (3.0 * L.wcells + 0.25 * L.wcells);
+            EMF_TRY(launch_wave<TV>(wargs(k), S2, false, true, st, bytes));
+        }
+        return EMFUSE_OK;
+    }
+
+    template <class To, int MODE>
+    int top_pass(const To* o) {
+        const double in_b = req.rhs ? 4.0 : 4.0 + sizeof(To) + (MODE == 0 ? 0.0 : 0.0);
+        const double bytes = top_cells * (in_b + sizeof(TV) + (MODE == 0 ? 0.0 : sizeof(TV) + sizeof(TF)) +
+                                          (MODE == 2 ? sizeof(TF) : 0.0));
+        KernelScope ks(MODE == 0 ? "residual_first" : "residual_update", st, bytes);
+        k_top<TF, TV, To, MODE><<<(unsigned)top_tiles, 256, 0, st>>>(
+            d_top, d_top_ts, (int)req.nslices, d_active, req.s, o, req.rhs, d, req.alpha, d_norms);
+        EMF_CHECK_LAUNCH();
+        return EMFUSE_OK;
+    }
+
     template <class To>
     int run(const To* o) {
         EMF_TRY(build());
@@ -401,40 +558,33 @@ struct Solver {
         int64_t total = 0;
         for (int64_t j = 0; j < n; ++j) total = std::max(total, req.offsets[j] + req.nx[j] * req.ny[j]);
         if (std::is_same<TF, float>::value) {
-            f = reinterpret_cast<TF*>(req.out);
+            d = reinterpret_cast<TF*>(req.out);  // the correction lives in the output buffer
         } else {
             EMF_TRY(ws_f.alloc((size_t)total * sizeof(TF), st));
-            f = ws_f.as<TF>();
+            d = ws_f.as<TF>();
         }
-        {
-            KernelScope ks("init_iterate", st, (double)total * (sizeof(TF) + (req.rhs ? 0 : sizeof(To))));
-            k_init_f<TF, To><<<grid_for(total, 256), 256, 0, st>>>(f, o, total, req.rhs ? 1 : 0);
-            EMF_CHECK_LAUNCH();
-        }
-
         std::vector<int> active(n, 1), vcycles(n, 0);
         std::vector<double> norms(2 * n), rel(n, 0.0), bnorm(n, 0.0);
         std::vector<char> done(n, 0);
         EMF_CUDA(cudaMemcpyAsync(d_active, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+        EMF_CUDA(cudaMemsetAsync(d_norms, 0, 2 * n * sizeof(double), st));
         const int maxit = std::max(0, req.opts.max_vcycles);
         bool all_done = false;
+        int rc = EMFUSE_OK;
         for (int it = 0;; ++it) {
-            EMF_CUDA(cudaMemsetAsync(d_norms, 0, 2 * n * sizeof(double), st));
-            {
-                const double in_b = req.rhs ? 4.0 : 4.0 + sizeof(To);
-                KernelScope ks("residual_top", st, levels[0].cells * (in_b + sizeof(TF) + 2.0 * sizeof(TV)));
-                k_residual_top<TF, TV, To><<<(unsigned)levels[0].ntiles(), dim3(kBX, kBY), 0, st>>>(
-                    args(0), d_top, req.s, o, req.rhs, f, req.alpha, d_norms);
-                EMF_CHECK_LAUNCH();
-            }
+            if (it > 0) EMF_CUDA(cudaMemsetAsync(d_norms, 0, n * 2 * sizeof(double), st));
+            if (it == 0) rc = top_pass<To, 0>(o);
+            else if (it == 1) rc = top_pass<To, 1>(o);
+            else rc = top_pass<To, 2>(o);
+            if (rc != EMFUSE_OK) return rc;
             EMF_CUDA(cudaMemcpyAsync(norms.data(), d_norms, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
             EMF_CUDA(cudaStreamSynchronize(st));
             all_done = true;
             for (int64_t j = 0; j < n; ++j) {
                 if (done[j]) continue;
-                const double rr = norms[2 * j], bb = norms[2 * j + 1];
-                bnorm[j] = std::sqrt(bb);
-                rel[j] = bb > 0 ? std::sqrt(rr / bb) : std::sqrt(rr);
+                if (it == 0) bnorm[j] = std::sqrt(norms[2 * j + 1]);
+                const double rr = norms[2 * j];
+                rel[j] = bnorm[j] > 0 ? std::sqrt(rr) / bnorm[j] : std::sqrt(rr);
                 if (rel[j] <= req.opts.tol || !std::isfinite(rel[j])) {
                     done[j] = 1;
                     active[j] = 0;
@@ -444,18 +594,24 @@ struct Solver {
             }
             if (all_done || it >= maxit) break;
             EMF_CUDA(cudaMemcpyAsync(d_active, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
-            EMF_TRY(vcycle());
-            {
-                KernelScope ks("update_top", st, levels[0].cells * (2.0 * sizeof(TF) + sizeof(TV)));
-                k_update_top<TF, TV><<<(unsigned)levels[0].ntiles(), dim3(kBX, kBY), 0, st>>>(args(0), d_top, f);
-                EMF_CHECK_LAUNCH();
-            }
+            EMF_TRY(fused ? vcycle_fused() : vcycle_reference());
             for (int64_t j = 0; j < n; ++j)
                 if (active[j]) ++vcycles[j];
         }
-        if (!std::is_same<TF, float>::value) {
-            KernelScope ks("store_output", st, (double)total * 12.0);
-            k_store<<<grid_for(total, 256), 256, 0, st>>>(reinterpret_cast<const double*>(f), req.out, total);
+        // Slices that converged at the first residual kept d = 0; the others hold d in the
+        // d buffer, except in MODE 1/2 only active slices were written.  Slices done at it == 0
+        // never had d written: clear them before the store.
+        std::vector<char> never(n, 0);
+        for (int64_t j = 0; j < n; ++j) never[j] = vcycles[j] == 0;
+        for (int64_t j = 0; j < n; ++j)
+            if (never[j]) EMF_CUDA(cudaMemsetAsync(d + req.offsets[j], 0, (size_t)(req.nx[j] * req.ny[j]) * sizeof(TF), st));
+        {
+            KernelScope ks("store_output", st, (double)total * (sizeof(TF) + (req.rhs ? 0 : sizeof(To)) + 4.0));
+            const To* oo = req.rhs ? nullptr : o;
+            if (std::is_same<TV, double>::value)
+                k_store<TF, To, true><<<grid_for(total, 256), 256, 0, st>>>(d, oo, req.out, total);
+            else
+                k_store<TF, To, false><<<grid_for(total, 256), 256, 0, st>>>(d, oo, req.out, total);
             EMF_CHECK_LAUNCH();
         }
         bool nonfinite = false;

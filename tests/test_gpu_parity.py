@@ -93,11 +93,13 @@ def test_solve_odd_sizes(dev, shape, alpha):
     rng = np.random.default_rng(shape[0] * 1000 + shape[1])
     s = rng.uniform(0, 255, size=shape).astype(np.float32)
     o = (0.9 * s + rng.normal(0, 10, size=shape)).astype(np.float32)
+    # White-noise inputs make ||b|| large relative to the smooth error modes (kappa(A) = 1 + 8 /
+    # alpha), so the error bar needs a tighter residual than 1e-6 here; the mixed path gets it.
     f, stats = api.emfuse_screened_poisson(torch.from_numpy(s).to(dev), torch.from_numpy(o).to(dev),
-                                           alpha, return_stats=True)
+                                           alpha, api.default_opts(tol=1e-10), return_stats=True)
     ref = O.solve_dct(s, o, alpha)
     assert maxdiff(f.cpu().numpy(), ref) <= SOLVE_TOL
-    assert stats[0]["rel_residual"] <= 1e-6
+    assert stats[0]["rel_residual"] <= 1e-10
 
 
 def test_solve_ragged_batch(dev):
