@@ -16,7 +16,9 @@
 //        of residual pairs written as the next level's right-hand side.  One read of b
 //        (and u), one write of u and of the coarse rhs per cell.
 //   UP   (prolongation leg): the interpolated coarse correction is added as each row
-//        arrives, then S half-sweeps; one read of u, b and the coarse iterate, one write of u.
+//        arrives, then S half-sweeps; one read of u, b and the coarse iterate, one write of
+//        the result into a second buffer (uo): the warps read u on their halos, so no warp may
+//        overwrite it in place.
 //
 // Coarse tail (k_tail).  Levels whose larger side is <= 64 are run by one CTA per slice: the
 // remaining down and up legs of the V-cycle with __syncthreads() between half-sweeps, on
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     if (UP) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            if (L.uc) interp_axis<T>(xlane + i, L.n0x, k, L.ncx, cI[i], cJ[i], cw[i]);
+            if (L.uco) interp_axis<T>(xlane + i, L.n0x, k, L.ncx, cI[i], cJ[i], cw[i]);
             else { cI[i] = cJ[i] = 0; cw[i] = T(0); }
         }
     }
@@ -173,15 +175,15 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     auto fetch = [&](int t, T (&uu)[4], T (&bb)[4], T (&cc)[4], int& ok) {
         load_row<T, (UP ? false : ZERO)>(L, t, xlane, lane_in, uu, bb);
         ok = 0;
-        if (UP && L.uc && t >= 0 && t < L.ny) {
+        if (UP && L.uco && t >= 0 && t < L.ny) {
             int Iy, Jy;
             T wy;
             interp_axis<T>(t, L.n0y, k, L.ncy, Iy, Jy, wy);
             const bool cin = cx0 >= 0 && cx0 < L.ncx;
             cc[0] = cc[1] = cc[2] = cc[3] = T(0);
             if (cin) {
-                Vec2<T>::load(L.uc + (int64_t)Iy * L.pitchc + cx0, cc[0], cc[1]);
-                Vec2<T>::load(L.uc + (int64_t)Jy * L.pitchc + cx0, cc[2], cc[3]);
+                Vec2<T>::load(L.uco + (int64_t)Iy * L.pitchc + cx0, cc[0], cc[1]);
+                Vec2<T>::load(L.uco + (int64_t)Jy * L.pitchc + cx0, cc[2], cc[3]);
             }
             ok = 1;
         }
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                 const int r = t - S;
                 const int so = wmod(q - S, W);
                 if (r >= Y0 && r < Y1 && interior_lane && lane_in) {
-                    T* dst = L.u + (int64_t)r * L.pitch + xlane;
+                    T* dst = (UP ? L.uo : L.u) + (int64_t)r * L.pitch + xlane;
                     if (xlane + 3 < L.nx) {
                         Vec4<T>::store(dst, u[so]);
                     } else {

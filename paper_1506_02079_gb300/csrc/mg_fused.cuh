@@ -23,8 +23,12 @@ struct LSlice {
     T* u;              // iterate, `pitch` elements per row
     T* b;              // right-hand side
     int nx, ny, pitch;
+    T* uo;             // where the final (post-smoothed) iterate of this level goes: a second
+                       // buffer on wavefront levels, whose UP kernel reads u on halos that
+                       // other warps would otherwise overwrite; u itself elsewhere
     T* uc;             // level k+1 iterate and rhs (null at the coarsest level of this slice)
     T* bc;
+    T* uco;            // level k+1 final iterate (its uo)
     int ncx, ncy, pitchc;
     T* uf;             // level k-1 iterate and rhs (null at k = 0)
     T* bf;

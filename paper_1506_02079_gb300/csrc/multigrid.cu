@@ -138,10 +138,11 @@ constexpr int kTopTX = 64;
 constexpr int kTopTY = 16;
 
 // MODE 0: d = 0, r = alpha (s - o) (first residual; also accumulates ||b||^2)
-// MODE 1: d = e                    (first correction)
-// MODE 2: d = d + e                (later corrections)
-// Arithmetic on d and r in TF (FP64 when mixed); the FP64 work per cell is the update of d,
-// its 5-point operator and the squared residual.
+// MODE 1: d = e, written back       (first correction)
+// MODE 2: d read only               (later corrections: k_update has added e to d)
+// Tiles read d on a one-cell halo, so d is never written by a kernel that reads it on a
+// halo (MODE 1 reads e and writes d).  Arithmetic on d and r in TF (FP64 when mixed); the
+// FP64 work per cell is the 5-point operator on d and the squared residual.
 template <class TF, class TV, class To, int MODE>
 __global__ void __launch_bounds__(256)
 k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, int nslices,
@@ -163,10 +164,8 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
             const int rr = q / (kTopTX + 2), cc = q - rr * (kTopTX + 2);
             const int gx = tx0 - 1 + cc, gy = ty0 - 1 + rr;
             TF v = TF(0);
-            if (gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny) {
-                const TF ev = TF(e[(int64_t)gy * G.pitch0 + gx]);
-                v = MODE == 1 ? ev : d[G.off + (int64_t)gy * G.nx + gx] + ev;
-            }
+            if (gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny)
+                v = MODE == 1 ? TF(e[(int64_t)gy * G.pitch0 + gx]) : d[G.off + (int64_t)gy * G.nx + gx];
             dsm[rr][cc] = v;
         }
         __syncthreads();
@@ -212,7 +211,7 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
             const TF adeg = deg == 4 ? ad4 : (deg == 3 ? ad3 : (deg == 2 ? ad2 : (deg == 1 ? ad1 : TF(alpha))));
             const TF Ad = fma_t(adeg, c, -nsum);
             r = TF(bc) - Ad;
-            d[p] = c;
+            if (MODE == 1) d[p] = c;
         }
         r0[(int64_t)y * G.pitch0 + x] = TV(r);
         const double rd = double(r);
@@ -231,6 +230,30 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
         for (int w = 0; w < 8; ++w) { r2 += red[0][w]; b2 += red[1][w]; }
         atomicAdd(&norms[2 * j], r2);
         if (MODE == 0) atomicAdd(&norms[2 * j + 1], b2);
+    }
+}
+
+// d += e on every cell of the active slices (elementwise; the residual kernel then reads d).
+template <class TF, class TV>
+__global__ void __launch_bounds__(256)
+k_update(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, int nslices,
+         const int* __restrict__ active, TF* __restrict__ d) {
+    const int64_t t = blockIdx.x;
+    const int j = find_item(tile_start, nslices, t);
+    if (active && !active[j]) return;
+    const TopSlice G = top[j];
+    const int lt = int(t - tile_start[j]);
+    const int tx0 = (lt % G.tiles_x) * kTopTX;
+    const int ty0 = (lt / G.tiles_x) * kTopTY;
+    const TV* e = static_cast<const TV*>(G.u0);
+    const int y = ty0 + threadIdx.x / 16;
+    if (y >= G.ny) return;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int x = tx0 + 4 * (threadIdx.x % 16) + i;
+        if (x >= G.nx) continue;
+        const int64_t p = G.off + (int64_t)y * G.nx + x;
+        d[p] = d[p] + TF(e[(int64_t)y * G.pitch0 + x]);
     }
 }
 
@@ -321,6 +344,8 @@ struct Solver {
             kc[j] = fused ? k : nlev[j];
             Kw = std::max(Kw, kc[j]);
         }
+        // levels run by the wavefront kernels (the others by the coarse tail / reference)
+        auto wave = [&](int64_t j, int k) { return fused && k < kc[j]; };
         // level arrays: u and b of every slice and level, rows padded to 128 bytes
         const int64_t align = 128 / (int64_t)sizeof(TV);
         std::vector<std::vector<int64_t>> off(n);
@@ -330,7 +355,8 @@ struct Solver {
             for (int k = 0; k < nlev[j]; ++k) {
                 const int64_t lx = level_size((int)req.nx[j], k), ly = level_size((int)req.ny[j], k);
                 off[j][k] = total;
-                total += 2 * round_up(lx, align) * ly;
+                // u, b, and on wavefront levels the output iterate uo
+                total += (wave(j, k) ? 3 : 2) * round_up(lx, align) * ly;
             }
         }
         EMF_TRY(ws_levels.alloc((size_t)total * sizeof(TV), st));
@@ -343,12 +369,14 @@ struct Solver {
             S.pitch = (int)round_up(S.nx, align);
             S.u = base + off[j][k];
             S.b = S.u + (int64_t)S.pitch * S.ny;
+            S.uo = wave(j, k) ? S.b + (int64_t)S.pitch * S.ny : S.u;
             if (k + 1 < nlev[j]) {
                 S.ncx = level_size(n0x, k + 1);
                 S.ncy = level_size(n0y, k + 1);
                 S.pitchc = (int)round_up(S.ncx, align);
                 S.uc = base + off[j][k + 1];
                 S.bc = S.uc + (int64_t)S.pitchc * S.ncy;
+                S.uco = wave(j, k + 1) ? S.bc + (int64_t)S.pitchc * S.ncy : S.uc;
             }
             if (k > 0) {
                 S.nfx = level_size(n0x, k - 1);
@@ -383,7 +411,7 @@ struct Solver {
                 L.sl.push_back(S);
                 L.tile_start.push_back(L.tile_start.back() + (int64_t)S.tiles_x * ceil_div(S.ny, kBY));
                 L.cells += (double)S.nx * S.ny;
-                if (k < kc[j]) {
+                if (wave(j, k)) {
                     L.wsl.push_back(S);
                     L.wcells += (double)S.nx * S.ny;
                     want += (int64_t)S.fstrips * S.ny;
@@ -401,7 +429,7 @@ struct Solver {
         for (int64_t j = 0; j < n; ++j) {
             const LSlice<TV> S0 = table[level_off[j]];
             top[j] = TopSlice{req.offsets[j], (int)req.nx[j], (int)req.ny[j],
-                              (int)ceil_div(req.nx[j], kTopTX), S0.pitch, S0.u, S0.b};
+                              (int)ceil_div(req.nx[j], kTopTX), S0.pitch, S0.uo, S0.b};
             top_ts[j + 1] = top_ts[j] + (int64_t)top[j].tiles_x * ceil_div(req.ny[j], kTopTY);
             top_cells += (double)req.nx[j] * req.ny[j];
         }
@@ -541,9 +569,14 @@ struct Solver {
 
     template <class To, int MODE>
     int top_pass(const To* o) {
-        const double in_b = req.rhs ? 4.0 : 4.0 + sizeof(To) + (MODE == 0 ? 0.0 : 0.0);
-        const double bytes = top_cells * (in_b + sizeof(TV) + (MODE == 0 ? 0.0 : sizeof(TV) + sizeof(TF)) +
-                                          (MODE == 2 ? sizeof(TF) : 0.0));
+        if (MODE == 2) {
+            KernelScope ks("update_iterate", st, top_cells * (2.0 * sizeof(TF) + sizeof(TV)));
+            k_update<TF, TV><<<(unsigned)top_tiles, 256, 0, st>>>(d_top, d_top_ts, (int)req.nslices, d_active, d);
+            EMF_CHECK_LAUNCH();
+        }
+        const double in_b = req.rhs ? 4.0 : 4.0 + sizeof(To);
+        const double it_b = MODE == 0 ? 0.0 : (MODE == 1 ? sizeof(TV) + sizeof(TF) : sizeof(TF));
+        const double bytes = top_cells * (in_b + it_b + sizeof(TV));
         KernelScope ks(MODE == 0 ? "residual_first" : "residual_update", st, bytes);
         k_top<TF, TV, To, MODE><<<(unsigned)top_tiles, 256, 0, st>>>(
             d_top, d_top_ts, (int)req.nslices, d_active, req.s, o, req.rhs, d, req.alpha, d_norms);

@@ -41,7 +41,9 @@ def test_fused_equals_reference_schedule(dev, shape, nu, precision):
     fa, sa = solve(s, I0, 1e-3, fused=1, **kw)
     fb, sb = solve(s, I0, 1e-3, fused=0, **kw)
     assert torch.equal(fa, fb)
-    assert [x["rel_residual"] for x in sa] == [x["rel_residual"] for x in sb]
+    # residual norms are summed with atomics: equal up to the summation order
+    for x, y in zip(sa, sb):
+        assert x["rel_residual"] == pytest.approx(y["rel_residual"], rel=1e-12, abs=1e-300)
 
 
 def test_fused_equals_reference_ragged(dev):
