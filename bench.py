@@ -40,6 +40,7 @@ def parse():
     p.add_argument("--impl", default="emfuse", choices=["emfuse", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--nz", type=int, default=NZ, help="slices (smaller stacks for profiling only)")
     return p.parse_args()
 
 
@@ -120,10 +121,10 @@ def cpu_oracle_sample(I0_cpu, alpha, nout=4):
     return vox / dt, dt, f"{nout} output slices of {I0_cpu.shape[1]}x{I0_cpu.shape[2]} (smoothing over {b - a} planes + {nout} DCT solves)"
 
 
-def make_input(device):
+def make_input(device, nz=NZ):
     import torch
     from paper_1506_02079_gb300.synthetic import make_stack
-    return make_stack(NZ, NY, NX, SEED, device=device, out_dtype=torch.float32)
+    return make_stack(nz, NY, NX, SEED, device=device, out_dtype=torch.float32)
 
 
 def run_reference(args):
@@ -165,7 +166,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     L = api.lib()
-    I0 = make_input(dev)
+    I0 = make_input(dev, args.nz)
     out = torch.empty_like(I0)
     opts = api.default_opts(tol=1e-6, precision=api.PREC_MIXED)
     step = lambda: api.emfuse_correct_stack(I0, 1.0, 3.0, args.alpha, opts, out=out, return_stats=True)
@@ -193,7 +194,7 @@ def run_gpu(args):
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    voxels = NZ * NY * NX
+    voxels = args.nz * NY * NX
     value = voxels * world / (ms * 1e-3)
     worst_res = max(s["rel_residual"] for s in stats)
 
@@ -246,7 +247,7 @@ def run_gpu(args):
         # parity on a sampled slice of the timed output vs the CPU FP64 oracle
         from oracle import emfuse_oracle as O
         api.emfuse_correct_stack(I0, 1.0, 3.0, args.alpha, opts, out=out)
-        j = NZ // 2
+        j = args.nz // 2
         slab = I0[j - 9:j + 10].double().cpu().numpy()
         s = O.smooth_stack(slab, 1.0, 3.0)
         ref = O.solve_dct(s[9], slab[9], args.alpha)
@@ -262,7 +263,8 @@ def run_gpu(args):
                 "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "alpha": args.alpha, "nz": NZ, "ny": NY, "nx": NX,
+                "config": {"workload": WORKLOAD if args.nz == NZ else f"{args.nz} slices x 2048 x 2048 (profiling case)",
+                           "alpha": args.alpha, "nz": args.nz, "ny": NY, "nx": NX,
                            "seed": SEED, "l2": "inputs (1.07 GB) larger than L2 (129 MB)",
                            "parallelism": f"replicas x{world}"},
                 "gpu_launches": int(launches), "vcycles": max(vcycles), "max_rel_residual": worst_res,

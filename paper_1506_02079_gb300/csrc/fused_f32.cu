@@ -20,7 +20,6 @@ static int launch_wave_impl(const WaveArgs<T>& a, int S, bool zero_init, bool up
     switch (S) {
         case 2: EMF_WAVE(2); break;
         case 4: EMF_WAVE(4); break;
-        case 6: EMF_WAVE(6); break;
         default: set_error("wavefront kernel: unsupported sweep count"); return EMFUSE_EINVAL;
     }
 #undef EMF_WAVE

@@ -81,9 +81,7 @@ struct Vec2<double> {
 };
 
 constexpr int kWaveWarps = 8;
-// rows prefetched ahead of the row being consumed (the UP leg also stages coarse values)
-template <bool UP>
-struct Prefetch { static constexpr int value = UP ? 1 : 2; };
+
 
 __host__ __device__ constexpr int wmod(int a, int w) { return ((a % w) + w) % w; }
 
@@ -115,8 +113,8 @@ struct WaveOcc { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
 
 template <class T, int S, bool ZERO, bool UP>
 __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(WaveArgs<T> a) {
+    constexpr int kPF = 2;                  // rows fetched ahead of the row being consumed
     constexpr int NR = UP ? S + 2 : S + 3;  // rows t .. t-NR+1 are live
-    constexpr int kPF = Prefetch<UP>::value;
     constexpr int W = NR + kPF;
     const int lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * kWaveWarps + (threadIdx.x >> 5);
@@ -132,28 +130,43 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     const int Y1 = min(Y0 + a.ch, L.ny);
     const int Y1e = Y1 + (Y1 & 1);                 // residual rows run to an even end
     const int tb = Y0 - (UP ? S : S + 1);          // first row of the march
-    const int te = UP ? Y1 - 1 + S : Y1e + S;      // last step
-    const int last_load = UP ? Y1 - 1 + S : Y1e + S;
+    const int te = UP ? Y1 - 1 + S : Y1e + S;      // last step (and last row loaded)
     const int k = a.k;
     const T alpha = a.alpha, sk = a.sk;
 
     const int xlane = X0 + 4 * lane;
     const bool lane_in = xlane >= 0 && xlane < L.nx;  // X0 is a multiple of 4: all-or-none
-    AxisCoef<T> ax[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) ax[i] = axis_coef<T>(xlane + i, L.nx, L.n0x, k);
     const bool interior_lane = lane >= kWaveHalo / 4 && lane < 32 - kWaveHalo / 4;
+    AxisCoef<T> ax[4];
+    T dint[4], idint[4];  // diagonal and its reciprocal on interior rows
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        ax[i] = axis_coef<T>(xlane + i, L.nx, L.n0x, k);
+        AxisCoef<T> one;
+        one.w = T(1); one.gm = T(1); one.gp = T(1);
+        const Coef<T> c = make_coef<T>(ax[i], one, k, alpha, sk);
+        dint[i] = c.D;
+        idint[i] = c.iD;
+    }
 
-    // prolongation geometry along x (UP): coarse columns 2l-1 .. 2l+2 relative to X0/2
-    int cI[4], cJ[4];
-    T cw[4];
-    const int cx0 = X0 / 2 + 2 * lane;  // coarse column of cells 0/1 of this lane
+    // prolongation geometry along x (UP): coarse columns cx0-1 .. cx0+2 around the lane
+    const int cx0 = X0 / 2 + 2 * lane;
+    int oI[4], oJ[4];
+    T cwx[4];
+    bool std_lane = true;  // interior pattern: J = I-1, I+1, I-1, I+1 with weight 1/4
     if (UP) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            if (L.uco) interp_axis<T>(xlane + i, L.n0x, k, L.ncx, cI[i], cJ[i], cw[i]);
-            else { cI[i] = cJ[i] = 0; cw[i] = T(0); }
+            int I = 0, J = 0;
+            T w = T(0);
+            if (L.uco && lane_in) interp_axis<T>(xlane + i, L.n0x, k, L.ncx, I, J, w);
+            oI[i] = I - cx0 + 1;
+            oJ[i] = J - cx0 + 1;
+            cwx[i] = w;
         }
+        std_lane = oI[0] == 1 && oJ[0] == 0 && oI[1] == 1 && oJ[1] == 2 && oI[2] == 2 && oJ[2] == 1 &&
+                   oI[3] == 2 && oJ[3] == 3 && cwx[0] == T(0.25) && cwx[1] == T(0.25) &&
+                   cwx[2] == T(0.25) && cwx[3] == T(0.25);
     }
 
     T u[W][4], b[W][4];
@@ -161,104 +174,103 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     for (int r = 0; r < W; ++r)
 #pragma unroll
         for (int i = 0; i < 4; ++i) { u[r][i] = T(0); b[r][i] = T(0); }
-    // coarse values staged with each prefetched row (UP): rows Iy and Jy, columns 2l..2l+1
-    T cr[W][4];
-    int crow_ok[W];
-#pragma unroll
-    for (int r = 0; r < W; ++r) {
-        crow_ok[r] = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) cr[r][i] = T(0);
-    }
+    // UP: coarse values (rows Iy, Jy; columns cx0, cx0+1) and row weight of the row fetched
+    // last, consumed one step later when the correction is added to that row
+    T pc[4] = {T(0), T(0), T(0), T(0)};
+    T pwy = T(0);
+    bool pok = false;
     T rsum[2] = {T(0), T(0)};  // restriction partial sums (DOWN)
 
-    auto fetch = [&](int t, T (&uu)[4], T (&bb)[4], T (&cc)[4], int& ok) {
+    auto fetch = [&](int t, T (&uu)[4], T (&bb)[4]) {
         load_row<T, (UP ? false : ZERO)>(L, t, xlane, lane_in, uu, bb);
-        ok = 0;
-        if (UP && L.uco && t >= 0 && t < L.ny) {
-            int Iy, Jy;
-            T wy;
-            interp_axis<T>(t, L.n0y, k, L.ncy, Iy, Jy, wy);
-            const bool cin = cx0 >= 0 && cx0 < L.ncx;
-            cc[0] = cc[1] = cc[2] = cc[3] = T(0);
-            if (cin) {
-                Vec2<T>::load(L.uco + (int64_t)Iy * L.pitchc + cx0, cc[0], cc[1]);
-                Vec2<T>::load(L.uco + (int64_t)Jy * L.pitchc + cx0, cc[2], cc[3]);
+        if (UP) {
+            pok = L.uco && t >= 0 && t < L.ny;
+            if (pok) {
+                int Iy, Jy;
+                interp_axis<T>(t, L.n0y, k, L.ncy, Iy, Jy, pwy);
+                pc[0] = pc[1] = pc[2] = pc[3] = T(0);
+                if (cx0 >= 0 && cx0 < L.ncx) {
+                    Vec2<T>::load(L.uco + (int64_t)Iy * L.pitchc + cx0, pc[0], pc[1]);
+                    Vec2<T>::load(L.uco + (int64_t)Jy * L.pitchc + cx0, pc[2], pc[3]);
+                }
             }
-            ok = 1;
+        }
+    };
+    // UP: add the interpolated coarse correction (staged in pc / pwy) to row slot rs
+    auto prolong = [&](T (&uu)[4]) {
+        if (!pok) return;  // uniform across the warp
+        const T r0m = __shfl_up_sync(0xffffffffu, pc[1], 1);    // column cx0-1 (lane-1)
+        const T r0p = __shfl_down_sync(0xffffffffu, pc[0], 1);  // column cx0+2 (lane+1)
+        const T r1m = __shfl_up_sync(0xffffffffu, pc[3], 1);
+        const T r1p = __shfl_down_sync(0xffffffffu, pc[2], 1);
+        if (!lane_in) return;
+        const T v0[4] = {r0m, pc[0], pc[1], r0p};
+        const T v1[4] = {r1m, pc[2], pc[3], r1p};
+        if (std_lane && xlane + 3 < L.nx) {
+            const T q = T(0.25);
+            uu[0] = uu[0] + bilinear<T>(v0[1], v0[0], v1[1], v1[0], q, pwy);
+            uu[1] = uu[1] + bilinear<T>(v0[1], v0[2], v1[1], v1[2], q, pwy);
+            uu[2] = uu[2] + bilinear<T>(v0[2], v0[1], v1[2], v1[1], q, pwy);
+            uu[3] = uu[3] + bilinear<T>(v0[2], v0[3], v1[2], v1[3], q, pwy);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (xlane + i >= L.nx) continue;
+                uu[i] = uu[i] + bilinear<T>(pick4<T>(v0, oI[i]), pick4<T>(v0, oJ[i]), pick4<T>(v1, oI[i]),
+                                            pick4<T>(v1, oJ[i]), cwx[i], pwy);
+            }
         }
     };
 
-#pragma unroll
-    for (int p = 0; p < kPF; ++p) fetch(tb + p, u[p], b[p], cr[p], crow_ok[p]);
+    // rows tb and tb+1 are in flight before the march; in UP the correction of a row is added
+    // one step after its fetch (when the coarse loads have landed)
+    fetch(tb, u[0], b[0]);
+    if (UP) prolong(u[0]);
+    fetch(tb + 1, u[1], b[1]);
 
     for (int t0 = tb; t0 <= te; t0 += W) {
 #pragma unroll
         for (int q = 0; q < W; ++q) {
             const int t = t0 + q;
             if (t > te) break;
-            // prefetch row t + kPF into its slot (which held row t + kPF - W, no longer live)
-            if (t + kPF <= last_load) {
-                const int ps = wmod(q + kPF, W);
-                fetch(t + kPF, u[ps], b[ps], cr[ps], crow_ok[ps]);
-            }
-            // UP: add the interpolated coarse correction to the arriving row
-            if (UP) {
-                const int cs = wmod(q, W);
-                if (crow_ok[cs]) {
-                    int Iy, Jy;
-                    T wy;
-                    interp_axis<T>(t, L.n0y, k, L.ncy, Iy, Jy, wy);
-                    // neighbours 2l-1 (lane-1's second value) and 2l+2 (lane+1's first)
-                    const T r0m = __shfl_up_sync(0xffffffffu, cr[cs][1], 1);
-                    const T r0p = __shfl_down_sync(0xffffffffu, cr[cs][0], 1);
-                    const T r1m = __shfl_up_sync(0xffffffffu, cr[cs][3], 1);
-                    const T r1p = __shfl_down_sync(0xffffffffu, cr[cs][2], 1);
-                    const T v0[4] = {r0m, cr[cs][0], cr[cs][1], r0p};  // columns 2l-1 .. 2l+2
-                    const T v1[4] = {r1m, cr[cs][2], cr[cs][3], r1p};
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if (xlane + i >= L.nx || !lane_in) continue;
-                        const int oi = cI[i] - cx0 + 1, oj = cJ[i] - cx0 + 1;  // in 0..3
-                        const T p = bilinear<T>(pick4<T>(v0, oi), pick4<T>(v0, oj), pick4<T>(v1, oi),
-                                                pick4<T>(v1, oj), cw[i], wy);
-                        u[cs][i] = u[cs][i] + p;
-                    }
-                }
-            }
+            // UP: finish row t + 1 (fetched one step ago), then fetch row t + 2 into the slot
+            // of row t + 2 - W, which is no longer live
+            if (UP) prolong(u[wmod(q + 1, W)]);
+            if (t + kPF <= te) fetch(t + kPF, u[wmod(q + kPF, W)], b[wmod(q + kPF, W)]);
             // half-sweeps: stage s updates row t - s with colour (s - 1) & 1
 #pragma unroll
             for (int s = 1; s <= S; ++s) {
                 const int r = t - s;
                 if (r < tb || r < 0 || r >= L.ny) continue;
-                const int sc_ = wmod(q - s, W), sn_ = wmod(q - s - 1, W), ss_ = wmod(q - s + 1, W);
-                const AxisCoef<T> ay = axis_coef<T>(r, L.ny, L.n0y, k);
+                const int sc = wmod(q - s, W), sn = wmod(q - s - 1, W), ss = wmod(q - s + 1, W);
                 const int color = (s - 1) & 1;
                 const int first = (xlane + r + color) & 1;  // first cell index with this colour
                 // neighbour from the adjacent lane: cell 3 of lane-1 or cell 0 of lane+1
-                const T west = __shfl_up_sync(0xffffffffu, u[sc_][3], 1);
-                const T east = __shfl_down_sync(0xffffffffu, u[sc_][0], 1);
+                const T west = __shfl_up_sync(0xffffffffu, u[sc][3], 1);
+                const T east = __shfl_down_sync(0xffffffffu, u[sc][0], 1);
                 if (!lane_in) continue;
+                const bool irow = interior_row(r, L.ny, k);
+                const AxisCoef<T> ay = axis_coef<T>(r, L.ny, L.n0y, k);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    // cells {0,2} when first == 0, {1,3} when first == 1
-                    const int i0 = 2 * h;
-                    T* row = u[sc_];
-                    if (first == 0) {
-                        const int i = i0;
+                    T* row = u[sc];
+                    if (first == 0) {  // cells 0 and 2
+                        const int i = 2 * h;
                         if (xlane + i < L.nx) {
                             const T uw = (i == 0) ? west : row[i - 1];
                             const T ue = row[i + 1];
-                            const Coef<T> c = make_coef<T>(ax[i], ay, k, alpha, sk);
-                            row[i] = gs_update<T>(c, b[sc_][i], uw, ue, u[sn_][i], u[ss_][i]);
+                            const Coef<T> c = irow ? interior_row_coef<T>(ax[i], k, sk, dint[i], idint[i])
+                                                   : make_coef<T>(ax[i], ay, k, alpha, sk);
+                            row[i] = gs_update<T>(c, b[sc][i], uw, ue, u[sn][i], u[ss][i]);
                         }
-                    } else {
-                        const int i = i0 + 1;
+                    } else {           // cells 1 and 3
+                        const int i = 2 * h + 1;
                         if (xlane + i < L.nx) {
                             const T uw = row[i - 1];
                             const T ue = (i == 3) ? east : row[i + 1];
-                            const Coef<T> c = make_coef<T>(ax[i], ay, k, alpha, sk);
-                            row[i] = gs_update<T>(c, b[sc_][i], uw, ue, u[sn_][i], u[ss_][i]);
+                            const Coef<T> c = irow ? interior_row_coef<T>(ax[i], k, sk, dint[i], idint[i])
+                                                   : make_coef<T>(ax[i], ay, k, alpha, sk);
+                            row[i] = gs_update<T>(c, b[sc][i], uw, ue, u[sn][i], u[ss][i]);
                         }
                     }
                 }
@@ -285,35 +297,33 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                 const T west = __shfl_up_sync(0xffffffffu, u[sr][3], 1);
                 const T east = __shfl_down_sync(0xffffffffu, u[sr][0], 1);
                 if (r >= Y0 && r < Y1e && L.bc) {
-                    T res[4];
-                    if (r < L.ny && lane_in) {
+                    const bool row_in = r < L.ny && lane_in;
+                    T res[4] = {T(0), T(0), T(0), T(0)};
+                    if (row_in) {
+                        const bool irow = interior_row(r, L.ny, k);
                         const AxisCoef<T> ay = axis_coef<T>(r, L.ny, L.n0y, k);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const T uw = i == 0 ? west : u[sr][i - 1];
                             const T ue = i == 3 ? east : u[sr][i + 1];
-                            const Coef<T> c = make_coef<T>(ax[i], ay, k, alpha, sk);
+                            const Coef<T> c = irow ? interior_row_coef<T>(ax[i], k, sk, dint[i], idint[i])
+                                                   : make_coef<T>(ax[i], ay, k, alpha, sk);
                             res[i] = residual_at<T>(c, b[sr][i], u[sr][i], uw, ue, u[srn][i], u[srs][i]);
                         }
                     }
-                    const bool row_in = r < L.ny && lane_in;
+                    // same summation order as the reference restriction:
+                    // (((0 + r00) + r01) + r10) + r11
                     if ((r & 1) == 0) {
-                        // same order as the reference restriction: ((0 + r00) + r01) + r10) + r11
                         rsum[0] = T(0);
                         rsum[1] = T(0);
-                        if (row_in) {
-                            if (xlane + 0 < L.nx) rsum[0] = rsum[0] + res[0];
-                            if (xlane + 1 < L.nx) rsum[0] = rsum[0] + res[1];
-                            if (xlane + 2 < L.nx) rsum[1] = rsum[1] + res[2];
-                            if (xlane + 3 < L.nx) rsum[1] = rsum[1] + res[3];
-                        }
-                    } else {
-                        if (row_in) {
-                            if (xlane + 0 < L.nx) rsum[0] = rsum[0] + res[0];
-                            if (xlane + 1 < L.nx) rsum[0] = rsum[0] + res[1];
-                            if (xlane + 2 < L.nx) rsum[1] = rsum[1] + res[2];
-                            if (xlane + 3 < L.nx) rsum[1] = rsum[1] + res[3];
-                        }
+                    }
+                    if (row_in) {
+                        if (xlane + 0 < L.nx) rsum[0] = rsum[0] + res[0];
+                        if (xlane + 1 < L.nx) rsum[0] = rsum[0] + res[1];
+                        if (xlane + 2 < L.nx) rsum[1] = rsum[1] + res[2];
+                        if (xlane + 3 < L.nx) rsum[1] = rsum[1] + res[3];
+                    }
+                    if (r & 1) {
                         const int J = r >> 1;
                         if (interior_lane && lane_in && J < L.ncy) {
                             T* dst = L.bc + (int64_t)J * L.pitchc + cx0;

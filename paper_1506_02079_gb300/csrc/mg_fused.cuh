@@ -14,8 +14,10 @@ namespace emfuse {
 
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ float div_t(float a, float b) { return __fdiv_rn(a, b); }
-__device__ __forceinline__ double div_t(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float rcp_t(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double rcp_t(double a) { return __drcp_rn(a); }
+__device__ __forceinline__ float mul_t(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_t(double a, double b) { return __dmul_rn(a, b); }
 
 // One slice at one multigrid level (device-visible).
 template <class T>
@@ -69,7 +71,7 @@ __device__ __forceinline__ AxisCoef<T> axis_coef(int i, int n, int n0, int k) {
 
 template <class T>
 struct Coef {
-    T cw, ce, cn, cs, D;
+    T cw, ce, cn, cs, D, iD;  // iD = correctly rounded 1 / D
 };
 
 // Finite-volume stencil of level k at a cell (interior cells: alpha + L/4^k).
@@ -83,6 +85,7 @@ __device__ __forceinline__ Coef<T> make_coef(const AxisCoef<T>& ax, const AxisCo
         c.cn = ay.gm;
         c.cs = ay.gp;
         c.D = alpha + (((c.cw + c.ce) + c.cn) + c.cs);
+        c.iD = rcp_t(c.D);
         return c;
     }
     c.cw = sk * (ay.w * ax.gm);
@@ -90,7 +93,35 @@ __device__ __forceinline__ Coef<T> make_coef(const AxisCoef<T>& ax, const AxisCo
     c.cn = sk * (ax.w * ay.gm);
     c.cs = sk * (ax.w * ay.gp);
     c.D = fma_t(alpha, ax.w * ay.w, ((c.cw + c.ce) + c.cn) + c.cs);
+    c.iD = rcp_t(c.D);
     return c;
+}
+
+// The stencil of a cell on an interior row (ay = {1, 1, 1}) with D and 1/D taken from a
+// per-column cache (d, id) computed by make_coef on such a row: the same values make_coef
+// returns, without recomputing the diagonal and its reciprocal.
+template <class T>
+__device__ __forceinline__ Coef<T> interior_row_coef(const AxisCoef<T>& ax, int k, T sk, T d, T id) {
+    Coef<T> c;
+    if (k == 0) {
+        c.cw = ax.gm;
+        c.ce = ax.gp;
+        c.cn = T(1);
+        c.cs = T(1);
+    } else {
+        c.cw = sk * (T(1) * ax.gm);
+        c.ce = sk * (T(1) * ax.gp);
+        c.cn = sk * (ax.w * T(1));
+        c.cs = sk * (ax.w * T(1));
+    }
+    c.D = d;
+    c.iD = id;
+    return c;
+}
+
+// Rows whose axis_coef is {1, 1, 1} (see axis_coef).
+__device__ __forceinline__ bool interior_row(int r, int n, int k) {
+    return k == 0 ? (r >= 1 && r + 1 < n) : (r >= 1 && r + 2 < n);
 }
 
 template <class T>
@@ -100,14 +131,14 @@ __device__ __forceinline__ Coef<T> coef_at(int x, int y, int nx, int ny, int n0x
 }
 
 
-// Gauss-Seidel update u_p = (b_p + sum_q c_pq u_q) / D_p.
+// Gauss-Seidel update u_p = (b_p + sum_q c_pq u_q) * (1 / D_p).
 template <class T>
 __device__ __forceinline__ T gs_update(const Coef<T>& c, T b, T uw, T ue, T un, T us) {
     T acc = fma_t(c.cw, uw, b);
     acc = fma_t(c.ce, ue, acc);
     acc = fma_t(c.cn, un, acc);
     acc = fma_t(c.cs, us, acc);
-    return div_t(acc, c.D);
+    return mul_t(acc, c.iD);
 }
 
 // Residual b_p - (D_p u_p - sum_q c_pq u_q).

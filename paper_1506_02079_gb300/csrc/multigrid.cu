@@ -329,7 +329,7 @@ struct Solver {
 
     Solver(const SolveRequest& r, cudaStream_t s) : req(r), st(s) {}
 
-    static bool wave_ok(int nu) { return nu == 1 || nu == 2 || (nu == 3 && sizeof(TV) == 4); }
+    static bool wave_ok(int nu) { return nu == 1 || nu == 2; }
 
     int build() {
         const int64_t n = req.nslices;

@@ -33,8 +33,6 @@ def solve(s, o, alpha, **kw):
 @pytest.mark.parametrize("nu", [(1, 1), (2, 2), (3, 3), (2, 1), (1, 3)])
 @pytest.mark.parametrize("precision", [api.PREC_FP32, api.PREC_MIXED, api.PREC_FP64])
 def test_fused_equals_reference_schedule(dev, shape, nu, precision):
-    if precision == api.PREC_FP64 and 3 in nu and shape[1] * shape[2] > 100000:
-        pytest.skip("FP64 nu=3 runs the reference schedule only")
     I0 = make_stack(*shape, seed=21).to(dev)
     s = api.emfuse_smooth_z(I0, 1.0, 3.0)
     kw = dict(nu_pre=nu[0], nu_post=nu[1], precision=precision, max_vcycles=3, tol=0.0)
