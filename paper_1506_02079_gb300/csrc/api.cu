@@ -37,8 +37,8 @@ static int resolve_opts(const emfuse_solve_opts* in, emfuse_solve_opts* out) {
 static bool dtype_ok(int dt) { return dt == EMFUSE_U8 || dt == EMFUSE_F32; }
 static size_t dtype_size(int dt) { return dt == EMFUSE_U8 ? 1 : 4; }
 
-// Largest supported side: level indices and pitches are 32-bit.
-constexpr int64_t kMaxSide = (int64_t)1 << 30;
+// Largest supported side: level geometry is computed in 32-bit integers.
+constexpr int64_t kMaxSide = (int64_t)1 << 29;
 
 static int check_sigma(float sxy, float sz) {
     if (!(sxy >= 0.f) || !(sz >= 0.f) || !std::isfinite(sxy) || !std::isfinite(sz))
@@ -104,7 +104,7 @@ int emfuse_smooth_z(const void* in, int dt, float* out, int64_t nx, int64_t ny, 
     if (!in || !out) return einval("emfuse_smooth_z: null pointer");
     if (!dtype_ok(dt)) return einval("emfuse_smooth_z: dtype must be EMFUSE_U8 or EMFUSE_F32");
     if (nx < 1 || ny < 1 || nz < 1 || nx > kMaxSide || ny > kMaxSide || nz > kMaxSide)
-        return einval("emfuse_smooth_z: sizes must be in [1, 2^30]");
+        return einval("emfuse_smooth_z: sizes must be in [1, 2^29]");
     if (pitch < nx) return einval("emfuse_smooth_z: pitch must be >= nx");
     if (z0 < 0 || z1 > nz || z0 >= z1) return einval("emfuse_smooth_z: need 0 <= z0 < z1 <= nz");
     EMF_TRY(check_sigma(sigma_xy, sigma_z));
@@ -122,7 +122,7 @@ int emfuse_screened_poisson(const float* s, const float* o, float* f, int64_t ns
     if (f == s || f == o) return einval("emfuse_screened_poisson: f must not alias s or o");
     for (int64_t j = 0; j < nslices; ++j) {
         if (nx[j] < 1 || ny[j] < 1 || nx[j] > kMaxSide || ny[j] > kMaxSide)
-            return einval("emfuse_screened_poisson: slice sizes must be in [1, 2^30]");
+            return einval("emfuse_screened_poisson: slice sizes must be in [1, 2^29]");
         if (offsets[j] < 0) return einval("emfuse_screened_poisson: negative offset");
     }
     EMF_TRY(check_alpha(alpha));
@@ -151,7 +151,7 @@ int emfuse_correct_stack(const void* in, int dt, int in_is_host, float* out, int
     if (!in || !out) return einval("emfuse_correct_stack: null pointer");
     if (!dtype_ok(dt)) return einval("emfuse_correct_stack: dtype must be EMFUSE_U8 or EMFUSE_F32");
     if (nx < 1 || ny < 1 || nz < 1 || nx > kMaxSide || ny > kMaxSide || nz > kMaxSide)
-        return einval("emfuse_correct_stack: sizes must be in [1, 2^30]");
+        return einval("emfuse_correct_stack: sizes must be in [1, 2^29]");
     EMF_TRY(check_sigma(sigma_xy, sigma_z));
     EMF_TRY(check_alpha(alpha));
     emfuse_solve_opts o2;
@@ -210,7 +210,7 @@ int emfuse_backward(const float* grad_f, const float* f, const float* s, const v
     if (!grad_f) return einval("emfuse_backward: grad_f is null");
     if (!dtype_ok(dt)) return einval("emfuse_backward: dtype must be EMFUSE_U8 or EMFUSE_F32");
     if (nx < 1 || ny < 1 || nz < 1 || nx > kMaxSide || ny > kMaxSide || nz > kMaxSide)
-        return einval("emfuse_backward: sizes must be in [1, 2^30]");
+        return einval("emfuse_backward: sizes must be in [1, 2^29]");
     if (grad_alpha && (!f || !s)) return einval("emfuse_backward: grad_alpha needs f and s");
     if (grad_sigma_z && !o) return einval("emfuse_backward: grad_sigma_z needs o (I0)");
     EMF_TRY(check_alpha(alpha));

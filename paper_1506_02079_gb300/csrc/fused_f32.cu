@@ -11,11 +11,17 @@ static int launch_wave_impl(const WaveArgs<T>& a, int S, bool zero_init, bool up
     const char* name = up ? (a.k == 0 ? "wave_up_l0" : "wave_up_coarse")
                           : (a.k == 0 ? "wave_down_l0" : "wave_down_coarse");
     KernelScope ks(name, st, bytes);
+    const int smem = kWaveWarps * fused_detail::WaveRing<T>::kWarpBytes;
+#define EMF_WAVE_ONE(KERNEL)                                                                 \
+    do {                                                                                     \
+        cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
+        KERNEL<<<grid, kWaveWarps * 32, smem, st>>>(a);                                      \
+    } while (0)
 #define EMF_WAVE(SS)                                                                         \
     do {                                                                                     \
-        if (up) fused_detail::k_wave<T, SS, false, true><<<grid, kWaveWarps * 32, 0, st>>>(a);             \
-        else if (zero_init) fused_detail::k_wave<T, SS, true, false><<<grid, kWaveWarps * 32, 0, st>>>(a); \
-        else fused_detail::k_wave<T, SS, false, false><<<grid, kWaveWarps * 32, 0, st>>>(a);              \
+        if (up) EMF_WAVE_ONE((fused_detail::k_wave<T, SS, false, true>));                    \
+        else if (zero_init) EMF_WAVE_ONE((fused_detail::k_wave<T, SS, true, false>));        \
+        else EMF_WAVE_ONE((fused_detail::k_wave<T, SS, false, false>));                      \
     } while (0)
     switch (S) {
         case 2: EMF_WAVE(2); break;
@@ -23,6 +29,7 @@ static int launch_wave_impl(const WaveArgs<T>& a, int S, bool zero_init, bool up
         default: set_error("wavefront kernel: unsupported sweep count"); return EMFUSE_EINVAL;
     }
 #undef EMF_WAVE
+#undef EMF_WAVE_ONE
     EMF_CHECK_LAUNCH();
     return EMFUSE_OK;
 }

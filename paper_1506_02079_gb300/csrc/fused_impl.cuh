@@ -28,6 +28,7 @@
 
 #include "emfuse_common.cuh"
 #include "mg_fused.cuh"
+#include "tma.cuh"
 
 namespace emfuse {
 namespace fused_detail {
@@ -91,37 +92,56 @@ __device__ __forceinline__ T pick4(const T (&v)[4], int i) {
     return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3]));
 }
 
-// Loads row t of u (unless ZERO) and b for the lane's 4 cells; zero outside the level.
-template <class T, bool ZERO>
-__device__ __forceinline__ void load_row(const LSlice<T>& L, int t, int xlane, bool lane_in,
-                                         T (&u)[4], T (&b)[4]) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) { u[i] = T(0); b[i] = T(0); }
-    if (t < 0 || t >= L.ny || !lane_in) return;
-    const int64_t off = (int64_t)t * L.pitch + xlane;
-    Vec4<T>::load(L.b + off, b);
-    if (!ZERO) Vec4<T>::load(L.u + off, u);
-    // cells past nx sit in the row padding: mask them
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        if (xlane + i >= L.nx) { u[i] = T(0); b[i] = T(0); }
-}
-
 // FP32 kernels keep two CTAs per SM; FP64 windows need twice the registers.
 template <class T>
 struct WaveOcc { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
 
+// Stencil of a cell on a non-interior row (slice edge, partial coarse cell): rare, so kept
+// out of line to keep the march small enough for the instruction cache.
+template <class T>
+__device__ __noinline__ Coef<T> edge_row_coef(AxisCoef<T> ax, int r, int ny, int n0y, int k, T alpha, T sk) {
+    return make_coef<T>(ax, axis_coef<T>(r, ny, n0y, k), k, alpha, sk);
+}
+
+// Prolongation for lanes whose cells do not follow the interior 1/4-3/4 pattern.
+template <class T>
+__device__ __noinline__ void prolong_generic(T (&uu)[4], const T (&v0)[4], const T (&v1)[4], const int (&oI)[4],
+                                             const int (&oJ)[4], const T (&cwx)[4], T wy, int xlane, int nx) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (xlane + i >= nx) continue;
+        uu[i] = uu[i] + bilinear<T>(pick4<T>(v0, oI[i]), pick4<T>(v0, oJ[i]), pick4<T>(v1, oI[i]),
+                                    pick4<T>(v1, oJ[i]), cwx[i], wy);
+    }
+}
+
+// Shared-memory ring of one warp: NB slots, each holding one row of u and b of the strip
+// (128 cells) and, for the prolongation leg, the two coarse rows around it.
+template <class T>
+struct WaveRing {
+    static constexpr int kNB = 4;                                    // rows in flight
+    static constexpr int kRowBytes = kWaveWidth * (int)sizeof(T);
+    static constexpr int kCoarseBytes = (kWaveCoarseW * 2 * (int)sizeof(T) + 127) / 128 * 128;
+    static constexpr int kSlotBytes = 2 * kRowBytes + kCoarseBytes;
+    static constexpr int kWarpBytes = kNB * kSlotBytes + 128;        // + the slot barriers
+};
+
 template <class T, int S, bool ZERO, bool UP>
 __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(WaveArgs<T> a) {
-    constexpr int kPF = 2;                  // rows fetched ahead of the row being consumed
-    constexpr int NR = UP ? S + 2 : S + 3;  // rows t .. t-NR+1 are live
-    constexpr int W = NR + kPF;
+    using R = WaveRing<T>;
+    constexpr int NB = R::kNB;
+    constexpr int NR = UP ? S + 2 : S + 3;  // window: rows t-NR+1 .. t, slot NR-1 = row t
+    extern __shared__ __align__(128) unsigned char wave_smem[];
     const int lane = threadIdx.x & 31;
-    const int64_t item = (int64_t)blockIdx.x * kWaveWarps + (threadIdx.x >> 5);
+    const int warp = threadIdx.x >> 5;
+    const int64_t item = (int64_t)blockIdx.x * kWaveWarps + warp;
     if (item >= a.nitems) return;
     const int j = find_item(a.item_start, a.nsl, item);
     const LSlice<T> L = a.sl[j];
     if (a.active && !a.active[L.slice]) return;
+    const CUtensorMap* map_u = a.maps + 3 * j;
+    const CUtensorMap* map_b = map_u + 1;
+    const CUtensorMap* map_c = map_u + 2;
     const int li = int(item - a.item_start[j]);
     const int strip = li % L.fstrips;
     const int chunk = li / L.fstrips;
@@ -130,7 +150,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     const int Y1 = min(Y0 + a.ch, L.ny);
     const int Y1e = Y1 + (Y1 & 1);                 // residual rows run to an even end
     const int tb = Y0 - (UP ? S : S + 1);          // first row of the march
-    const int te = UP ? Y1 - 1 + S : Y1e + S;      // last step (and last row loaded)
+    const int te = UP ? Y1 - 1 + S : Y1e + S;      // last row (each row is loaded once)
     const int k = a.k;
     const T alpha = a.alpha, sk = a.sk;
 
@@ -151,15 +171,17 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
 
     // prolongation geometry along x (UP): coarse columns cx0-1 .. cx0+2 around the lane
     const int cx0 = X0 / 2 + 2 * lane;
+    const int cbox_x = X0 / 2 - 4;  // first coarse column staged (a multiple of 2 elements x 16 B)
     int oI[4], oJ[4];
     T cwx[4];
     bool std_lane = true;  // interior pattern: J = I-1, I+1, I-1, I+1 with weight 1/4
+    const bool has_coarse = UP && L.uco != nullptr;
     if (UP) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             int I = 0, J = 0;
             T w = T(0);
-            if (L.uco && lane_in) interp_axis<T>(xlane + i, L.n0x, k, L.ncx, I, J, w);
+            if (has_coarse && lane_in) interp_axis<T>(xlane + i, L.n0x, k, L.ncx, I, J, w);
             oI[i] = I - cx0 + 1;
             oJ[i] = J - cx0 + 1;
             cwx[i] = w;
@@ -169,168 +191,195 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                    cwx[2] == T(0.25) && cwx[3] == T(0.25);
     }
 
-    T u[W][4], b[W][4];
+    // ---- shared-memory ring and its barriers
+    unsigned char* ring = wave_smem + (size_t)warp * R::kWarpBytes;
+    const uint32_t ring_s = smem_addr(ring);
+    const uint32_t bar_s = ring_s + NB * R::kSlotBytes;
+    if (lane == 0) {
+        for (int s = 0; s < NB; ++s) mbar_init(bar_s + 8 * s, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    constexpr uint32_t kRowB = R::kRowBytes;
+    // issue the TMA loads of row t into its slot (lane 0 only)
+    auto issue = [&](int t) {
+        const int slot = (t - tb) % NB;
+        const uint32_t base = ring_s + slot * R::kSlotBytes, bar = bar_s + 8 * slot;
+        const bool coarse = has_coarse && t >= 0 && t < L.ny;
+        uint32_t bytes = kRowB + (ZERO ? 0u : kRowB);
+        int y0c = 0;
+        if (coarse) {
+            int Iy, Jy;
+            T wy;
+            interp_axis<T>(t, L.n0y, k, L.ncy, Iy, Jy, wy);
+            y0c = min(Iy, Jy);
+            bytes += kWaveCoarseW * 2 * (uint32_t)sizeof(T);
+        }
+        fence_proxy_async();
+        mbar_expect_tx(bar, bytes);
+        tma_load_2d(base + kRowB, map_b, X0, t, bar);
+        if (!ZERO) tma_load_2d(base, map_u, X0, t, bar);
+        if (coarse) tma_load_2d(base + 2 * kRowB, map_c, cbox_x, y0c, bar);
+    };
+    if (lane == 0)
+        for (int p = 0; p < NB && tb + p <= te; ++p) issue(tb + p);
+
+    T u[NR][4], b[NR][4];
 #pragma unroll
-    for (int r = 0; r < W; ++r)
+    for (int r = 0; r < NR; ++r)
 #pragma unroll
         for (int i = 0; i < 4; ++i) { u[r][i] = T(0); b[r][i] = T(0); }
-    // UP: coarse values (rows Iy, Jy; columns cx0, cx0+1) and row weight of the row fetched
-    // last, consumed one step later when the correction is added to that row
-    T pc[4] = {T(0), T(0), T(0), T(0)};
-    T pwy = T(0);
-    bool pok = false;
     T rsum[2] = {T(0), T(0)};  // restriction partial sums (DOWN)
 
-    auto fetch = [&](int t, T (&uu)[4], T (&bb)[4]) {
-        load_row<T, (UP ? false : ZERO)>(L, t, xlane, lane_in, uu, bb);
-        if (UP) {
-            pok = L.uco && t >= 0 && t < L.ny;
-            if (pok) {
-                int Iy, Jy;
-                interp_axis<T>(t, L.n0y, k, L.ncy, Iy, Jy, pwy);
-                pc[0] = pc[1] = pc[2] = pc[3] = T(0);
-                if (cx0 >= 0 && cx0 < L.ncx) {
-                    Vec2<T>::load(L.uco + (int64_t)Iy * L.pitchc + cx0, pc[0], pc[1]);
-                    Vec2<T>::load(L.uco + (int64_t)Jy * L.pitchc + cx0, pc[2], pc[3]);
+#pragma unroll 1
+    for (int t = tb; t <= te; ++t) {
+        const int n = t - tb;
+        const int slot = n % NB;
+        const uint32_t bar = bar_s + 8 * slot;
+        if (!mbar_wait_warp(bar, (n / NB) & 1)) {
+            // give up: flag the host, let the copies already issued land, leave
+            if (lane == 0) atomicExch(a.err, 1);
+            for (int tt = t + 1; tt <= te && tt < t + NB; ++tt)
+                mbar_wait_warp(bar_s + 8 * ((tt - tb) % NB), ((tt - tb) / NB) & 1);
+            return;
+        }
+        // shift the window and bring in row t
+#pragma unroll
+        for (int r = 0; r < NR - 1; ++r)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { u[r][i] = u[r + 1][i]; b[r][i] = b[r + 1][i]; }
+        const unsigned char* sl_ptr = ring + slot * R::kSlotBytes;
+        {
+            const T* ub = reinterpret_cast<const T*>(sl_ptr);
+            const T* bb = reinterpret_cast<const T*>(sl_ptr + kRowB);
+            Vec4<T>::load(bb + 4 * lane, b[NR - 1]);
+            if (ZERO) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) u[NR - 1][i] = T(0);
+            } else {
+                Vec4<T>::load(ub + 4 * lane, u[NR - 1]);
+            }
+        }
+        // UP: add the interpolated coarse correction to row t
+        if (has_coarse && t >= 0 && t < L.ny) {
+            int Iy, Jy;
+            T wy;
+            interp_axis<T>(t, L.n0y, k, L.ncy, Iy, Jy, wy);
+            const int y0c = min(Iy, Jy);
+            const T* cb = reinterpret_cast<const T*>(sl_ptr + 2 * kRowB);
+            const T* c0 = cb + (Iy - y0c) * kWaveCoarseW + 2 * lane + 3;  // column cx0 - 1
+            const T* c1 = cb + (Jy - y0c) * kWaveCoarseW + 2 * lane + 3;
+            const T v0[4] = {c0[0], c0[1], c0[2], c0[3]};
+            const T v1[4] = {c1[0], c1[1], c1[2], c1[3]};
+            if (lane_in) {
+                T(&row)[4] = u[NR - 1];
+                if (std_lane && xlane + 3 < L.nx) {
+                    const T q = T(0.25);
+                    row[0] = row[0] + bilinear<T>(v0[1], v0[0], v1[1], v1[0], q, wy);
+                    row[1] = row[1] + bilinear<T>(v0[1], v0[2], v1[1], v1[2], q, wy);
+                    row[2] = row[2] + bilinear<T>(v0[2], v0[1], v1[2], v1[1], q, wy);
+                    row[3] = row[3] + bilinear<T>(v0[2], v0[3], v1[2], v1[3], q, wy);
+                } else {
+                    prolong_generic<T>(row, v0, v1, oI, oJ, cwx, wy, xlane, L.nx);
                 }
             }
         }
-    };
-    // UP: add the interpolated coarse correction (staged in pc / pwy) to row slot rs
-    auto prolong = [&](T (&uu)[4]) {
-        if (!pok) return;  // uniform across the warp
-        const T r0m = __shfl_up_sync(0xffffffffu, pc[1], 1);    // column cx0-1 (lane-1)
-        const T r0p = __shfl_down_sync(0xffffffffu, pc[0], 1);  // column cx0+2 (lane+1)
-        const T r1m = __shfl_up_sync(0xffffffffu, pc[3], 1);
-        const T r1p = __shfl_down_sync(0xffffffffu, pc[2], 1);
-        if (!lane_in) return;
-        const T v0[4] = {r0m, pc[0], pc[1], r0p};
-        const T v1[4] = {r1m, pc[2], pc[3], r1p};
-        if (std_lane && xlane + 3 < L.nx) {
-            const T q = T(0.25);
-            uu[0] = uu[0] + bilinear<T>(v0[1], v0[0], v1[1], v1[0], q, pwy);
-            uu[1] = uu[1] + bilinear<T>(v0[1], v0[2], v1[1], v1[2], q, pwy);
-            uu[2] = uu[2] + bilinear<T>(v0[2], v0[1], v1[2], v1[1], q, pwy);
-            uu[3] = uu[3] + bilinear<T>(v0[2], v0[3], v1[2], v1[3], q, pwy);
-        } else {
+        // the slot is consumed: refill it with row t + NB
+        __syncwarp();
+        if (lane == 0 && t + NB <= te) issue(t + NB);
+
+        // half-sweeps: stage s updates row t - s (window slot NR-1-s) with colour (s - 1) & 1
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (xlane + i >= L.nx) continue;
-                uu[i] = uu[i] + bilinear<T>(pick4<T>(v0, oI[i]), pick4<T>(v0, oJ[i]), pick4<T>(v1, oI[i]),
-                                            pick4<T>(v1, oJ[i]), cwx[i], pwy);
+        for (int s = 1; s <= S; ++s) {
+            const int r = t - s;
+            if (r < tb || r < 0 || r >= L.ny) continue;
+            T(&row)[4] = u[NR - 1 - s];
+            const T(&nrow)[4] = u[NR - 2 - s];
+            const T(&srow)[4] = u[NR - s];
+            const T(&brow)[4] = b[NR - 1 - s];
+            const int color = (s - 1) & 1;
+            const int first = (xlane + r + color) & 1;  // first cell index with this colour
+            const T west = __shfl_up_sync(0xffffffffu, row[3], 1);   // cell 3 of lane-1
+            const T east = __shfl_down_sync(0xffffffffu, row[0], 1);  // cell 0 of lane+1
+            if (!lane_in) continue;
+            const bool irow = interior_row(r, L.ny, k);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (first == 0) {  // cells 0 and 2
+                    const int i = 2 * h;
+                    if (xlane + i < L.nx) {
+                        const T uw = (i == 0) ? west : row[i - 1];
+                        const T ue = row[i + 1];
+                        const Coef<T> c = irow ? interior_row_coef<T>(ax[i], k, sk, dint[i], idint[i])
+                                               : edge_row_coef<T>(ax[i], r, L.ny, L.n0y, k, alpha, sk);
+                        row[i] = gs_update<T>(c, brow[i], uw, ue, nrow[i], srow[i]);
+                    }
+                } else {           // cells 1 and 3
+                    const int i = 2 * h + 1;
+                    if (xlane + i < L.nx) {
+                        const T uw = row[i - 1];
+                        const T ue = (i == 3) ? east : row[i + 1];
+                        const Coef<T> c = irow ? interior_row_coef<T>(ax[i], k, sk, dint[i], idint[i])
+                                               : edge_row_coef<T>(ax[i], r, L.ny, L.n0y, k, alpha, sk);
+                        row[i] = gs_update<T>(c, brow[i], uw, ue, nrow[i], srow[i]);
+                    }
+                }
             }
         }
-    };
-
-    // rows tb and tb+1 are in flight before the march; in UP the correction of a row is added
-    // one step after its fetch (when the coarse loads have landed)
-    fetch(tb, u[0], b[0]);
-    if (UP) prolong(u[0]);
-    fetch(tb + 1, u[1], b[1]);
-
-    for (int t0 = tb; t0 <= te; t0 += W) {
+        // output of the row that completed all half-sweeps
+        {
+            const int r = t - S;
+            if (r >= Y0 && r < Y1 && interior_lane && lane_in) {
+                const T(&orow)[4] = u[NR - 1 - S];
+                T* dst = (UP ? L.uo : L.u) + (int64_t)r * L.pitch + xlane;
+                if (xlane + 3 < L.nx) {
+                    Vec4<T>::store(dst, orow);
+                } else {
 #pragma unroll
-        for (int q = 0; q < W; ++q) {
-            const int t = t0 + q;
-            if (t > te) break;
-            // UP: finish row t + 1 (fetched one step ago), then fetch row t + 2 into the slot
-            // of row t + 2 - W, which is no longer live
-            if (UP) prolong(u[wmod(q + 1, W)]);
-            if (t + kPF <= te) fetch(t + kPF, u[wmod(q + kPF, W)], b[wmod(q + kPF, W)]);
-            // half-sweeps: stage s updates row t - s with colour (s - 1) & 1
-#pragma unroll
-            for (int s = 1; s <= S; ++s) {
-                const int r = t - s;
-                if (r < tb || r < 0 || r >= L.ny) continue;
-                const int sc = wmod(q - s, W), sn = wmod(q - s - 1, W), ss = wmod(q - s + 1, W);
-                const int color = (s - 1) & 1;
-                const int first = (xlane + r + color) & 1;  // first cell index with this colour
-                // neighbour from the adjacent lane: cell 3 of lane-1 or cell 0 of lane+1
-                const T west = __shfl_up_sync(0xffffffffu, u[sc][3], 1);
-                const T east = __shfl_down_sync(0xffffffffu, u[sc][0], 1);
-                if (!lane_in) continue;
-                const bool irow = interior_row(r, L.ny, k);
-                const AxisCoef<T> ay = axis_coef<T>(r, L.ny, L.n0y, k);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    T* row = u[sc];
-                    if (first == 0) {  // cells 0 and 2
-                        const int i = 2 * h;
-                        if (xlane + i < L.nx) {
-                            const T uw = (i == 0) ? west : row[i - 1];
-                            const T ue = row[i + 1];
-                            const Coef<T> c = irow ? interior_row_coef<T>(ax[i], k, sk, dint[i], idint[i])
-                                                   : make_coef<T>(ax[i], ay, k, alpha, sk);
-                            row[i] = gs_update<T>(c, b[sc][i], uw, ue, u[sn][i], u[ss][i]);
-                        }
-                    } else {           // cells 1 and 3
-                        const int i = 2 * h + 1;
-                        if (xlane + i < L.nx) {
-                            const T uw = row[i - 1];
-                            const T ue = (i == 3) ? east : row[i + 1];
-                            const Coef<T> c = irow ? interior_row_coef<T>(ax[i], k, sk, dint[i], idint[i])
-                                                   : make_coef<T>(ax[i], ay, k, alpha, sk);
-                            row[i] = gs_update<T>(c, b[sc][i], uw, ue, u[sn][i], u[ss][i]);
-                        }
-                    }
+                    for (int i = 0; i < 4; ++i)
+                        if (xlane + i < L.nx) dst[i] = orow[i];
                 }
             }
-            // output of the row that completed all half-sweeps
-            {
-                const int r = t - S;
-                const int so = wmod(q - S, W);
-                if (r >= Y0 && r < Y1 && interior_lane && lane_in) {
-                    T* dst = (UP ? L.uo : L.u) + (int64_t)r * L.pitch + xlane;
-                    if (xlane + 3 < L.nx) {
-                        Vec4<T>::store(dst, u[so]);
-                    } else {
+        }
+        if (!UP) {
+            // residual of row t - S - 1 (slot 1; neighbours in slots 0 and 2) and its restriction
+            const int r = t - S - 1;
+            const T(&rrow)[4] = u[1];
+            const T west = __shfl_up_sync(0xffffffffu, rrow[3], 1);
+            const T east = __shfl_down_sync(0xffffffffu, rrow[0], 1);
+            if (r >= Y0 && r < Y1e && L.bc) {
+                const bool row_in = r < L.ny && lane_in;
+                T res[4] = {T(0), T(0), T(0), T(0)};
+                if (row_in) {
+                    const bool irow = interior_row(r, L.ny, k);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            if (xlane + i < L.nx) dst[i] = u[so][i];
+                    for (int i = 0; i < 4; ++i) {
+                        const T uw = i == 0 ? west : rrow[i - 1];
+                        const T ue = i == 3 ? east : rrow[i + 1];
+                        const Coef<T> c = irow ? interior_row_coef<T>(ax[i], k, sk, dint[i], idint[i])
+                                               : edge_row_coef<T>(ax[i], r, L.ny, L.n0y, k, alpha, sk);
+                        res[i] = residual_at<T>(c, b[1][i], rrow[i], uw, ue, u[0][i], u[2][i]);
                     }
                 }
-            }
-            if (!UP) {
-                // residual of row t - S - 1 and its 2x2 restriction
-                const int r = t - S - 1;
-                const int sr = wmod(q - S - 1, W), srn = wmod(q - S - 2, W), srs = wmod(q - S, W);
-                const T west = __shfl_up_sync(0xffffffffu, u[sr][3], 1);
-                const T east = __shfl_down_sync(0xffffffffu, u[sr][0], 1);
-                if (r >= Y0 && r < Y1e && L.bc) {
-                    const bool row_in = r < L.ny && lane_in;
-                    T res[4] = {T(0), T(0), T(0), T(0)};
-                    if (row_in) {
-                        const bool irow = interior_row(r, L.ny, k);
-                        const AxisCoef<T> ay = axis_coef<T>(r, L.ny, L.n0y, k);
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const T uw = i == 0 ? west : u[sr][i - 1];
-                            const T ue = i == 3 ? east : u[sr][i + 1];
-                            const Coef<T> c = irow ? interior_row_coef<T>(ax[i], k, sk, dint[i], idint[i])
-                                                   : make_coef<T>(ax[i], ay, k, alpha, sk);
-                            res[i] = residual_at<T>(c, b[sr][i], u[sr][i], uw, ue, u[srn][i], u[srs][i]);
-                        }
-                    }
-                    // same summation order as the reference restriction:
-                    // (((0 + r00) + r01) + r10) + r11
-                    if ((r & 1) == 0) {
-                        rsum[0] = T(0);
-                        rsum[1] = T(0);
-                    }
-                    if (row_in) {
-                        if (xlane + 0 < L.nx) rsum[0] = rsum[0] + res[0];
-                        if (xlane + 1 < L.nx) rsum[0] = rsum[0] + res[1];
-                        if (xlane + 2 < L.nx) rsum[1] = rsum[1] + res[2];
-                        if (xlane + 3 < L.nx) rsum[1] = rsum[1] + res[3];
-                    }
-                    if (r & 1) {
-                        const int J = r >> 1;
-                        if (interior_lane && lane_in && J < L.ncy) {
-                            T* dst = L.bc + (int64_t)J * L.pitchc + cx0;
-                            const T v0 = rsum[0] * T(0.25), v1 = rsum[1] * T(0.25);
-                            if (cx0 + 1 < L.ncx) Vec2<T>::store(dst, v0, v1);
-                            else if (cx0 < L.ncx) dst[0] = v0;
-                        }
+                // same summation order as the reference restriction:
+                // (((0 + r00) + r01) + r10) + r11
+                if ((r & 1) == 0) {
+                    rsum[0] = T(0);
+                    rsum[1] = T(0);
+                }
+                if (row_in) {
+                    if (xlane + 0 < L.nx) rsum[0] = rsum[0] + res[0];
+                    if (xlane + 1 < L.nx) rsum[0] = rsum[0] + res[1];
+                    if (xlane + 2 < L.nx) rsum[1] = rsum[1] + res[2];
+                    if (xlane + 3 < L.nx) rsum[1] = rsum[1] + res[3];
+                }
+                if (r & 1) {
+                    const int J = r >> 1;
+                    if (interior_lane && lane_in && J < L.ncy) {
+                        T* dst = L.bc + (int64_t)J * L.pitchc + cx0;
+                        const T v0 = rsum[0] * T(0.25), v1 = rsum[1] * T(0.25);
+                        if (cx0 + 1 < L.ncx) Vec2<T>::store(dst, v0, v1);
+                        else if (cx0 < L.ncx) dst[0] = v0;
                     }
                 }
             }

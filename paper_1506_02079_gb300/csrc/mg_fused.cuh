@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda.h>
+
 #include "emfuse_common.cuh"
 
 namespace emfuse {
@@ -156,18 +158,23 @@ __device__ __forceinline__ T residual_at(const Coef<T>& c, T b, T u, T uw, T ue,
 template <class T>
 __device__ __forceinline__ void interp_axis(int x, int n0, int k, int nc, int& I, int& J, T& wJ) {
     I = x >> 1;
-    const long long fs = (long long)x << k, cs = (long long)I << (k + 1);
-    const long long hf = min((long long)1 << k, (long long)n0 - fs);
-    const long long hc = min((long long)1 << (k + 1), (long long)n0 - cs);
-    const long long cf2 = 2 * fs + hf, cc2 = 2 * cs + hc;  // twice the centres
+    if (x >= 2 && I + 2 < nc) {  // fine cell and both coarse cells full: weight exactly 1/4
+        J = (x & 1) ? I + 1 : I - 1;
+        wJ = T(0.25);
+        return;
+    }
+    const int fs = x << k, cs = I << (k + 1);  // sides are < 2^29, so twice them fit an int
+    const int hf = min(1 << k, n0 - fs);
+    const int hc = min(1 << (k + 1), n0 - cs);
+    const int cf2 = 2 * fs + hf, cc2 = 2 * cs + hc;  // twice the centres
     J = I;
     wJ = T(0);
     if (cf2 == cc2) return;
     const int Jn = cf2 < cc2 ? I - 1 : I + 1;
     if (Jn < 0 || Jn >= nc) return;
-    const long long js = (long long)Jn << (k + 1);
-    const long long hj = min((long long)1 << (k + 1), (long long)n0 - js);
-    const long long cj2 = 2 * js + hj;
+    const int js = Jn << (k + 1);
+    const int hj = min(1 << (k + 1), n0 - js);
+    const int cj2 = 2 * js + hj;
     J = Jn;
     wJ = T(cf2 > cc2 ? cf2 - cc2 : cc2 - cf2) / T(cj2 > cc2 ? cj2 - cc2 : cc2 - cj2);
 }
@@ -207,6 +214,7 @@ constexpr int kWaveHalo = 8;                      // x halo of a strip (cells, m
 constexpr int kWaveWidth = 128;                   // strip width: 32 lanes x 4 cells
 constexpr int kWaveIW = kWaveWidth - 2 * kWaveHalo;  // interior cells per strip
 constexpr int kTailMax = 64;                      // levels with max side <= this go to the tail
+constexpr int kWaveCoarseW = 72;                  // coarse columns staged per strip (UP)
 
 template <class T>
 struct WaveArgs {
@@ -219,6 +227,8 @@ struct WaveArgs {
     T alpha;
     T sk;
     const int* active;
+    const CUtensorMap* maps;     // per wavefront slice: u, b and the coarse output iterate
+    int* err;                    // set to 1 when a bounded wait gives up
 };
 
 template <class T>

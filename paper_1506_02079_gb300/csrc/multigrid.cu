@@ -31,6 +31,7 @@
 #include "emfuse_common.cuh"
 #include "emfuse_internal.cuh"
 #include "mg_fused.cuh"
+#include "tma.cuh"
 
 namespace emfuse {
 
@@ -282,6 +283,8 @@ struct LevelPlan {
     int64_t* d_ts = nullptr;
     LSlice<T>* d_wsl = nullptr;
     int64_t* d_is = nullptr;
+    std::vector<CUtensorMap> maps;      // per wavefront slice: u, b, coarse output iterate
+    CUtensorMap* d_maps = nullptr;
     int k = 0;
     int ch = 64;                        // wavefront rows per work item
     double cells = 0;                   // cells of this level summed over its slices
@@ -313,12 +316,13 @@ struct Solver {
     const SolveRequest& req;
     cudaStream_t st;
     std::vector<LevelPlan<TV>> levels;
-    DeviceBuffer ws_levels, ws_desc, ws_f, ws_norms, ws_active;
+    DeviceBuffer ws_levels, ws_desc, ws_f, ws_norms, ws_active, ws_err;
     std::vector<int> nlev, kc;
     int Kmax = 0, Kw = 0;       // levels, and levels with wavefront work
     TF* d = nullptr;
     double* d_norms = nullptr;
     int* d_active = nullptr;
+    int* d_err = nullptr;
     TopSlice* d_top = nullptr;
     int64_t* d_top_ts = nullptr;
     int64_t top_tiles = 0;
@@ -420,8 +424,21 @@ struct Solver {
             // rows per work item: as tall as possible while keeping ~4 waves of warps
             L.ch = 128;
             while (L.ch > 16 && want / L.ch < (int64_t)kNumSMs * 16 * 4) L.ch /= 2;
-            for (const auto& S : L.wsl)
+            for (const auto& S : L.wsl) {
                 L.item_start.push_back(L.item_start.back() + (int64_t)S.fstrips * ceil_div(S.ny, L.ch));
+                // TMA maps: rows of u and b (one 128-cell strip row per box) and the two
+                // coarse rows around a fine row for the prolongation
+                CUtensorMap mu, mb, mc;
+                EMF_TRY(encode_tensor_map_2d(&mu, S.u, sizeof(TV), S.nx, S.ny, S.pitch, kWaveWidth, 1));
+                EMF_TRY(encode_tensor_map_2d(&mb, S.b, sizeof(TV), S.nx, S.ny, S.pitch, kWaveWidth, 1));
+                if (S.uco)
+                    EMF_TRY(encode_tensor_map_2d(&mc, S.uco, sizeof(TV), S.ncx, S.ncy, S.pitchc, kWaveCoarseW, 2));
+                else
+                    mc = mu;
+                L.maps.push_back(mu);
+                L.maps.push_back(mb);
+                L.maps.push_back(mc);
+            }
         }
         // finest-level (residual kernel) tiling
         std::vector<TopSlice> top(n);
@@ -441,8 +458,9 @@ struct Solver {
                 tail_cells += (double)S.nx * S.ny;
             }
         Blob blob;
-        std::vector<size_t> pos_sl(Kmax), pos_ts(Kmax), pos_wsl(Kmax), pos_is(Kmax);
+        std::vector<size_t> pos_sl(Kmax), pos_ts(Kmax), pos_wsl(Kmax), pos_is(Kmax), pos_maps(Kmax);
         for (int k = 0; k < Kmax; ++k) {
+            pos_maps[k] = blob.add(levels[k].maps);
             pos_sl[k] = blob.add(levels[k].sl);
             pos_ts[k] = blob.add(levels[k].tile_start);
             pos_wsl[k] = blob.add(levels[k].wsl);
@@ -459,6 +477,7 @@ struct Solver {
             levels[k].d_ts = reinterpret_cast<int64_t*>(dbase + pos_ts[k]);
             levels[k].d_wsl = reinterpret_cast<LSlice<TV>*>(dbase + pos_wsl[k]);
             levels[k].d_is = reinterpret_cast<int64_t*>(dbase + pos_is[k]);
+            levels[k].d_maps = reinterpret_cast<CUtensorMap*>(dbase + pos_maps[k]);
         }
         d_top = reinterpret_cast<TopSlice*>(dbase + pos_top);
         d_top_ts = reinterpret_cast<int64_t*>(dbase + pos_top_ts);
@@ -466,6 +485,9 @@ struct Solver {
         d_norms = ws_norms.as<double>();
         EMF_TRY(ws_active.alloc(n * sizeof(int), st));
         d_active = ws_active.as<int>();
+        EMF_TRY(ws_err.alloc(sizeof(int), st));
+        d_err = ws_err.as<int>();
+        EMF_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
         tail.table = reinterpret_cast<const LSlice<TV>*>(dbase + pos_table);
         tail.level_off = reinterpret_cast<const int*>(dbase + pos_loff);
         tail.nlev = reinterpret_cast<const int*>(dbase + pos_nlev);
@@ -502,6 +524,8 @@ struct Solver {
         a.alpha = TV(req.alpha);
         a.sk = TV(std::ldexp(1.0, -2 * k));
         a.active = d_active;
+        a.maps = levels[k].d_maps;
+        a.err = d_err;
         return a;
     }
 
@@ -611,7 +635,13 @@ struct Solver {
             else rc = top_pass<To, 2>(o);
             if (rc != EMFUSE_OK) return rc;
             EMF_CUDA(cudaMemcpyAsync(norms.data(), d_norms, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+            int err_flag = 0;
+            EMF_CUDA(cudaMemcpyAsync(&err_flag, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
             EMF_CUDA(cudaStreamSynchronize(st));
+            if (err_flag) {
+                set_error("a bounded device-side wait (TMA row ring) expired");
+                return EMFUSE_ETIMEOUT;
+            }
             all_done = true;
             for (int64_t j = 0; j < n; ++j) {
                 if (done[j]) continue;

