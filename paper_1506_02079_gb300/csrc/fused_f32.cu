@@ -11,17 +11,20 @@ static int launch_wave_impl(const WaveArgs<T>& a, int S, bool zero_init, bool up
     const char* name = up ? (a.k == 0 ? "wave_up_l0" : "wave_up_coarse")
                           : (a.k == 0 ? "wave_down_l0" : "wave_down_coarse");
     KernelScope ks(name, st, bytes);
-    const int smem = kWaveWarps * fused_detail::WaveRing<T>::kWarpBytes;
-#define EMF_WAVE_ONE(KERNEL)                                                                 \
+#define EMF_WAVE_ONE(KERNEL, SMEM)                                                           \
     do {                                                                                     \
+        const int smem = SMEM;                                                               \
         cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
         KERNEL<<<grid, kWaveWarps * 32, smem, st>>>(a);                                      \
     } while (0)
 #define EMF_WAVE(SS)                                                                         \
     do {                                                                                     \
-        if (up) EMF_WAVE_ONE((fused_detail::k_wave<T, SS, false, true>));                    \
-        else if (zero_init) EMF_WAVE_ONE((fused_detail::k_wave<T, SS, true, false>));        \
-        else EMF_WAVE_ONE((fused_detail::k_wave<T, SS, false, false>));                      \
+        if (up) EMF_WAVE_ONE((fused_detail::k_wave<T, SS, false, true>),                     \
+                             (fused_detail::wave_smem_bytes<T, SS, false, true>()));         \
+        else if (zero_init) EMF_WAVE_ONE((fused_detail::k_wave<T, SS, true, false>),         \
+                                         (fused_detail::wave_smem_bytes<T, SS, true, false>())); \
+        else EMF_WAVE_ONE((fused_detail::k_wave<T, SS, false, false>),                       \
+                          (fused_detail::wave_smem_bytes<T, SS, false, false>()));           \
     } while (0)
     switch (S) {
         case 2: EMF_WAVE(2); break;

@@ -103,6 +103,21 @@ __device__ __noinline__ Coef<T> edge_row_coef(AxisCoef<T> ax, int r, int ny, int
     return make_coef<T>(ax, axis_coef<T>(r, ny, n0y, k), k, alpha, sk);
 }
 
+// Half-sweep of one colour on a non-interior row (out of line, see edge_row_coef).
+template <class T>
+__device__ __noinline__ void edge_row_update(T (&row)[4], const T (&brow)[4], const T (&nrow)[4],
+                                             const T (&srow)[4], const AxisCoef<T> (&ax)[4], int first, T west,
+                                             T east, int r, int ny, int n0y, int k, T alpha, T sk) {
+    const AxisCoef<T> ay = axis_coef<T>(r, ny, n0y, k);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = 2 * h + first;
+        const T uw = i == 0 ? west : row[i - 1];
+        const T ue = i == 3 ? east : row[i + 1];
+        row[i] = gs_update<T>(make_coef<T>(ax[i], ay, k, alpha, sk), brow[i], uw, ue, nrow[i], srow[i]);
+    }
+}
+
 // Prolongation for lanes whose cells do not follow the interior 1/4-3/4 pattern.
 template <class T>
 __device__ __noinline__ void prolong_generic(T (&uu)[4], const T (&v0)[4], const T (&v1)[4], const int (&oI)[4],
@@ -115,21 +130,32 @@ __device__ __noinline__ void prolong_generic(T (&uu)[4], const T (&v0)[4], const
     }
 }
 
-// Shared-memory ring of one warp: NB slots, each holding one row of u and b of the strip
-// (128 cells) and, for the prolongation leg, the two coarse rows around it.
-template <class T>
+// Shared-memory ring of one warp: one slot per row from the oldest row still needed (the
+// residual row, S + 1 behind the newest) to the newest row in flight (kAhead - 1 ahead).  A
+// slot holds the strip's row of u and b (128 cells) and, for the prolongation leg, the two
+// coarse rows around it.  b is read from the ring when a half-sweep needs it; u moves into a
+// register window when its row arrives.
+template <class T, int S, bool ZERO, bool UP>
 struct WaveRing {
-    static constexpr int kNB = 4;                                    // rows in flight
+    static constexpr int kAhead = 4;                                 // rows in flight
+    static constexpr int kNB = kAhead + S + 2;                       // b slots (and barriers)
     static constexpr int kRowBytes = kWaveWidth * (int)sizeof(T);
-    static constexpr int kCoarseBytes = (kWaveCoarseW * 2 * (int)sizeof(T) + 127) / 128 * 128;
-    static constexpr int kSlotBytes = 2 * kRowBytes + kCoarseBytes;
-    static constexpr int kWarpBytes = kNB * kSlotBytes + 128;        // + the slot barriers
+    static constexpr int kCoarseBytes = UP ? (kWaveCoarseW * 2 * (int)sizeof(T) + 127) / 128 * 128 : 0;
+    // u and the coarse rows are consumed when their row arrives: kAhead slots suffice
+    static constexpr int kUSlotBytes = (ZERO ? 0 : kRowBytes) + kCoarseBytes;
+    static constexpr int kBRingBytes = kNB * kRowBytes;
+    static constexpr int kURingBytes = kAhead * kUSlotBytes;
+    static constexpr int kWarpBytes = kBRingBytes + kURingBytes + (kNB * 8 + 127) / 128 * 128;
 };
 
 template <class T, int S, bool ZERO, bool UP>
+constexpr int wave_smem_bytes() { return kWaveWarps * WaveRing<T, S, ZERO, UP>::kWarpBytes; }
+
+template <class T, int S, bool ZERO, bool UP>
 __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(WaveArgs<T> a) {
-    using R = WaveRing<T>;
+    using R = WaveRing<T, S, ZERO, UP>;
     constexpr int NB = R::kNB;
+    constexpr int AHEAD = R::kAhead;
     constexpr int NR = UP ? S + 2 : S + 3;  // window: rows t-NR+1 .. t, slot NR-1 = row t
     extern __shared__ __align__(128) unsigned char wave_smem[];
     const int lane = threadIdx.x & 31;
@@ -192,9 +218,11 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     }
 
     // ---- shared-memory ring and its barriers
-    unsigned char* ring = wave_smem + (size_t)warp * R::kWarpBytes;
+    unsigned char* ring = wave_smem + (size_t)warp * R::kWarpBytes;   // b rows
+    unsigned char* uring = ring + R::kBRingBytes;                       // u row + coarse rows
     const uint32_t ring_s = smem_addr(ring);
-    const uint32_t bar_s = ring_s + NB * R::kSlotBytes;
+    const uint32_t uring_s = ring_s + R::kBRingBytes;
+    const uint32_t bar_s = uring_s + R::kURingBytes;
     if (lane == 0) {
         for (int s = 0; s < NB; ++s) mbar_init(bar_s + 8 * s, 1);
         mbar_init_fence();
@@ -204,7 +232,8 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     // issue the TMA loads of row t into its slot (lane 0 only)
     auto issue = [&](int t) {
         const int slot = (t - tb) % NB;
-        const uint32_t base = ring_s + slot * R::kSlotBytes, bar = bar_s + 8 * slot;
+        const uint32_t bdst = ring_s + slot * kRowB, bar = bar_s + 8 * slot;
+        const uint32_t udst = uring_s + ((t - tb) % AHEAD) * R::kUSlotBytes;
         const bool coarse = has_coarse && t >= 0 && t < L.ny;
         uint32_t bytes = kRowB + (ZERO ? 0u : kRowB);
         int y0c = 0;
@@ -217,18 +246,27 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
         }
         fence_proxy_async();
         mbar_expect_tx(bar, bytes);
-        tma_load_2d(base + kRowB, map_b, X0, t, bar);
-        if (!ZERO) tma_load_2d(base, map_u, X0, t, bar);
-        if (coarse) tma_load_2d(base + 2 * kRowB, map_c, cbox_x, y0c, bar);
+        tma_load_2d(bdst, map_b, X0, t, bar);
+        if (!ZERO) tma_load_2d(udst, map_u, X0, t, bar);
+        if (coarse) tma_load_2d(udst + (ZERO ? 0 : kRowB), map_c, cbox_x, y0c, bar);
     };
     if (lane == 0)
-        for (int p = 0; p < NB && tb + p <= te; ++p) issue(tb + p);
+        for (int p = 0; p < AHEAD && tb + p <= te; ++p) issue(tb + p);
 
-    T u[NR][4], b[NR][4];
+    T u[NR][4];
 #pragma unroll
     for (int r = 0; r < NR; ++r)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) { u[r][i] = T(0); b[r][i] = T(0); }
+        for (int i = 0; i < 4; ++i) u[r][i] = T(0);
+    // b of row t - d lives in ring slot (t - d - tb) mod NB; rows before tb read as zero
+    auto brow_of = [&](int rr, T (&v)[4]) {
+        if (rr < tb) {
+            v[0] = v[1] = v[2] = v[3] = T(0);
+        } else {
+            const T* bb = reinterpret_cast<const T*>(ring + ((rr - tb) % NB) * kRowB);
+            Vec4<T>::load(bb + 4 * lane, v);
+        }
+    };
     T rsum[2] = {T(0), T(0)};  // restriction partial sums (DOWN)
 
 #pragma unroll 1
@@ -239,7 +277,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
         if (!mbar_wait_warp(bar, (n / NB) & 1)) {
             // give up: flag the host, let the copies already issued land, leave
             if (lane == 0) atomicExch(a.err, 1);
-            for (int tt = t + 1; tt <= te && tt < t + NB; ++tt)
+            for (int tt = t + 1; tt <= te && tt < t + AHEAD; ++tt)
                 mbar_wait_warp(bar_s + 8 * ((tt - tb) % NB), ((tt - tb) / NB) & 1);
             return;
         }
@@ -247,12 +285,10 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
 #pragma unroll
         for (int r = 0; r < NR - 1; ++r)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) { u[r][i] = u[r + 1][i]; b[r][i] = b[r + 1][i]; }
-        const unsigned char* sl_ptr = ring + slot * R::kSlotBytes;
+            for (int i = 0; i < 4; ++i) u[r][i] = u[r + 1][i];
+        const unsigned char* sl_ptr = uring + (n % AHEAD) * R::kUSlotBytes;
         {
             const T* ub = reinterpret_cast<const T*>(sl_ptr);
-            const T* bb = reinterpret_cast<const T*>(sl_ptr + kRowB);
-            Vec4<T>::load(bb + 4 * lane, b[NR - 1]);
             if (ZERO) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) u[NR - 1][i] = T(0);
@@ -266,7 +302,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
             T wy;
             interp_axis<T>(t, L.n0y, k, L.ncy, Iy, Jy, wy);
             const int y0c = min(Iy, Jy);
-            const T* cb = reinterpret_cast<const T*>(sl_ptr + 2 * kRowB);
+            const T* cb = reinterpret_cast<const T*>(sl_ptr + (ZERO ? 0 : kRowB));
             const T* c0 = cb + (Iy - y0c) * kWaveCoarseW + 2 * lane + 3;  // column cx0 - 1
             const T* c1 = cb + (Jy - y0c) * kWaveCoarseW + 2 * lane + 3;
             const T v0[4] = {c0[0], c0[1], c0[2], c0[3]};
@@ -284,9 +320,9 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                 }
             }
         }
-        // the slot is consumed: refill it with row t + NB
+        // refill the slot of row t + AHEAD - NB (whose b is no longer needed) with row t + AHEAD
         __syncwarp();
-        if (lane == 0 && t + NB <= te) issue(t + NB);
+        if (lane == 0 && t + AHEAD <= te) issue(t + AHEAD);
 
         // half-sweeps: stage s updates row t - s (window slot NR-1-s) with colour (s - 1) & 1
 #pragma unroll
@@ -296,34 +332,30 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
             T(&row)[4] = u[NR - 1 - s];
             const T(&nrow)[4] = u[NR - 2 - s];
             const T(&srow)[4] = u[NR - s];
-            const T(&brow)[4] = b[NR - 1 - s];
+            T brow[4];
+            brow_of(r, brow);
             const int color = (s - 1) & 1;
             const int first = (xlane + r + color) & 1;  // first cell index with this colour
             const T west = __shfl_up_sync(0xffffffffu, row[3], 1);   // cell 3 of lane-1
             const T east = __shfl_down_sync(0xffffffffu, row[0], 1);  // cell 0 of lane+1
-            if (!lane_in) continue;
+            // Cells outside the level (x < 0 or x >= nx) are updated too: their coefficients
+            // decouple them (zero faces), in-level cells give them zero weight, and they are
+            // never written back, so no per-cell bounds test is needed.
             const bool irow = interior_row(r, L.ny, k);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            if (irow) {
                 if (first == 0) {  // cells 0 and 2
-                    const int i = 2 * h;
-                    if (xlane + i < L.nx) {
-                        const T uw = (i == 0) ? west : row[i - 1];
-                        const T ue = row[i + 1];
-                        const Coef<T> c = irow ? interior_row_coef<T>(ax[i], k, sk, dint[i], idint[i])
-                                               : edge_row_coef<T>(ax[i], r, L.ny, L.n0y, k, alpha, sk);
-                        row[i] = gs_update<T>(c, brow[i], uw, ue, nrow[i], srow[i]);
-                    }
+                    row[0] = gs_update<T>(interior_row_coef<T>(ax[0], k, sk, dint[0], idint[0]), brow[0], west,
+                                          row[1], nrow[0], srow[0]);
+                    row[2] = gs_update<T>(interior_row_coef<T>(ax[2], k, sk, dint[2], idint[2]), brow[2], row[1],
+                                          row[3], nrow[2], srow[2]);
                 } else {           // cells 1 and 3
-                    const int i = 2 * h + 1;
-                    if (xlane + i < L.nx) {
-                        const T uw = row[i - 1];
-                        const T ue = (i == 3) ? east : row[i + 1];
-                        const Coef<T> c = irow ? interior_row_coef<T>(ax[i], k, sk, dint[i], idint[i])
-                                               : edge_row_coef<T>(ax[i], r, L.ny, L.n0y, k, alpha, sk);
-                        row[i] = gs_update<T>(c, brow[i], uw, ue, nrow[i], srow[i]);
-                    }
+                    row[1] = gs_update<T>(interior_row_coef<T>(ax[1], k, sk, dint[1], idint[1]), brow[1], row[0],
+                                          row[2], nrow[1], srow[1]);
+                    row[3] = gs_update<T>(interior_row_coef<T>(ax[3], k, sk, dint[3], idint[3]), brow[3], row[2],
+                                          east, nrow[3], srow[3]);
                 }
+            } else {
+                edge_row_update<T>(row, brow, nrow, srow, ax, first, west, east, r, L.ny, L.n0y, k, alpha, sk);
             }
         }
         // output of the row that completed all half-sweeps
@@ -351,6 +383,8 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                 const bool row_in = r < L.ny && lane_in;
                 T res[4] = {T(0), T(0), T(0), T(0)};
                 if (row_in) {
+                    T brow[4];
+                    brow_of(r, brow);
                     const bool irow = interior_row(r, L.ny, k);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -358,7 +392,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                         const T ue = i == 3 ? east : rrow[i + 1];
                         const Coef<T> c = irow ? interior_row_coef<T>(ax[i], k, sk, dint[i], idint[i])
                                                : edge_row_coef<T>(ax[i], r, L.ny, L.n0y, k, alpha, sk);
-                        res[i] = residual_at<T>(c, b[1][i], rrow[i], uw, ue, u[0][i], u[2][i]);
+                        res[i] = residual_at<T>(c, brow[i], rrow[i], uw, ue, u[0][i], u[2][i]);
                     }
                 }
                 // same summation order as the reference restriction:

@@ -53,6 +53,12 @@ struct AxisCoef {
 template <class T>
 __device__ __forceinline__ AxisCoef<T> axis_coef(int i, int n, int n0, int k) {
     AxisCoef<T> a;
+    if (i < 0 || i >= n) {  // outside the level: a finite, decoupled cell (never written back)
+        a.w = T(1);
+        a.gm = T(0);
+        a.gp = T(0);
+        return a;
+    }
     if (k == 0) {
         a.w = T(1);
         a.gm = i > 0 ? T(1) : T(0);

@@ -174,7 +174,9 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
     const float af = float(alpha);
     // alpha + deg for deg = 1..4, selected without indexing (deg 0 only for 1 x 1 slices)
     const TF ad1 = TF(alpha) + TF(1), ad2 = TF(alpha) + TF(2), ad3 = TF(alpha) + TF(3), ad4 = TF(alpha) + TF(4);
-    double rr = 0.0, bb = 0.0;
+    // squared norms: FP32 partial sums over a warp's 128 cells, FP64 from there on (per-block
+    // sums, per-slice atomics); this keeps the FP64 pipe for the residual itself
+    float rrf = 0.f, bbf = 0.f;
     const int ly = tid / 16;
     const int y = ty0 + ly;
 #pragma unroll
@@ -187,7 +189,7 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
         float bc;
         if (rhs) {
             bc = rhs[p];
-            if (MODE == 0) bb = fma(double(bc), double(bc), bb);
+            if (MODE == 0) bbf = fmaf(bc, bc, bbf);
         } else {
             const float sv = s[p], ov = float(o[p]);
             bc = af * (sv - ov);
@@ -199,7 +201,7 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
                 if (hn) lo += ov - float(o[p - G.nx]);
                 if (hs) lo += ov - float(o[p + G.nx]);
                 const float b = fmaf(af, sv, lo);
-                bb = fma(double(b), double(b), bb);
+                bbf = fmaf(b, b, bbf);
             }
         }
         TF r;
@@ -214,17 +216,18 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
             r = TF(bc) - Ad;
             if (MODE == 1) d[p] = c;
         }
-        r0[(int64_t)y * G.pitch0 + x] = TV(r);
-        const double rd = double(r);
-        rr = fma(rd, rd, rr);
+        const TV rv = TV(r);
+        r0[(int64_t)y * G.pitch0 + x] = rv;
+        const float rf = float(rv);
+        rrf = fmaf(rf, rf, rrf);
     }
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) {
-        rr += __shfl_xor_sync(0xffffffffu, rr, m);
-        if (MODE == 0) bb += __shfl_xor_sync(0xffffffffu, bb, m);
+        rrf += __shfl_xor_sync(0xffffffffu, rrf, m);
+        if (MODE == 0) bbf += __shfl_xor_sync(0xffffffffu, bbf, m);
     }
     __shared__ double red[2][8];
-    if ((tid & 31) == 0) { red[0][tid >> 5] = rr; red[1][tid >> 5] = bb; }
+    if ((tid & 31) == 0) { red[0][tid >> 5] = double(rrf); red[1][tid >> 5] = double(bbf); }
     __syncthreads();
     if (tid == 0) {
         double r2 = 0.0, b2 = 0.0;
