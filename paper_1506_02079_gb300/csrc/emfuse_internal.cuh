@@ -10,6 +10,9 @@
 
 namespace emfuse {
 
+// ---- device error word set by kernels whose bounded waits expire (runtime.cu)
+int* device_error_flag();
+
 // ---- smoothing (smooth.cu)
 int support_radius(float sigma);
 std::vector<float> gaussian_taps(float sigma, int R);

@@ -319,7 +319,7 @@ struct Solver {
     const SolveRequest& req;
     cudaStream_t st;
     std::vector<LevelPlan<TV>> levels;
-    DeviceBuffer ws_levels, ws_desc, ws_f, ws_norms, ws_active, ws_err;
+    DeviceBuffer ws_levels, ws_desc, ws_f, ws_norms, ws_active;
     std::vector<int> nlev, kc;
     int Kmax = 0, Kw = 0;       // levels, and levels with wavefront work
     TF* d = nullptr;
@@ -488,9 +488,11 @@ struct Solver {
         d_norms = ws_norms.as<double>();
         EMF_TRY(ws_active.alloc(n * sizeof(int), st));
         d_active = ws_active.as<int>();
-        EMF_TRY(ws_err.alloc(sizeof(int), st));
-        d_err = ws_err.as<int>();
-        EMF_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+        d_err = device_error_flag();
+        if (!d_err) {
+            set_error("could not allocate the device error word");
+            return EMFUSE_ECUDA;
+        }
         tail.table = reinterpret_cast<const LSlice<TV>*>(dbase + pos_table);
         tail.level_off = reinterpret_cast<const int*>(dbase + pos_loff);
         tail.nlev = reinterpret_cast<const int*>(dbase + pos_nlev);
@@ -642,7 +644,9 @@ struct Solver {
             EMF_CUDA(cudaMemcpyAsync(&err_flag, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
             EMF_CUDA(cudaStreamSynchronize(st));
             if (err_flag) {
-                set_error("a bounded device-side wait (TMA row ring) expired");
+                cudaMemsetAsync(d_err, 0, sizeof(int), st);
+                cudaStreamSynchronize(st);
+                set_error("a bounded device-side wait (TMA staging) expired");
                 return EMFUSE_ETIMEOUT;
             }
             all_done = true;

@@ -55,6 +55,28 @@ int encode_tensor_map_2d(CUtensorMap* out, const void* base, int elem_bytes, int
     return EMFUSE_OK;
 }
 
+int encode_tensor_map_3d(CUtensorMap* out, const void* base, int elem_bytes, int64_t nx, int64_t ny,
+                         int64_t nz, int64_t pitch, int box_x, int box_y) {
+    auto fn = tensor_map_encoder();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled is not available from the CUDA driver");
+        return EMFUSE_ECUDA;
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)(pitch * elem_bytes), (cuuint64_t)(pitch * ny * elem_bytes)};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(out, elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                          const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled (3-D) failed with CUresult " + std::to_string((int)r));
+        return EMFUSE_ECUDA;
+    }
+    return EMFUSE_OK;
+}
+
 namespace {
 std::atomic<uint64_t> g_launches{0};
 std::atomic<bool> g_profiling{false};
@@ -96,6 +118,23 @@ KernelScope::~KernelScope() {
         std::lock_guard<std::mutex> lk(g_mu);
         g_recs.push_back(Rec{name_, a_, b_, bytes_});
     }
+}
+
+// One int per device, allocated on first use and kept for the life of the process: kernels
+// whose bounded waits give up set it; solves read and clear it when they synchronise.
+int* device_error_flag() {
+    static std::mutex mu;
+    static int* flags[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!flags[dev]) {
+        int* p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+        flags[dev] = p;
+    }
+    return flags[dev];
 }
 
 }  // namespace emfuse

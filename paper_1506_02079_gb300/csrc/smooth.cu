@@ -2,8 +2,14 @@
 // (Sec. 3 "Anisotropic Smoothing"), with the Gaussian cut off beyond three standard deviations
 // (Sec. 3 "Implementation") and the weights renormalised over the taps inside the stack.
 //
-// Two implementations:
-//   * smooth_fused_kernel: one HBM pass.  A CTA owns a 64x16 xy-tile and marches along z.
+// Three implementations:
+//   * smooth_tma_kernel (default): one HBM pass.  A CTA owns a 64x16 xy-tile and marches
+//     along z.  Input planes (tile plus xy halo) arrive by TMA bulk tensor copies into two
+//     shared-memory buffers, the next plane in flight while the current one is blurred; the
+//     hardware zero-fills the halo outside the stack.  x then y blur from shared memory with
+//     vector loads, then a 19-plane register ring along z (rotated, so the march stays a
+//     small rolled loop).  Needs rows whose byte pitch is a multiple of 16.
+//   * smooth_fused_kernel: the same data flow with plain loads, for any pitch.
 //     Each input plane is staged in shared memory with its xy halo, blurred in x then y,
 //     and pushed into a per-thread ring of the last P planes held in registers; the z-blur of
 //     the plane R behind is emitted from the ring.  The ring index is a compile-time constant
@@ -20,6 +26,7 @@
 
 #include "emfuse_common.cuh"
 #include "emfuse_internal.cuh"
+#include "tma.cuh"
 
 namespace emfuse {
 
@@ -130,6 +137,155 @@ smooth_fused_kernel(const Tin* __restrict__ in, float* __restrict__ out, int nx,
                 }
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------- TMA-staged kernel
+template <class Tin, int R>
+struct SmTile {
+    static constexpr int HX = sizeof(Tin) == 1 ? 16 : 4;  // staged columns left of the tile
+    static constexpr int BX = kTX + 2 * HX;                // x-start stays 16-byte aligned
+    static constexpr int BY = kTY + 2 * R;
+    static constexpr int kPlaneBytes = BX * BY * (int)sizeof(Tin);
+    static constexpr int kPlaneStride = (kPlaneBytes + 127) / 128 * 128;  // TMA destinations 128-B aligned
+};
+
+template <class Tin>
+__device__ __forceinline__ void load_word(const Tin* p, float (&v)[4]);
+template <>
+__device__ __forceinline__ void load_word<float>(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void load_word<uint8_t>(const uint8_t* p, float (&v)[4]) {
+    const uchar4 q = *reinterpret_cast<const uchar4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+
+template <class Tin, int R>
+__global__ void __launch_bounds__(kThreads, 2)
+smooth_tma_kernel(const __grid_constant__ CUtensorMap map, float* __restrict__ out, int nx, int ny, int nz,
+                  int64_t pitch, int z0, int z1, const float* __restrict__ inv_nx,
+                  const float* __restrict__ inv_ny, const float* __restrict__ inv_nz, SmoothParams prm,
+                  int* __restrict__ err) {
+    using G = SmTile<Tin, R>;
+    constexpr int P = 19;  // z ring: supports floor(3 sigma_z) <= 9
+    __shared__ __align__(128) unsigned char s_raw[2 * G::kPlaneStride];
+    __shared__ __align__(16) float s_x[G::BY][kTX];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int Rz = prm.Rz;
+    const int zin_lo = max(0, z0 - Rz), zin_hi = min(nz, z1 + Rz), zi_end = z1 + Rz;
+    const uint32_t bar[2] = {smem_addr(&s_bar[0]), smem_addr(&s_bar[1])};
+    if (tid == 0) {
+        mbar_init(bar[0], 1);
+        mbar_init(bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int zi) {  // thread 0: plane zi into buffer (zi - zin_lo) & 1
+        const int bf = (zi - zin_lo) & 1;
+        fence_proxy_async();
+        mbar_expect_tx(bar[bf], G::kPlaneBytes);
+        tma_load_3d(smem_addr(s_raw + bf * G::kPlaneStride), &map, x0 - G::HX, y0 - R, zi, bar[bf]);
+    };
+    if (tid == 0 && zin_lo < zin_hi) issue(zin_lo);
+
+    float w[2 * R + 1];
+#pragma unroll
+    for (int d = 0; d < 2 * R + 1; ++d) w[d] = prm.wxy[d];
+    const int tx = tid % 16, ty = tid / 16;
+    const int gy = y0 + ty;
+    const float iny = inv_ny[min(gy, ny - 1)];
+    float ring[P][4];
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ring[q][i] = 0.f;
+    const int64_t plane = pitch * (int64_t)ny;
+
+#pragma unroll 1
+    for (int zi = zin_lo; zi < zi_end; ++zi) {
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (zi < zin_hi) {
+            const int bf = (zi - zin_lo) & 1;
+            if (tid == 0 && zi + 1 < zin_hi) issue(zi + 1);
+            bool ok = false;
+            for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(bar[bf], ((zi - zin_lo) >> 1) & 1);
+            if (!__syncthreads_and(ok)) {
+                // give up: flag the host, let the copy in flight land, leave
+                if (tid == 0) {
+                    atomicExch(err, 1);
+                    if (zi + 1 < zin_hi)
+                        for (int it = 0; it < kWaitLimit; ++it)
+                            if (mbar_try_wait(bar[bf ^ 1], ((zi + 1 - zin_lo) >> 1) & 1)) break;
+                }
+                __syncthreads();
+                return;
+            }
+            // x blur: (row, group of 4 columns) items; the span of a group is 3 aligned words
+            const Tin(*s_in)[G::BX] = reinterpret_cast<const Tin(*)[G::BX]>(s_raw + bf * G::kPlaneStride);
+            for (int item = tid; item < G::BY * 16; item += kThreads) {
+                const int r = item >> 4, g = item & 15;
+                float s0[4], s1[4], s2[4];
+                load_word<Tin>(&s_in[r][4 * g + G::HX - 4], s0);
+                load_word<Tin>(&s_in[r][4 * g + G::HX], s1);
+                load_word<Tin>(&s_in[r][4 * g + G::HX + 4], s2);
+                const float s[12] = {s0[0], s0[1], s0[2], s0[3], s1[0], s1[1], s1[2], s1[3],
+                                     s2[0], s2[1], s2[2], s2[3]};
+                float o[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int d = -R; d <= R; ++d) acc = fmaf(w[d + R], s[4 + i + d], acc);
+                    o[i] = acc * inv_nx[min(x0 + 4 * g + i, nx - 1)];
+                }
+                *reinterpret_cast<float4*>(&s_x[r][4 * g]) = make_float4(o[0], o[1], o[2], o[3]);
+            }
+            __syncthreads();
+            // y blur of this thread's 4 columns on row ty
+#pragma unroll
+            for (int d = -R; d <= R; ++d) {
+                const float4 q = *reinterpret_cast<const float4*>(&s_x[ty + R + d][4 * tx]);
+                v[0] = fmaf(w[d + R], q.x, v[0]);
+                v[1] = fmaf(w[d + R], q.y, v[1]);
+                v[2] = fmaf(w[d + R], q.z, v[2]);
+                v[3] = fmaf(w[d + R], q.w, v[3]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] *= iny;
+        }
+        // push into the z ring (slot P-1 = plane zi) and emit plane zi - Rz
+#pragma unroll
+        for (int q = 0; q < P - 1; ++q)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ring[q][i] = ring[q + 1][i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ring[P - 1][i] = v[i];
+        const int zo = zi - Rz;
+        if (zo >= z0 && zo < z1 && gy < ny) {
+            float o4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int jj = 0; jj < P; ++jj) {
+                const float wz = prm.wz[jj];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) o4[i] = fmaf(wz, ring[P - 1 - jj][i], o4[i]);
+            }
+            const float inz = inv_nz[zo];
+            float* dst = out + (int64_t)(zo - z0) * plane + (int64_t)gy * pitch + x0 + 4 * tx;
+            const int gx = x0 + 4 * tx;
+            if (gx + 3 < nx && (pitch & 3) == 0) {
+                *reinterpret_cast<float4*>(dst) = make_float4(o4[0] * inz, o4[1] * inz, o4[2] * inz, o4[3] * inz);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (gx + i < nx) dst[i] = o4[i] * inz;
+            }
+        }
+        __syncthreads();  // s_x and the input buffer of plane zi are reused
     }
 }
 
@@ -248,6 +404,49 @@ int smooth_stack(const void* in, int dt, float* out, int64_t nx, int64_t ny, int
     const float* inv_y = inv_x + nx;
     const float* inv_z = inv_y + ny;
 
+    const size_t esz = dt == EMFUSE_U8 ? 1 : 4;
+    const bool tma_ok = Rxy <= 4 && Rz <= 9 && force_path == 0 && (pitch * (int64_t)esz) % 16 == 0 &&
+                        (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+    if (tma_ok) {
+        SmoothParams prm{};
+        prm.Rxy = Rxy;
+        prm.Rz = Rz;
+        for (int d = 0; d < 2 * Rxy + 1; ++d) prm.wxy[d] = wxy[d];
+        for (int j = 0; j < 2 * Rz + 1; ++j) prm.wz[j] = wz[2 * Rz - j];
+        CUtensorMap map;
+        const int hx = dt == EMFUSE_U8 ? 16 : 4;
+        EMF_TRY(encode_tensor_map_3d(&map, in, (int)esz, nx, ny, nz, pitch, kTX + 2 * hx, kTY + 2 * Rxy));
+        int* err = device_error_flag();
+        if (!err) {
+            set_error("could not allocate the device error word");
+            return EMFUSE_ECUDA;
+        }
+        dim3 grid((unsigned)ceil_div(nx, kTX), (unsigned)ceil_div(ny, kTY));
+        const int64_t zin0 = std::max<int64_t>(0, z0 - Rz), zin1 = std::min<int64_t>(nz, z1 + Rz);
+        {
+            KernelScope ks("smooth_tma", st, (double)nx * ny * ((zin1 - zin0) * (double)esz + (z1 - z0) * 4.0));
+#define EMF_SMOOTH_TMA(RR)                                                                         \
+    do {                                                                                           \
+        if (dt == EMFUSE_U8)                                                                       \
+            smooth_tma_kernel<uint8_t, RR><<<grid, kThreads, 0, st>>>(map, out, (int)nx, (int)ny, (int)nz, \
+                pitch, (int)z0, (int)z1, inv_x, inv_y, inv_z, prm, err);              \
+        else                                                                                       \
+            smooth_tma_kernel<float, RR><<<grid, kThreads, 0, st>>>(map, out, (int)nx, (int)ny, (int)nz, \
+                pitch, (int)z0, (int)z1, inv_x, inv_y, inv_z, prm, err);              \
+    } while (0)
+            switch (Rxy) {
+                case 0: EMF_SMOOTH_TMA(0); break;
+                case 1: EMF_SMOOTH_TMA(1); break;
+                case 2: EMF_SMOOTH_TMA(2); break;
+                case 3: EMF_SMOOTH_TMA(3); break;
+                default: EMF_SMOOTH_TMA(4); break;
+            }
+#undef EMF_SMOOTH_TMA
+            EMF_CHECK_LAUNCH();
+        }
+        // a timed-out wait is reported by the next call that synchronises (the solves)
+        return EMFUSE_OK;
+    }
     const bool fused_ok = Rxy <= kMaxRxy && Rz <= 9 && force_path != 1;
     if (fused_ok) {
         SmoothParams prm{};
@@ -284,7 +483,6 @@ int smooth_stack(const void* in, int dt, float* out, int64_t nx, int64_t ny, int
     DeviceBuffer t1, t2;
     EMF_TRY(t1.alloc((size_t)(nzin * ny * nx) * sizeof(float), st));
     EMF_TRY(t2.alloc((size_t)(nzin * ny * nx) * sizeof(float), st));
-    const size_t esz = dt == EMFUSE_U8 ? 1 : 4;
     const void* in0 = (const char*)in + (size_t)(zin0 * ny * pitch) * esz;
     EMF_TRY(launch_axis(in0, dt, t1.as<float>(), (int)nx, (int)ny, (int)nzin, pitch, nx, 0, wxy,
                         nullptr, inv_x, 0.f, st));

@@ -17,6 +17,10 @@ namespace emfuse {
 // box_x x box_y elements; out-of-range elements read as zero.
 int encode_tensor_map_2d(CUtensorMap* out, const void* base, int elem_bytes, int64_t nx, int64_t ny,
                          int64_t pitch, int box_x, int box_y);
+// 3-D tensor map over a stack of nz planes of ny rows (row pitch `pitch` elements), element
+// type uint8 (elem_bytes 1) or float32 (4); boxes of box_x x box_y x 1.
+int encode_tensor_map_3d(CUtensorMap* out, const void* base, int elem_bytes, int64_t nx, int64_t ny,
+                         int64_t nz, int64_t pitch, int box_x, int box_y);
 
 // ---------------------------------------------------------------- device
 constexpr int kWaitLimit = 1 << 20;
@@ -72,6 +76,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
 }
 
