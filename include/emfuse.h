@@ -67,7 +67,10 @@ typedef struct {
     int precision;       /* emfuse_precision.  Default EMFUSE_PREC_MIXED.                  */
     int fused;           /* 1: fused wavefront kernels on large levels; 0: one kernel per
                             half-sweep (reference schedule).  Default 1.                   */
-    int reserved[6];     /* must be zero                                                   */
+    int first_vcycles;   /* V-cycles in the first outer iteration (the second continues from
+                            the first's correction in FP32 before the first FP64 residual).
+                            0 = default (2).                                               */
+    int reserved[5];     /* must be zero                                                   */
 } emfuse_solve_opts;
 
 /* Per-slice result of a solve. */

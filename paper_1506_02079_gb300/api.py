@@ -46,7 +46,7 @@ class EmfuseUnavailable(RuntimeError):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_vcycles", ctypes.c_int), ("nu_pre", ctypes.c_int),
                 ("nu_post", ctypes.c_int), ("precision", ctypes.c_int), ("fused", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("first_vcycles", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class SliceStats(ctypes.Structure):

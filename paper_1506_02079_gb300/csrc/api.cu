@@ -31,6 +31,8 @@ static int resolve_opts(const emfuse_solve_opts* in, emfuse_solve_opts* out) {
         return einval("opts.nu_pre / nu_post must be in [0, 8] with at least one sweep");
     if (out->precision < EMFUSE_PREC_FP32 || out->precision > EMFUSE_PREC_FP64)
         return einval("opts.precision must be EMFUSE_PREC_FP32, _MIXED or _FP64");
+    if (out->first_vcycles == 0) out->first_vcycles = 2;
+    if (out->first_vcycles < 1 || out->first_vcycles > 8) return einval("opts.first_vcycles must be in [1, 8]");
     return EMFUSE_OK;
 }
 
@@ -91,6 +93,7 @@ void emfuse_default_opts(emfuse_solve_opts* o) {
     o->nu_post = 2;
     o->precision = EMFUSE_PREC_MIXED;
     o->fused = 1;
+    o->first_vcycles = 2;
 }
 
 const char* emfuse_last_error(void) { return last_error(); }

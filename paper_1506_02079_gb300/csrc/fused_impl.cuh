@@ -138,7 +138,8 @@ __device__ __noinline__ void prolong_generic(T (&uu)[4], const T (&v0)[4], const
 template <class T, int S, bool ZERO, bool UP>
 struct WaveRing {
     static constexpr int kAhead = 4;                                 // rows in flight
-    static constexpr int kNB = kAhead + S + 2;                       // b slots (and barriers)
+    static constexpr int kNB = 16;                                   // b slots (and barriers)
+    static_assert(kAhead + S + 2 <= kNB, "b ring too short for the half-sweep window");
     static constexpr int kRowBytes = kWaveWidth * (int)sizeof(T);
     static constexpr int kCoarseBytes = UP ? (kWaveCoarseW * 2 * (int)sizeof(T) + 127) / 128 * 128 : 0;
     // u and the coarse rows are consumed when their row arrives: kAhead slots suffice
@@ -165,9 +166,9 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     const int j = find_item(a.item_start, a.nsl, item);
     const LSlice<T> L = a.sl[j];
     if (a.active && !a.active[L.slice]) return;
-    const CUtensorMap* map_u = a.maps + 3 * j;
-    const CUtensorMap* map_b = map_u + 1;
-    const CUtensorMap* map_c = map_u + 2;
+    const CUtensorMap* map_b = a.maps + 4 * j + 1;
+    const CUtensorMap* map_c = a.maps + 4 * j + 2;
+    const CUtensorMap* map_u = a.maps + 4 * j + a.u_map;
     const int li = int(item - a.item_start[j]);
     const int strip = li % L.fstrips;
     const int chunk = li / L.fstrips;
@@ -218,8 +219,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     }
 
     // ---- shared-memory ring and its barriers
-    unsigned char* ring = wave_smem + (size_t)warp * R::kWarpBytes;   // b rows
-    unsigned char* uring = ring + R::kBRingBytes;                       // u row + coarse rows
+    unsigned char* ring = wave_smem + (size_t)warp * R::kWarpBytes;   // b rows, then u row + coarse rows
     const uint32_t ring_s = smem_addr(ring);
     const uint32_t uring_s = ring_s + R::kBRingBytes;
     const uint32_t bar_s = uring_s + R::kURingBytes;
@@ -231,9 +231,9 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     constexpr uint32_t kRowB = R::kRowBytes;
     // issue the TMA loads of row t into its slot (lane 0 only)
     auto issue = [&](int t) {
-        const int slot = (t - tb) % NB;
+        const int slot = (t - tb) & (NB - 1);
         const uint32_t bdst = ring_s + slot * kRowB, bar = bar_s + 8 * slot;
-        const uint32_t udst = uring_s + ((t - tb) % AHEAD) * R::kUSlotBytes;
+        const uint32_t udst = uring_s + ((t - tb) & (AHEAD - 1)) * R::kUSlotBytes;
         const bool coarse = has_coarse && t >= 0 && t < L.ny;
         uint32_t bytes = kRowB + (ZERO ? 0u : kRowB);
         int y0c = 0;
@@ -263,8 +263,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
         if (rr < tb) {
             v[0] = v[1] = v[2] = v[3] = T(0);
         } else {
-            const T* bb = reinterpret_cast<const T*>(ring + ((rr - tb) % NB) * kRowB);
-            Vec4<T>::load(bb + 4 * lane, v);
+            lds4(ring_s + ((rr - tb) & (NB - 1)) * kRowB + 4 * lane * (uint32_t)sizeof(T), v);
         }
     };
     T rsum[2] = {T(0), T(0)};  // restriction partial sums (DOWN)
@@ -272,13 +271,13 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
 #pragma unroll 1
     for (int t = tb; t <= te; ++t) {
         const int n = t - tb;
-        const int slot = n % NB;
+        const int slot = n & (NB - 1);
         const uint32_t bar = bar_s + 8 * slot;
         if (!mbar_wait_warp(bar, (n / NB) & 1)) {
             // give up: flag the host, let the copies already issued land, leave
             if (lane == 0) atomicExch(a.err, 1);
             for (int tt = t + 1; tt <= te && tt < t + AHEAD; ++tt)
-                mbar_wait_warp(bar_s + 8 * ((tt - tb) % NB), ((tt - tb) / NB) & 1);
+                mbar_wait_warp(bar_s + 8 * ((tt - tb) & (NB - 1)), ((tt - tb) / NB) & 1);
             return;
         }
         // shift the window and bring in row t
@@ -286,15 +285,12 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
         for (int r = 0; r < NR - 1; ++r)
 #pragma unroll
             for (int i = 0; i < 4; ++i) u[r][i] = u[r + 1][i];
-        const unsigned char* sl_ptr = uring + (n % AHEAD) * R::kUSlotBytes;
-        {
-            const T* ub = reinterpret_cast<const T*>(sl_ptr);
-            if (ZERO) {
+        const uint32_t us_addr = uring_s + (n & (AHEAD - 1)) * R::kUSlotBytes;
+        if (ZERO) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) u[NR - 1][i] = T(0);
-            } else {
-                Vec4<T>::load(ub + 4 * lane, u[NR - 1]);
-            }
+            for (int i = 0; i < 4; ++i) u[NR - 1][i] = T(0);
+        } else {
+            lds4(us_addr + 4 * lane * (uint32_t)sizeof(T), u[NR - 1]);
         }
         // UP: add the interpolated coarse correction to row t
         if (has_coarse && t >= 0 && t < L.ny) {
@@ -302,11 +298,13 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
             T wy;
             interp_axis<T>(t, L.n0y, k, L.ncy, Iy, Jy, wy);
             const int y0c = min(Iy, Jy);
-            const T* cb = reinterpret_cast<const T*>(sl_ptr + (ZERO ? 0 : kRowB));
-            const T* c0 = cb + (Iy - y0c) * kWaveCoarseW + 2 * lane + 3;  // column cx0 - 1
-            const T* c1 = cb + (Jy - y0c) * kWaveCoarseW + 2 * lane + 3;
-            const T v0[4] = {c0[0], c0[1], c0[2], c0[3]};
-            const T v1[4] = {c1[0], c1[1], c1[2], c1[3]};
+            const uint32_t cb = us_addr + (ZERO ? 0 : kRowB);
+            const uint32_t c0 = cb + ((Iy - y0c) * kWaveCoarseW + 2 * lane + 3) * (uint32_t)sizeof(T);  // col cx0-1
+            const uint32_t c1 = cb + ((Jy - y0c) * kWaveCoarseW + 2 * lane + 3) * (uint32_t)sizeof(T);
+            const T v0[4] = {lds1(c0, T(0)), lds1(c0 + sizeof(T), T(0)), lds1(c0 + 2 * sizeof(T), T(0)),
+                             lds1(c0 + 3 * sizeof(T), T(0))};
+            const T v1[4] = {lds1(c1, T(0)), lds1(c1 + sizeof(T), T(0)), lds1(c1 + 2 * sizeof(T), T(0)),
+                             lds1(c1 + 3 * sizeof(T), T(0))};
             if (lane_in) {
                 T(&row)[4] = u[NR - 1];
                 if (std_lane && xlane + 3 < L.nx) {
@@ -452,11 +450,13 @@ __global__ void __launch_bounds__(512) k_tail(TailArgs<T> a) {
     for (int k = kc; k <= K; ++k) {
         const LSlice<T> L = lv[k];
         const T sk = T(ldexp(1.0, -2 * k));
-        for (int p = threadIdx.x; p < L.nx * L.ny; p += blockDim.x) {
-            const int y = p / L.nx, x = p - y * L.nx;
-            L.u[(int64_t)y * L.pitch + x] = T(0);
+        if (!(a.cont && k == 0)) {  // coarse levels solve for a correction from zero
+            for (int p = threadIdx.x; p < L.nx * L.ny; p += blockDim.x) {
+                const int y = p / L.nx, x = p - y * L.nx;
+                L.u[(int64_t)y * L.pitch + x] = T(0);
+            }
+            __syncthreads();
         }
-        __syncthreads();
         tail_relax<T>(L, k, a.alpha, sk, a.nu_pre);
         if (k < K) {
             const LSlice<T> C = lv[k + 1];

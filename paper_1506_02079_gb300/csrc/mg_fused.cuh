@@ -233,7 +233,9 @@ struct WaveArgs {
     T alpha;
     T sk;
     const int* active;
-    const CUtensorMap* maps;     // per wavefront slice: u, b and the coarse output iterate
+    const CUtensorMap* maps;     // per wavefront slice: u, b, coarse output iterate, uo
+    int u_map;                   // map the initial u is read from: 0 (u) or 3 (uo, to continue
+                                 // from the previous V-cycle's result)
     int* err;                    // set to 1 when a bounded wait gives up
 };
 
@@ -247,6 +249,7 @@ struct TailArgs {
     T alpha;
     int nu_pre, nu_post;
     const int* active;
+    int cont;                    // 1: a slice whose tail starts at level 0 continues from u
 };
 
 template <class T>

@@ -181,7 +181,7 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
     const int y = ty0 + ly;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const int lx = 4 * (tid % 16) + i;
+        const int lx = (tid % 16) + 16 * i;  // consecutive threads, consecutive cells
         const int x = tx0 + lx;
         if (x >= G.nx || y >= G.ny) continue;
         const int64_t p = G.off + (int64_t)y * G.nx + x;
@@ -254,7 +254,7 @@ k_update(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_star
     if (y >= G.ny) return;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const int x = tx0 + 4 * (threadIdx.x % 16) + i;
+        const int x = tx0 + (threadIdx.x % 16) + 16 * i;
         if (x >= G.nx) continue;
         const int64_t p = G.off + (int64_t)y * G.nx + x;
         d[p] = d[p] + TF(e[(int64_t)y * G.pitch0 + x]);
@@ -438,9 +438,12 @@ struct Solver {
                     EMF_TRY(encode_tensor_map_2d(&mc, S.uco, sizeof(TV), S.ncx, S.ncy, S.pitchc, kWaveCoarseW, 2));
                 else
                     mc = mu;
+                CUtensorMap mo;
+                EMF_TRY(encode_tensor_map_2d(&mo, S.uo, sizeof(TV), S.nx, S.ny, S.pitch, kWaveWidth, 1));
                 L.maps.push_back(mu);
                 L.maps.push_back(mb);
                 L.maps.push_back(mc);
+                L.maps.push_back(mo);
             }
         }
         // finest-level (residual kernel) tiling
@@ -502,6 +505,7 @@ struct Solver {
         tail.nu_pre = req.opts.nu_pre;
         tail.nu_post = req.opts.nu_post;
         tail.active = d_active;
+        tail.cont = 0;
         EMF_CUDA(cudaStreamSynchronize(st));  // the host staging blob goes out of scope
         return EMFUSE_OK;
     }
@@ -530,6 +534,7 @@ struct Solver {
         a.sk = TV(std::ldexp(1.0, -2 * k));
         a.active = d_active;
         a.maps = levels[k].d_maps;
+        a.u_map = 0;
         a.err = d_err;
         return a;
     }
@@ -549,11 +554,12 @@ struct Solver {
     }
 
     // Reference schedule: one kernel per half-sweep, restriction and prolongation.
-    int vcycle_reference() {
+    // cont = continue from the level-0 iterate of the previous V-cycle instead of zero.
+    int vcycle_reference(bool cont) {
         const int nu1 = req.opts.nu_pre, nu2 = req.opts.nu_post;
-        // level-0 iterate starts at zero
-        for (const auto& S : levels[0].sl)
-            EMF_CUDA(cudaMemsetAsync(S.u, 0, (size_t)S.pitch * S.ny * sizeof(TV), st));
+        if (!cont)
+            for (const auto& S : levels[0].sl)
+                EMF_CUDA(cudaMemsetAsync(S.u, 0, (size_t)S.pitch * S.ny * sizeof(TV), st));
         for (int k = 0; k < Kmax; ++k) {
             EMF_TRY(relax(k, nu1));
             if (k + 1 < Kmax) {
@@ -578,15 +584,21 @@ struct Solver {
     }
 
     // Fused schedule: wavefront DOWN on large levels, one coarse-tail kernel, wavefront UP.
-    int vcycle_fused() {
+    // cont = continue from the previous V-cycle's level-0 result (read from uo).
+    int vcycle_fused(bool cont) {
         const int S1 = 2 * req.opts.nu_pre, S2 = 2 * req.opts.nu_post;
         for (int k = 0; k < Kw; ++k) {
             const auto& L = levels[k];
-            // reads b, writes u and the coarse rhs
-            const double bytes = sizeof(TV) * (2.0 * L.wcells + 0.25 * L.wcells);
-            EMF_TRY(launch_wave<TV>(wargs(k), S1, true, false, st, bytes));
+            const bool from_prev = cont && k == 0;
+            // reads b (and u when continuing), writes u and the coarse rhs
+            const double bytes = sizeof(TV) * ((from_prev ? 3.0 : 2.0) * L.wcells + 0.25 * L.wcells);
+            WaveArgs<TV> a = wargs(k);
+            a.u_map = from_prev ? 3 : 0;
+            EMF_TRY(launch_wave<TV>(a, S1, !from_prev, false, st, bytes));
         }
-        EMF_TRY(launch_tail<TV>(tail, st, sizeof(TV) * 2.0 * tail_cells));
+        TailArgs<TV> ta = tail;
+        ta.cont = cont ? 1 : 0;  // slices that start in the tail continue from their level-0 u
+        EMF_TRY(launch_tail<TV>(ta, st, sizeof(TV) * 2.0 * tail_cells));
         for (int k = Kw - 1; k >= 0; --k) {
             const auto& L = levels[k];
             // reads u, b and the coarse iterate, writes u
@@ -631,6 +643,7 @@ struct Solver {
         EMF_CUDA(cudaMemcpyAsync(d_active, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
         EMF_CUDA(cudaMemsetAsync(d_norms, 0, 2 * n * sizeof(double), st));
         const int maxit = std::max(0, req.opts.max_vcycles);
+        int vdone = 0;
         bool all_done = false;
         int rc = EMFUSE_OK;
         for (int it = 0;; ++it) {
@@ -662,11 +675,17 @@ struct Solver {
                     all_done = false;
                 }
             }
-            if (all_done || it >= maxit) break;
+            if (all_done || vdone >= maxit) break;
             EMF_CUDA(cudaMemcpyAsync(d_active, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
-            EMF_TRY(fused ? vcycle_fused() : vcycle_reference());
-            for (int64_t j = 0; j < n; ++j)
-                if (active[j]) ++vcycles[j];
+            // the first outer iteration runs first_vcycles V-cycles in FP32, each continuing
+            // from the previous one's correction, before the first FP64 residual
+            const int nv = it == 0 ? std::min(req.opts.first_vcycles, maxit - vdone) : 1;
+            for (int v = 0; v < nv; ++v) {
+                EMF_TRY(fused ? vcycle_fused(v > 0) : vcycle_reference(v > 0));
+                for (int64_t j = 0; j < n; ++j)
+                    if (active[j]) ++vcycles[j];
+            }
+            vdone += nv;
         }
         // Slices that converged at the first residual kept d = 0; the others hold d in the
         // d buffer, except in MODE 1/2 only active slices were written.  Slices done at it == 0
