@@ -6,7 +6,7 @@
 
 #include <string>
 
-#include "../../include/emfuse.h"
+#include "emfuse.h"  // from include/ (-I)
 
 namespace emfuse {
 

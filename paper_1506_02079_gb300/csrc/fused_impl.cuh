@@ -81,7 +81,7 @@ struct Vec2<double> {
     }
 };
 
-constexpr int kWaveWarps = 8;
+constexpr int kWaveWarps = 4;  // warps (strips) per CTA
 
 
 __host__ __device__ constexpr int wmod(int a, int w) { return ((a % w) + w) % w; }
@@ -92,29 +92,39 @@ __device__ __forceinline__ T pick4(const T (&v)[4], int i) {
     return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3]));
 }
 
-// FP32 kernels keep two CTAs per SM; FP64 windows need twice the registers.
+// CTAs per SM the register budget is sized for (FP64 windows take twice the registers).
 template <class T>
-struct WaveOcc { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
+struct WaveOcc { static constexpr int value = sizeof(T) == 4 ? 4 : 2; };
 
-// Stencil of a cell on a non-interior row (slice edge, partial coarse cell): rare, so kept
-// out of line to keep the march small enough for the instruction cache.
+// Half-sweep of one colour for a lane on a boundary row or with a boundary cell: per-cell
+// stencils (rare, so kept out of line to keep the march small).
 template <class T>
-__device__ __noinline__ Coef<T> edge_row_coef(AxisCoef<T> ax, int r, int ny, int n0y, int k, T alpha, T sk) {
-    return make_coef<T>(ax, axis_coef<T>(r, ny, n0y, k), k, alpha, sk);
-}
-
-// Half-sweep of one colour on a non-interior row (out of line, see edge_row_coef).
-template <class T>
-__device__ __noinline__ void edge_row_update(T (&row)[4], const T (&brow)[4], const T (&nrow)[4],
-                                             const T (&srow)[4], const AxisCoef<T> (&ax)[4], int first, T west,
-                                             T east, int r, int ny, int n0y, int k, T alpha, T sk) {
+__device__ __noinline__ void edge_update(T (&row)[4], const T (&brow)[4], const T (&nrow)[4], const T (&srow)[4],
+                                         int first, T west, T east, int xlane, int r, int nx, int ny, int n0x,
+                                         int n0y, int k, T alpha, T sk) {
     const AxisCoef<T> ay = axis_coef<T>(r, ny, n0y, k);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int i = 2 * h + first;
         const T uw = i == 0 ? west : row[i - 1];
         const T ue = i == 3 ? east : row[i + 1];
-        row[i] = gs_update<T>(make_coef<T>(ax[i], ay, k, alpha, sk), brow[i], uw, ue, nrow[i], srow[i]);
+        const Coef<T> c = make_coef<T>(axis_coef<T>(xlane + i, nx, n0x, k), ay, k, alpha, sk);
+        row[i] = gs_update<T>(c, brow[i], uw, ue, nrow[i], srow[i]);
+    }
+}
+
+// Residuals of a lane's 4 cells with per-cell stencils (boundary lanes and rows).
+template <class T>
+__device__ __noinline__ void edge_residual(T (&res)[4], const T (&rrow)[4], const T (&brow)[4], const T (&nrow)[4],
+                                           const T (&srow)[4], T west, T east, int xlane, int r, int nx, int ny,
+                                           int n0x, int n0y, int k, T alpha, T sk) {
+    const AxisCoef<T> ay = axis_coef<T>(r, ny, n0y, k);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const T uw = i == 0 ? west : rrow[i - 1];
+        const T ue = i == 3 ? east : rrow[i + 1];
+        const Coef<T> c = make_coef<T>(axis_coef<T>(xlane + i, nx, n0x, k), ay, k, alpha, sk);
+        res[i] = residual_at<T>(c, brow[i], rrow[i], uw, ue, nrow[i], srow[i]);
     }
 }
 
@@ -137,7 +147,7 @@ __device__ __noinline__ void prolong_generic(T (&uu)[4], const T (&v0)[4], const
 // register window when its row arrives.
 template <class T, int S, bool ZERO, bool UP>
 struct WaveRing {
-    static constexpr int kAhead = 4;                                 // rows in flight
+    static constexpr int kAhead = sizeof(T) == 4 ? 8 : 4;            // rows in flight
     static constexpr int kNB = 16;                                   // b slots (and barriers)
     static_assert(kAhead + S + 2 <= kNB, "b ring too short for the half-sweep window");
     static constexpr int kRowBytes = kWaveWidth * (int)sizeof(T);
@@ -184,16 +194,17 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     const int xlane = X0 + 4 * lane;
     const bool lane_in = xlane >= 0 && xlane < L.nx;  // X0 is a multiple of 4: all-or-none
     const bool interior_lane = lane >= kWaveHalo / 4 && lane < 32 - kWaveHalo / 4;
-    AxisCoef<T> ax[4];
-    T dint[4], idint[4];  // diagonal and its reciprocal on interior rows
+    // Interior cells (full cells with full neighbours) all share one stencil: the values
+    // make_coef returns for them, computed once.  xint: all 4 cells of the lane are interior
+    // along x; rows are checked with interior_row.
+    AxisCoef<T> one;
+    one.w = T(1); one.gm = T(1); one.gp = T(1);
+    const Coef<T> ci = make_coef<T>(one, one, k, alpha, sk);
+    bool xint = true;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        ax[i] = axis_coef<T>(xlane + i, L.nx, L.n0x, k);
-        AxisCoef<T> one;
-        one.w = T(1); one.gm = T(1); one.gp = T(1);
-        const Coef<T> c = make_coef<T>(ax[i], one, k, alpha, sk);
-        dint[i] = c.D;
-        idint[i] = c.iD;
+        const AxisCoef<T> q = axis_coef<T>(xlane + i, L.nx, L.n0x, k);
+        xint = xint && q.w == T(1) && q.gm == T(1) && q.gp == T(1);
     }
 
     // prolongation geometry along x (UP): coarse columns cx0-1 .. cx0+2 around the lane
@@ -244,7 +255,9 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
             y0c = min(Iy, Jy);
             bytes += kWaveCoarseW * 2 * (uint32_t)sizeof(T);
         }
-        fence_proxy_async();
+        // No proxy fence here: the u/coarse slot being refilled was read (LDS) and its values
+        // consumed before the __syncwarp that precedes this issue, and the b slot was last
+        // read NB - AHEAD - S - 1 >= 5 rows ago.
         mbar_expect_tx(bar, bytes);
         tma_load_2d(bdst, map_b, X0, t, bar);
         if (!ZERO) tma_load_2d(udst, map_u, X0, t, bar);
@@ -339,21 +352,17 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
             // Cells outside the level (x < 0 or x >= nx) are updated too: their coefficients
             // decouple them (zero faces), in-level cells give them zero weight, and they are
             // never written back, so no per-cell bounds test is needed.
-            const bool irow = interior_row(r, L.ny, k);
-            if (irow) {
+            if (xint && interior_row(r, L.ny, k)) {
                 if (first == 0) {  // cells 0 and 2
-                    row[0] = gs_update<T>(interior_row_coef<T>(ax[0], k, sk, dint[0], idint[0]), brow[0], west,
-                                          row[1], nrow[0], srow[0]);
-                    row[2] = gs_update<T>(interior_row_coef<T>(ax[2], k, sk, dint[2], idint[2]), brow[2], row[1],
-                                          row[3], nrow[2], srow[2]);
+                    row[0] = gs_update<T>(ci, brow[0], west, row[1], nrow[0], srow[0]);
+                    row[2] = gs_update<T>(ci, brow[2], row[1], row[3], nrow[2], srow[2]);
                 } else {           // cells 1 and 3
-                    row[1] = gs_update<T>(interior_row_coef<T>(ax[1], k, sk, dint[1], idint[1]), brow[1], row[0],
-                                          row[2], nrow[1], srow[1]);
-                    row[3] = gs_update<T>(interior_row_coef<T>(ax[3], k, sk, dint[3], idint[3]), brow[3], row[2],
-                                          east, nrow[3], srow[3]);
+                    row[1] = gs_update<T>(ci, brow[1], row[0], row[2], nrow[1], srow[1]);
+                    row[3] = gs_update<T>(ci, brow[3], row[2], east, nrow[3], srow[3]);
                 }
             } else {
-                edge_row_update<T>(row, brow, nrow, srow, ax, first, west, east, r, L.ny, L.n0y, k, alpha, sk);
+                edge_update<T>(row, brow, nrow, srow, first, west, east, xlane, r, L.nx, L.ny, L.n0x, L.n0y, k,
+                               alpha, sk);
             }
         }
         // output of the row that completed all half-sweeps
@@ -383,14 +392,14 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                 if (row_in) {
                     T brow[4];
                     brow_of(r, brow);
-                    const bool irow = interior_row(r, L.ny, k);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const T uw = i == 0 ? west : rrow[i - 1];
-                        const T ue = i == 3 ? east : rrow[i + 1];
-                        const Coef<T> c = irow ? interior_row_coef<T>(ax[i], k, sk, dint[i], idint[i])
-                                               : edge_row_coef<T>(ax[i], r, L.ny, L.n0y, k, alpha, sk);
-                        res[i] = residual_at<T>(c, brow[i], rrow[i], uw, ue, u[0][i], u[2][i]);
+                    if (xint && interior_row(r, L.ny, k)) {
+                        res[0] = residual_at<T>(ci, brow[0], rrow[0], west, rrow[1], u[0][0], u[2][0]);
+                        res[1] = residual_at<T>(ci, brow[1], rrow[1], rrow[0], rrow[2], u[0][1], u[2][1]);
+                        res[2] = residual_at<T>(ci, brow[2], rrow[2], rrow[1], rrow[3], u[0][2], u[2][2]);
+                        res[3] = residual_at<T>(ci, brow[3], rrow[3], rrow[2], east, u[0][3], u[2][3]);
+                    } else {
+                        edge_residual<T>(res, rrow, brow, u[0], u[2], west, east, xlane, r, L.nx, L.ny, L.n0x,
+                                         L.n0y, k, alpha, sk);
                     }
                 }
                 // same summation order as the reference restriction:
