@@ -1,19 +1,20 @@
 // Fused multigrid schedule.
 //
 // Wavefront kernel (k_wave).  One warp owns a strip of 128 cells (32 lanes x 4 consecutive
-// cells) and marches down a chunk of rows.  All nu red-black sweeps are pipelined in one
-// pass: at step t the warp loads row t and applies half-sweep s (s = 1..S, S = 2 nu) to row
-// t - s.  Half-sweep s only reads the other colour, whose latest update (half-sweep s - 1)
-// reached rows t-s-1 .. t-s+1 before half-sweep s + 1 touches them, so the result is exactly
-// that of S global half-sweeps (Gauss-Seidel red-black, colour (x + y) mod 2).  The rows in
-// flight live in registers (a window of S + 3 rows plus the prefetch distance); the window is
-// indexed with compile-time slots by unrolling the march by the window length.  Neighbours
-// along x come from warp shuffles, so the strip edges are recomputed by the adjacent strips
-// (8-cell overlap on each side).
+// cells) and marches down a chunk of rows two at a time.  All nu red-black sweeps are
+// pipelined in one pass: at step T the warp receives row pair T (rows 2T, 2T+1) and applies
+// half-sweep s (s = 1..S, S = 2 nu) to pair T - s.  Half-sweep s only reads the other colour,
+// whose latest update (half-sweep s - 1) reached pairs T-s-1 .. T-s+1 before half-sweep s + 1
+// touches them, so the result is exactly that of S global half-sweeps (Gauss-Seidel
+// red-black, colour (x + y) mod 2).  Row pairs arrive by TMA (one 128 x 2 box per array) into
+// a per-warp shared-memory ring guarded by mbarriers with bounded waits; u moves into a
+// register window of S + 3 pairs, b is read from the ring when a half-sweep needs it.
+// Neighbours along x come from warp shuffles, so strip edges are recomputed by the adjacent
+// strips (8-cell overlap on each side).
 //
 //   DOWN (restriction leg): optional zero initial guess (the first half-sweep then needs no
-//        load of u), S half-sweeps, the residual of the row S + 1 behind, and the 2x2 sum /4
-//        of residual pairs written as the next level's right-hand side.  One read of b
+//        load of u), S half-sweeps, the residual of the pair S + 1 behind, and its 2x2 sums / 4
+//        written as one row of the next level's right-hand side.  One read of b
 //        (and u), one write of u and of the coarse rhs per cell.
 //   UP   (prolongation leg): the interpolated coarse correction is added as each row
 //        arrives, then S half-sweeps; one read of u, b and the coarse iterate, one write of
@@ -96,42 +97,107 @@ __device__ __forceinline__ T pick4(const T (&v)[4], int i) {
 template <class T>
 struct WaveOcc { static constexpr int value = sizeof(T) == 4 ? 4 : 2; };
 
-// Half-sweep of one colour for a lane on a boundary row or with a boundary cell: per-cell
-// stencils (rare, so kept out of line to keep the march small).
+// ---------------------------------------------------------------- per-cell stencils
+// Interior cells (full cells with full neighbours) all share one stencil.  Cells on a slice
+// edge, a partial coarse cell or outside the level take per-cell stencils: cheap selects at
+// level 0 (degree 2..4, reciprocals tabulated once per kernel), the general finite-volume
+// formula out of line on coarse levels.
 template <class T>
-__device__ __noinline__ void edge_update(T (&row)[4], const T (&brow)[4], const T (&nrow)[4], const T (&srow)[4],
-                                         int first, T west, T east, int xlane, int r, int nx, int ny, int n0x,
-                                         int n0y, int k, T alpha, T sk) {
-    const AxisCoef<T> ay = axis_coef<T>(r, ny, n0y, k);
+struct StencilTab {
+    Coef<T> ci;   // interior stencil
+    T d[5], id[5];  // level 0: alpha + deg and its reciprocal, deg = 0..4
+};
+
+template <class T>
+__device__ __forceinline__ void make_stencil_tab(StencilTab<T>& tab, int k, T alpha, T sk) {
+    AxisCoef<T> one;
+    one.w = T(1); one.gm = T(1); one.gp = T(1);
+    tab.ci = make_coef<T>(one, one, k, alpha, sk);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int i = 2 * h + first;
-        const T uw = i == 0 ? west : row[i - 1];
-        const T ue = i == 3 ? east : row[i + 1];
-        const Coef<T> c = make_coef<T>(axis_coef<T>(xlane + i, nx, n0x, k), ay, k, alpha, sk);
-        row[i] = gs_update<T>(c, brow[i], uw, ue, nrow[i], srow[i]);
+    for (int q = 0; q < 5; ++q) {
+        tab.d[q] = alpha + T(q);  // = alpha + (((cw + ce) + cn) + cs) for 0/1 coefficients
+        tab.id[q] = rcp_t(tab.d[q]);
     }
 }
 
-// Residuals of a lane's 4 cells with per-cell stencils (boundary lanes and rows).
 template <class T>
-__device__ __noinline__ void edge_residual(T (&res)[4], const T (&rrow)[4], const T (&brow)[4], const T (&nrow)[4],
-                                           const T (&srow)[4], T west, T east, int xlane, int r, int nx, int ny,
-                                           int n0x, int n0y, int k, T alpha, T sk) {
-    const AxisCoef<T> ay = axis_coef<T>(r, ny, n0y, k);
+__device__ __forceinline__ T pick5(const T (&v)[5], int i) {
+    return i <= 1 ? (i == 0 ? v[0] : v[1]) : (i == 2 ? v[2] : (i == 3 ? v[3] : v[4]));
+}
+
+// Level-0 stencil of cell (x, r) from selects; equal to make_coef at level 0.
+template <class T>
+__device__ __forceinline__ Coef<T> level0_coef(const StencilTab<T>& tab, int x, int r, int nx, int ny) {
+    Coef<T> c;
+    const bool in = x >= 0 && x < nx && r >= 0 && r < ny;
+    const int w = in && x > 0, e = in && x + 1 < nx, n = in && r > 0, s = in && r + 1 < ny;
+    c.cw = T(w); c.ce = T(e); c.cn = T(n); c.cs = T(s);
+    const int deg = w + e + n + s;
+    if (in) {
+        c.D = pick5<T>(tab.d, deg);
+        c.iD = pick5<T>(tab.id, deg);
+    } else {  // outside the level: decoupled (the w = 1 cell of axis_coef) -> D = alpha
+        c.D = tab.d[0];
+        c.iD = tab.id[0];
+    }
+    return c;
+}
+
+template <class T>
+__device__ __noinline__ Coef<T> coarse_cell_coef(int x, int r, int nx, int ny, int n0x, int n0y, int k, T alpha,
+                                                 T sk) {
+    return make_coef<T>(axis_coef<T>(x, nx, n0x, k), axis_coef<T>(r, ny, n0y, k), k, alpha, sk);
+}
+
+template <class T>
+__device__ __forceinline__ Coef<T> edge_coef(const StencilTab<T>& tab, int x, int r, int nx, int ny, int n0x,
+                                             int n0y, int k, T alpha, T sk) {
+    return k == 0 ? level0_coef<T>(tab, x, r, nx, ny) : coarse_cell_coef<T>(x, r, nx, ny, n0x, n0y, k, alpha, sk);
+}
+
+// Half-sweep of one colour on one row of the lane's 4 cells (cells f and f + 2).
+template <class T>
+__device__ __forceinline__ void sweep_row(T (&row)[4], const T (&brow)[4], const T (&nrow)[4], const T (&srow)[4],
+                                          int f, T west, T east, bool fast, const StencilTab<T>& tab, int xlane,
+                                          int r, int nx, int ny, int n0x, int n0y, int k, T alpha, T sk) {
+    if (fast) {
+        if (f == 0) {
+            row[0] = gs_update<T>(tab.ci, brow[0], west, row[1], nrow[0], srow[0]);
+            row[2] = gs_update<T>(tab.ci, brow[2], row[1], row[3], nrow[2], srow[2]);
+        } else {
+            row[1] = gs_update<T>(tab.ci, brow[1], row[0], row[2], nrow[1], srow[1]);
+            row[3] = gs_update<T>(tab.ci, brow[3], row[2], east, nrow[3], srow[3]);
+        }
+    } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = 2 * h + f;
+            const T uw = i == 0 ? west : row[i - 1];
+            const T ue = i == 3 ? east : row[i + 1];
+            const Coef<T> c = edge_coef<T>(tab, xlane + i, r, nx, ny, n0x, n0y, k, alpha, sk);
+            row[i] = gs_update<T>(c, brow[i], uw, ue, nrow[i], srow[i]);
+        }
+    }
+}
+
+// Residuals of one row of the lane's 4 cells.
+template <class T>
+__device__ __forceinline__ void residual_row(T (&res)[4], const T (&row)[4], const T (&brow)[4], const T (&nrow)[4],
+                                             const T (&srow)[4], T west, T east, bool fast, const StencilTab<T>& tab,
+                                             int xlane, int r, int nx, int ny, int n0x, int n0y, int k, T alpha, T sk) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const T uw = i == 0 ? west : rrow[i - 1];
-        const T ue = i == 3 ? east : rrow[i + 1];
-        const Coef<T> c = make_coef<T>(axis_coef<T>(xlane + i, nx, n0x, k), ay, k, alpha, sk);
-        res[i] = residual_at<T>(c, brow[i], rrow[i], uw, ue, nrow[i], srow[i]);
+        const T uw = i == 0 ? west : row[i - 1];
+        const T ue = i == 3 ? east : row[i + 1];
+        const Coef<T> c = fast ? tab.ci : edge_coef<T>(tab, xlane + i, r, nx, ny, n0x, n0y, k, alpha, sk);
+        res[i] = residual_at<T>(c, brow[i], row[i], uw, ue, nrow[i], srow[i]);
     }
 }
 
 // Prolongation for lanes whose cells do not follow the interior 1/4-3/4 pattern.
 template <class T>
-__device__ __noinline__ void prolong_generic(T (&uu)[4], const T (&v0)[4], const T (&v1)[4], const int (&oI)[4],
-                                             const int (&oJ)[4], const T (&cwx)[4], T wy, int xlane, int nx) {
+__device__ __forceinline__ void prolong_generic(T (&uu)[4], const T (&v0)[4], const T (&v1)[4], const int (&oI)[4],
+                                                const int (&oJ)[4], const T (&cwx)[4], T wy, int xlane, int nx) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         if (xlane + i >= nx) continue;
@@ -140,21 +206,17 @@ __device__ __noinline__ void prolong_generic(T (&uu)[4], const T (&v0)[4], const
     }
 }
 
-// Shared-memory ring of one warp: one slot per row from the oldest row still needed (the
-// residual row, S + 1 behind the newest) to the newest row in flight (kAhead - 1 ahead).  A
-// slot holds the strip's row of u and b (128 cells) and, for the prolongation leg, the two
-// coarse rows around it.  b is read from the ring when a half-sweep needs it; u moves into a
-// register window when its row arrives.
+// Shared-memory rings of one warp, in units of row pairs.  b: one slot per pair from the
+// oldest pair still needed (the residual pair, S + 1 behind the newest) to the newest pair in
+// flight; u and the coarse rows (UP) are consumed when their pair arrives, so kAhead slots.
 template <class T, int S, bool ZERO, bool UP>
 struct WaveRing {
-    static constexpr int kAhead = sizeof(T) == 4 ? 8 : 4;            // rows in flight
-    static constexpr int kNB = 16;                                   // b slots (and barriers)
-    static_assert(kAhead + S + 2 <= kNB, "b ring too short for the half-sweep window");
-    static constexpr int kRowBytes = kWaveWidth * (int)sizeof(T);
-    static constexpr int kCoarseBytes = UP ? (kWaveCoarseW * 2 * (int)sizeof(T) + 127) / 128 * 128 : 0;
-    // u and the coarse rows are consumed when their row arrives: kAhead slots suffice
-    static constexpr int kUSlotBytes = (ZERO ? 0 : kRowBytes) + kCoarseBytes;
-    static constexpr int kBRingBytes = kNB * kRowBytes;
+    static constexpr int kAhead = 3;                                         // pairs in flight
+    static constexpr int kNB = kAhead + S + (UP ? 1 : 2);                    // b slots = barriers
+    static constexpr int kPairBytes = 2 * kWaveWidth * (int)sizeof(T);
+    static constexpr int kCoarseBytes = UP ? (kWaveCoarseW * 3 * (int)sizeof(T) + 127) / 128 * 128 : 0;
+    static constexpr int kUSlotBytes = (ZERO ? 0 : kPairBytes) + kCoarseBytes;
+    static constexpr int kBRingBytes = kNB * kPairBytes;
     static constexpr int kURingBytes = kAhead * kUSlotBytes;
     static constexpr int kWarpBytes = kBRingBytes + kURingBytes + (kNB * 8 + 127) / 128 * 128;
 };
@@ -167,7 +229,9 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     using R = WaveRing<T, S, ZERO, UP>;
     constexpr int NB = R::kNB;
     constexpr int AHEAD = R::kAhead;
-    constexpr int NR = UP ? S + 2 : S + 3;  // window: rows t-NR+1 .. t, slot NR-1 = row t
+    constexpr int NR = UP ? S + 2 : S + 3;      // window: pairs T-NR+1 .. T (slot NR-1 = pair T)
+    constexpr int HP = UP ? (S + 1) / 2 : (S + 2) / 2;  // halo pairs above the chunk
+    constexpr uint32_t kRowB = kWaveWidth * sizeof(T);
     extern __shared__ __align__(128) unsigned char wave_smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -183,33 +247,30 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     const int strip = li % L.fstrips;
     const int chunk = li / L.fstrips;
     const int X0 = strip * kWaveIW - kWaveHalo;
-    const int Y0 = chunk * a.ch;
+    const int Y0 = chunk * a.ch;                  // even
     const int Y1 = min(Y0 + a.ch, L.ny);
-    const int Y1e = Y1 + (Y1 & 1);                 // residual rows run to an even end
-    const int tb = Y0 - (UP ? S : S + 1);          // first row of the march
-    const int te = UP ? Y1 - 1 + S : Y1e + S;      // last row (each row is loaded once)
+    const int P0 = Y0 >> 1, P1 = (Y1 + 1) >> 1;   // output pairs [P0, P1)
+    const int pb = P0 - HP;                       // first pair of the march
+    const int te = UP ? P1 - 1 + S : P1 + S;      // last pair (each pair is loaded once)
     const int k = a.k;
     const T alpha = a.alpha, sk = a.sk;
+    const int nx = L.nx, ny = L.ny;
 
     const int xlane = X0 + 4 * lane;
-    const bool lane_in = xlane >= 0 && xlane < L.nx;  // X0 is a multiple of 4: all-or-none
+    const bool lane_in = xlane >= 0 && xlane < nx;  // X0 is a multiple of 4: all-or-none
     const bool interior_lane = lane >= kWaveHalo / 4 && lane < 32 - kWaveHalo / 4;
-    // Interior cells (full cells with full neighbours) all share one stencil: the values
-    // make_coef returns for them, computed once.  xint: all 4 cells of the lane are interior
-    // along x; rows are checked with interior_row.
-    AxisCoef<T> one;
-    one.w = T(1); one.gm = T(1); one.gp = T(1);
-    const Coef<T> ci = make_coef<T>(one, one, k, alpha, sk);
-    bool xint = true;
+    StencilTab<T> tab;
+    make_stencil_tab<T>(tab, k, alpha, sk);
+    bool xint = true;  // all 4 cells of the lane interior along x
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const AxisCoef<T> q = axis_coef<T>(xlane + i, L.nx, L.n0x, k);
+        const AxisCoef<T> q = axis_coef<T>(xlane + i, nx, L.n0x, k);
         xint = xint && q.w == T(1) && q.gm == T(1) && q.gp == T(1);
     }
 
     // prolongation geometry along x (UP): coarse columns cx0-1 .. cx0+2 around the lane
     const int cx0 = X0 / 2 + 2 * lane;
-    const int cbox_x = X0 / 2 - 4;  // first coarse column staged (a multiple of 2 elements x 16 B)
+    const int cbox_x = X0 / 2 - 4;  // first staged coarse column (x * size stays 16-B aligned)
     int oI[4], oJ[4];
     T cwx[4];
     bool std_lane = true;  // interior pattern: J = I-1, I+1, I-1, I+1 with weight 1/4
@@ -229,202 +290,210 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                    cwx[2] == T(0.25) && cwx[3] == T(0.25);
     }
 
-    // ---- shared-memory ring and its barriers
-    unsigned char* ring = wave_smem + (size_t)warp * R::kWarpBytes;   // b rows, then u row + coarse rows
+    // ---- rings and barriers
+    unsigned char* ring = wave_smem + (size_t)warp * R::kWarpBytes;
     const uint32_t ring_s = smem_addr(ring);
     const uint32_t uring_s = ring_s + R::kBRingBytes;
     const uint32_t bar_s = uring_s + R::kURingBytes;
     if (lane == 0) {
-        for (int s = 0; s < NB; ++s) mbar_init(bar_s + 8 * s, 1);
+        for (int q = 0; q < NB; ++q) mbar_init(bar_s + 8 * q, 1);
         mbar_init_fence();
     }
     __syncwarp();
-    constexpr uint32_t kRowB = R::kRowBytes;
-    // issue the TMA loads of row t into its slot (lane 0 only)
-    auto issue = [&](int t) {
-        const int slot = (t - tb) & (NB - 1);
-        const uint32_t bdst = ring_s + slot * kRowB, bar = bar_s + 8 * slot;
-        const uint32_t udst = uring_s + ((t - tb) & (AHEAD - 1)) * R::kUSlotBytes;
-        const bool coarse = has_coarse && t >= 0 && t < L.ny;
-        uint32_t bytes = kRowB + (ZERO ? 0u : kRowB);
-        int y0c = 0;
-        if (coarse) {
-            int Iy, Jy;
-            T wy;
-            interp_axis<T>(t, L.n0y, k, L.ncy, Iy, Jy, wy);
-            y0c = min(Iy, Jy);
-            bytes += kWaveCoarseW * 2 * (uint32_t)sizeof(T);
-        }
-        // No proxy fence here: the u/coarse slot being refilled was read (LDS) and its values
-        // consumed before the __syncwarp that precedes this issue, and the b slot was last
-        // read NB - AHEAD - S - 1 >= 5 rows ago.
+    // TMA loads of pair P (lane 0): b (and u) rows 2P, 2P+1; coarse rows P-1 .. P+1 (UP)
+    auto issue = [&](int P, int bslot, int uslot) {
+        const uint32_t bar = bar_s + 8 * bslot;
+        const uint32_t udst = uring_s + uslot * R::kUSlotBytes;
+        const bool coarse = has_coarse && 2 * P < ny && 2 * P + 1 >= 0;
+        const uint32_t bytes = R::kPairBytes + (ZERO ? 0u : (uint32_t)R::kPairBytes) +
+                               (coarse ? (uint32_t)(kWaveCoarseW * 3 * sizeof(T)) : 0u);
         mbar_expect_tx(bar, bytes);
-        tma_load_2d(bdst, map_b, X0, t, bar);
-        if (!ZERO) tma_load_2d(udst, map_u, X0, t, bar);
-        if (coarse) tma_load_2d(udst + (ZERO ? 0 : kRowB), map_c, cbox_x, y0c, bar);
+        tma_load_2d(ring_s + bslot * R::kPairBytes, map_b, X0, 2 * P, bar);
+        if (!ZERO) tma_load_2d(udst, map_u, X0, 2 * P, bar);
+        if (coarse) tma_load_2d(udst + (ZERO ? 0 : R::kPairBytes), map_c, cbox_x, P - 1, bar);
     };
     if (lane == 0)
-        for (int p = 0; p < AHEAD && tb + p <= te; ++p) issue(tb + p);
+        for (int p = 0; p < AHEAD && pb + p <= te; ++p) issue(pb + p, p, p);
 
-    T u[NR][4];
+    T w[NR][2][4];  // window of u pairs in registers
 #pragma unroll
-    for (int r = 0; r < NR; ++r)
+    for (int q = 0; q < NR; ++q)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) u[r][i] = T(0);
-    // b of row t - d lives in ring slot (t - d - tb) mod NB; rows before tb read as zero
-    auto brow_of = [&](int rr, T (&v)[4]) {
-        if (rr < tb) {
-            v[0] = v[1] = v[2] = v[3] = T(0);
-        } else {
-            lds4(ring_s + ((rr - tb) & (NB - 1)) * kRowB + 4 * lane * (uint32_t)sizeof(T), v);
-        }
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[q][h][i] = T(0);
+    auto bslot_of = [&](int bs, int back) { const int q = bs - back; return q < 0 ? q + NB : q; };
+    auto load_b = [&](int bslot, int h, T (&v)[4]) {
+        lds4(ring_s + bslot * R::kPairBytes + h * kRowB + 4 * lane * (uint32_t)sizeof(T), v);
     };
-    T rsum[2] = {T(0), T(0)};  // restriction partial sums (DOWN)
 
+    int bs = 0, us = 0;  // ring slots of pair T
+    uint32_t phase = 0;  // parity of the b-slot barriers in the current lap
 #pragma unroll 1
-    for (int t = tb; t <= te; ++t) {
-        const int n = t - tb;
-        const int slot = n & (NB - 1);
-        const uint32_t bar = bar_s + 8 * slot;
-        if (!mbar_wait_warp(bar, (n / NB) & 1)) {
+    for (int T_ = pb; T_ <= te; ++T_) {
+        const uint32_t bar = bar_s + 8 * bs;
+        if (!mbar_wait_warp(bar, phase)) {
             // give up: flag the host, let the copies already issued land, leave
             if (lane == 0) atomicExch(a.err, 1);
-            for (int tt = t + 1; tt <= te && tt < t + AHEAD; ++tt)
-                mbar_wait_warp(bar_s + 8 * ((tt - tb) & (NB - 1)), ((tt - tb) / NB) & 1);
+            int b2 = bs, ph2 = phase;
+            for (int tt = T_ + 1; tt <= te && tt < T_ + AHEAD; ++tt) {
+                if (++b2 == NB) { b2 = 0; ph2 ^= 1; }
+                mbar_wait_warp(bar_s + 8 * b2, ph2);
+            }
             return;
         }
-        // shift the window and bring in row t
+        // shift the window and bring in pair T
 #pragma unroll
-        for (int r = 0; r < NR - 1; ++r)
+        for (int q = 0; q < NR - 1; ++q)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) u[r][i] = u[r + 1][i];
-        const uint32_t us_addr = uring_s + (n & (AHEAD - 1)) * R::kUSlotBytes;
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) w[q][h][i] = w[q + 1][h][i];
+        const uint32_t us_addr = uring_s + us * R::kUSlotBytes;
         if (ZERO) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) u[NR - 1][i] = T(0);
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) w[NR - 1][h][i] = T(0);
         } else {
-            lds4(us_addr + 4 * lane * (uint32_t)sizeof(T), u[NR - 1]);
+            lds4(us_addr + 4 * lane * (uint32_t)sizeof(T), w[NR - 1][0]);
+            lds4(us_addr + kRowB + 4 * lane * (uint32_t)sizeof(T), w[NR - 1][1]);
         }
-        // UP: add the interpolated coarse correction to row t
-        if (has_coarse && t >= 0 && t < L.ny) {
-            int Iy, Jy;
-            T wy;
-            interp_axis<T>(t, L.n0y, k, L.ncy, Iy, Jy, wy);
-            const int y0c = min(Iy, Jy);
-            const uint32_t cb = us_addr + (ZERO ? 0 : kRowB);
-            const uint32_t c0 = cb + ((Iy - y0c) * kWaveCoarseW + 2 * lane + 3) * (uint32_t)sizeof(T);  // col cx0-1
-            const uint32_t c1 = cb + ((Jy - y0c) * kWaveCoarseW + 2 * lane + 3) * (uint32_t)sizeof(T);
-            const T v0[4] = {lds1(c0, T(0)), lds1(c0 + sizeof(T), T(0)), lds1(c0 + 2 * sizeof(T), T(0)),
-                             lds1(c0 + 3 * sizeof(T), T(0))};
-            const T v1[4] = {lds1(c1, T(0)), lds1(c1 + sizeof(T), T(0)), lds1(c1 + 2 * sizeof(T), T(0)),
-                             lds1(c1 + 3 * sizeof(T), T(0))};
-            if (lane_in) {
-                T(&row)[4] = u[NR - 1];
-                if (std_lane && xlane + 3 < L.nx) {
-                    const T q = T(0.25);
-                    row[0] = row[0] + bilinear<T>(v0[1], v0[0], v1[1], v1[0], q, wy);
-                    row[1] = row[1] + bilinear<T>(v0[1], v0[2], v1[1], v1[2], q, wy);
-                    row[2] = row[2] + bilinear<T>(v0[2], v0[1], v1[2], v1[1], q, wy);
-                    row[3] = row[3] + bilinear<T>(v0[2], v0[3], v1[2], v1[3], q, wy);
+        // UP: add the interpolated coarse correction to rows 2T and 2T+1
+        if (has_coarse && 2 * T_ < ny && 2 * T_ + 1 >= 0) {
+            const uint32_t cb = us_addr + (ZERO ? 0 : R::kPairBytes);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = 2 * T_ + h;
+                if (r < 0 || r >= ny) continue;
+                int Iy, Jy;
+                T wy;
+                interp_axis<T>(r, L.n0y, k, L.ncy, Iy, Jy, wy);
+                // coarse row q sits at box row q - (T - 1); columns cx0-1 .. cx0+2 at 2l+3 .. 2l+6
+                const uint32_t c0 = cb + ((Iy - T_ + 1) * kWaveCoarseW + 2 * lane + 2) * (uint32_t)sizeof(T);
+                const uint32_t c1 = cb + ((Jy - T_ + 1) * kWaveCoarseW + 2 * lane + 2) * (uint32_t)sizeof(T);
+                T a0[6], a1[6];  // columns 2l+2 .. 2l+7 of the box (8-byte aligned pairs)
+#pragma unroll
+                for (int m = 0; m < 6; m += 2) {
+                    lds2(c0 + m * sizeof(T), a0[m], a0[m + 1]);
+                    lds2(c1 + m * sizeof(T), a1[m], a1[m + 1]);
+                }
+                const T v0[4] = {a0[1], a0[2], a0[3], a0[4]};
+                const T v1[4] = {a1[1], a1[2], a1[3], a1[4]};
+                if (!lane_in) continue;
+                T(&row)[4] = w[NR - 1][h];
+                if (std_lane && xlane + 3 < nx) {
+                    const T q4 = T(0.25);
+                    row[0] = row[0] + bilinear<T>(v0[1], v0[0], v1[1], v1[0], q4, wy);
+                    row[1] = row[1] + bilinear<T>(v0[1], v0[2], v1[1], v1[2], q4, wy);
+                    row[2] = row[2] + bilinear<T>(v0[2], v0[1], v1[2], v1[1], q4, wy);
+                    row[3] = row[3] + bilinear<T>(v0[2], v0[3], v1[2], v1[3], q4, wy);
                 } else {
-                    prolong_generic<T>(row, v0, v1, oI, oJ, cwx, wy, xlane, L.nx);
+                    prolong_generic<T>(row, v0, v1, oI, oJ, cwx, wy, xlane, nx);
                 }
             }
         }
-        // refill the slot of row t + AHEAD - NB (whose b is no longer needed) with row t + AHEAD
+        // refill: pair T + AHEAD into the b slot of pair T + AHEAD - NB (no longer needed) and
+        // the u/coarse slot of pair T (just consumed)
         __syncwarp();
-        if (lane == 0 && t + AHEAD <= te) issue(t + AHEAD);
+        {
+            int nbs = bs + AHEAD;
+            if (nbs >= NB) nbs -= NB;
+            if (lane == 0 && T_ + AHEAD <= te) issue(T_ + AHEAD, nbs, us);
+        }
 
-        // half-sweeps: stage s updates row t - s (window slot NR-1-s) with colour (s - 1) & 1
+        // half-sweeps: stage s updates pair T - s (window slot NR-1-s) with colour (s - 1) & 1
 #pragma unroll
         for (int s = 1; s <= S; ++s) {
-            const int r = t - s;
-            if (r < tb || r < 0 || r >= L.ny) continue;
-            T(&row)[4] = u[NR - 1 - s];
-            const T(&nrow)[4] = u[NR - 2 - s];
-            const T(&srow)[4] = u[NR - s];
-            T brow[4];
-            brow_of(r, brow);
-            const int color = (s - 1) & 1;
-            const int first = (xlane + r + color) & 1;  // first cell index with this colour
-            const T west = __shfl_up_sync(0xffffffffu, row[3], 1);   // cell 3 of lane-1
-            const T east = __shfl_down_sync(0xffffffffu, row[0], 1);  // cell 0 of lane+1
-            // Cells outside the level (x < 0 or x >= nx) are updated too: their coefficients
-            // decouple them (zero faces), in-level cells give them zero weight, and they are
-            // never written back, so no per-cell bounds test is needed.
-            if (xint && interior_row(r, L.ny, k)) {
-                if (first == 0) {  // cells 0 and 2
-                    row[0] = gs_update<T>(ci, brow[0], west, row[1], nrow[0], srow[0]);
-                    row[2] = gs_update<T>(ci, brow[2], row[1], row[3], nrow[2], srow[2]);
-                } else {           // cells 1 and 3
-                    row[1] = gs_update<T>(ci, brow[1], row[0], row[2], nrow[1], srow[1]);
-                    row[3] = gs_update<T>(ci, brow[3], row[2], east, nrow[3], srow[3]);
-                }
-            } else {
-                edge_update<T>(row, brow, nrow, srow, first, west, east, xlane, r, L.nx, L.ny, L.n0x, L.n0y, k,
-                               alpha, sk);
-            }
+            const int m = T_ - s;
+            const int r0 = 2 * m, r1 = 2 * m + 1;
+            if (m < pb || r0 >= ny || r1 < 0) continue;
+            T(&p0)[4] = w[NR - 1 - s][0];
+            T(&p1)[4] = w[NR - 1 - s][1];
+            const T(&north)[4] = w[NR - 2 - s][1];  // row 2m - 1
+            const T(&south)[4] = w[NR - s][0];      // row 2m + 2
+            const int bq = bslot_of(bs, s);
+            T b0[4], b1[4];
+            load_b(bq, 0, b0);
+            load_b(bq, 1, b1);
+            const int f0 = (r0 + ((s - 1) & 1)) & 1;  // first cell of the colour on row r0
+            // Row r0 updates cells {0, 2} (needs cell 3 of lane-1) when f0 == 0, else {1, 3}
+            // (needs cell 0 of lane+1); row r1 the other way round.  One shuffle per row.
+            const int d0 = f0 == 0 ? -1 : 1;
+            const T x0 = __shfl_sync(0xffffffffu, f0 == 0 ? p0[3] : p0[0], lane + d0);
+            const T x1 = __shfl_sync(0xffffffffu, f0 == 0 ? p1[0] : p1[3], lane - d0);
+            const bool fast = xint && interior_row(r0, ny, k) && interior_row(r1, ny, k);
+            sweep_row<T>(p0, b0, north, p1, f0, x0, x0, fast, tab, xlane, r0, nx, ny, L.n0x, L.n0y, k, alpha, sk);
+            if (r1 < ny)
+                sweep_row<T>(p1, b1, p0, south, f0 ^ 1, x1, x1, fast, tab, xlane, r1, nx, ny, L.n0x, L.n0y, k, alpha,
+                             sk);
         }
-        // output of the row that completed all half-sweeps
+        // output of the pair that completed all half-sweeps
         {
-            const int r = t - S;
-            if (r >= Y0 && r < Y1 && interior_lane && lane_in) {
-                const T(&orow)[4] = u[NR - 1 - S];
-                T* dst = (UP ? L.uo : L.u) + (int64_t)r * L.pitch + xlane;
-                if (xlane + 3 < L.nx) {
-                    Vec4<T>::store(dst, orow);
-                } else {
+            const int m = T_ - S;
+            if (m >= P0 && m < P1 && interior_lane && lane_in) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        if (xlane + i < L.nx) dst[i] = orow[i];
+                for (int h = 0; h < 2; ++h) {
+                    const int r = 2 * m + h;
+                    if (r >= Y1) continue;
+                    const T(&orow)[4] = w[NR - 1 - S][h];
+                    T* dst = (UP ? L.uo : L.u) + (int64_t)r * L.pitch + xlane;
+                    if (xlane + 3 < nx) {
+                        Vec4<T>::store(dst, orow);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (xlane + i < nx) dst[i] = orow[i];
+                    }
                 }
             }
         }
         if (!UP) {
-            // residual of row t - S - 1 (slot 1; neighbours in slots 0 and 2) and its restriction
-            const int r = t - S - 1;
-            const T(&rrow)[4] = u[1];
-            const T west = __shfl_up_sync(0xffffffffu, rrow[3], 1);
-            const T east = __shfl_down_sync(0xffffffffu, rrow[0], 1);
-            if (r >= Y0 && r < Y1e && L.bc) {
-                const bool row_in = r < L.ny && lane_in;
-                T res[4] = {T(0), T(0), T(0), T(0)};
-                if (row_in) {
-                    T brow[4];
-                    brow_of(r, brow);
-                    if (xint && interior_row(r, L.ny, k)) {
-                        res[0] = residual_at<T>(ci, brow[0], rrow[0], west, rrow[1], u[0][0], u[2][0]);
-                        res[1] = residual_at<T>(ci, brow[1], rrow[1], rrow[0], rrow[2], u[0][1], u[2][1]);
-                        res[2] = residual_at<T>(ci, brow[2], rrow[2], rrow[1], rrow[3], u[0][2], u[2][2]);
-                        res[3] = residual_at<T>(ci, brow[3], rrow[3], rrow[2], east, u[0][3], u[2][3]);
-                    } else {
-                        edge_residual<T>(res, rrow, brow, u[0], u[2], west, east, xlane, r, L.nx, L.ny, L.n0x,
-                                         L.n0y, k, alpha, sk);
-                    }
+            // residual of pair m = T - S - 1 (slot 1; neighbours in slots 0 and 2) and its 2x2
+            // restriction: rows 2m and 2m+1 form coarse row m
+            const int m = T_ - S - 1;
+            const T(&q0)[4] = w[1][0];
+            const T(&q1)[4] = w[1][1];
+            const T w0 = __shfl_up_sync(0xffffffffu, q0[3], 1);
+            const T e0 = __shfl_down_sync(0xffffffffu, q0[0], 1);
+            const T w1 = __shfl_up_sync(0xffffffffu, q1[3], 1);
+            const T e1 = __shfl_down_sync(0xffffffffu, q1[0], 1);
+            if (m >= P0 && m < P1 && L.bc && lane_in) {
+                const int r0 = 2 * m, r1 = 2 * m + 1;
+                const int bq = bslot_of(bs, S + 1);
+                T b0[4], b1[4];
+                load_b(bq, 0, b0);
+                load_b(bq, 1, b1);
+                const bool fast = xint && interior_row(r0, ny, k) && interior_row(r1, ny, k);
+                T res0[4], res1[4] = {T(0), T(0), T(0), T(0)};
+                residual_row<T>(res0, q0, b0, w[0][1], q1, w0, e0, fast, tab, xlane, r0, nx, ny, L.n0x, L.n0y, k,
+                                alpha, sk);
+                const bool has_r1 = r1 < ny;
+                if (has_r1)
+                    residual_row<T>(res1, q1, b1, q0, w[2][0], w1, e1, fast, tab, xlane, r1, nx, ny, L.n0x, L.n0y, k,
+                                    alpha, sk);
+                // same summation order as the reference restriction: (((0 + r00) + r01) + r10) + r11
+                T c0 = T(0), c1 = T(0);
+                if (xlane + 0 < nx) c0 = c0 + res0[0];
+                if (xlane + 1 < nx) c0 = c0 + res0[1];
+                if (xlane + 2 < nx) c1 = c1 + res0[2];
+                if (xlane + 3 < nx) c1 = c1 + res0[3];
+                if (has_r1) {
+                    if (xlane + 0 < nx) c0 = c0 + res1[0];
+                    if (xlane + 1 < nx) c0 = c0 + res1[1];
+                    if (xlane + 2 < nx) c1 = c1 + res1[2];
+                    if (xlane + 3 < nx) c1 = c1 + res1[3];
                 }
-                // same summation order as the reference restriction:
-                // (((0 + r00) + r01) + r10) + r11
-                if ((r & 1) == 0) {
-                    rsum[0] = T(0);
-                    rsum[1] = T(0);
-                }
-                if (row_in) {
-                    if (xlane + 0 < L.nx) rsum[0] = rsum[0] + res[0];
-                    if (xlane + 1 < L.nx) rsum[0] = rsum[0] + res[1];
-                    if (xlane + 2 < L.nx) rsum[1] = rsum[1] + res[2];
-                    if (xlane + 3 < L.nx) rsum[1] = rsum[1] + res[3];
-                }
-                if (r & 1) {
-                    const int J = r >> 1;
-                    if (interior_lane && lane_in && J < L.ncy) {
-                        T* dst = L.bc + (int64_t)J * L.pitchc + cx0;
-                        const T v0 = rsum[0] * T(0.25), v1 = rsum[1] * T(0.25);
-                        if (cx0 + 1 < L.ncx) Vec2<T>::store(dst, v0, v1);
-                        else if (cx0 < L.ncx) dst[0] = v0;
-                    }
+                if (interior_lane && m < L.ncy) {
+                    T* dst = L.bc + (int64_t)m * L.pitchc + cx0;
+                    const T v0 = c0 * T(0.25), v1 = c1 * T(0.25);
+                    if (cx0 + 1 < L.ncx) Vec2<T>::store(dst, v0, v1);
+                    else if (cx0 < L.ncx) dst[0] = v0;
                 }
             }
         }
+        if (++bs == NB) { bs = 0; phase ^= 1; }
+        if (++us == AHEAD) us = 0;
     }
 }
 

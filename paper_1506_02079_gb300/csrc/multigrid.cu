@@ -429,17 +429,17 @@ struct Solver {
             while (L.ch > 16 && want / L.ch < (int64_t)kNumSMs * 16 * 4) L.ch /= 2;
             for (const auto& S : L.wsl) {
                 L.item_start.push_back(L.item_start.back() + (int64_t)S.fstrips * ceil_div(S.ny, L.ch));
-                // TMA maps: rows of u and b (one 128-cell strip row per box) and the two
-                // coarse rows around a fine row for the prolongation
+                // TMA maps: row pairs of u, b and uo (one 128 x 2 box per strip step) and the
+                // three coarse rows around a fine row pair for the prolongation
                 CUtensorMap mu, mb, mc;
-                EMF_TRY(encode_tensor_map_2d(&mu, S.u, sizeof(TV), S.nx, S.ny, S.pitch, kWaveWidth, 1));
-                EMF_TRY(encode_tensor_map_2d(&mb, S.b, sizeof(TV), S.nx, S.ny, S.pitch, kWaveWidth, 1));
+                EMF_TRY(encode_tensor_map_2d(&mu, S.u, sizeof(TV), S.nx, S.ny, S.pitch, kWaveWidth, 2));
+                EMF_TRY(encode_tensor_map_2d(&mb, S.b, sizeof(TV), S.nx, S.ny, S.pitch, kWaveWidth, 2));
                 if (S.uco)
-                    EMF_TRY(encode_tensor_map_2d(&mc, S.uco, sizeof(TV), S.ncx, S.ncy, S.pitchc, kWaveCoarseW, 2));
+                    EMF_TRY(encode_tensor_map_2d(&mc, S.uco, sizeof(TV), S.ncx, S.ncy, S.pitchc, kWaveCoarseW, 3));
                 else
                     mc = mu;
                 CUtensorMap mo;
-                EMF_TRY(encode_tensor_map_2d(&mo, S.uo, sizeof(TV), S.nx, S.ny, S.pitch, kWaveWidth, 1));
+                EMF_TRY(encode_tensor_map_2d(&mo, S.uo, sizeof(TV), S.nx, S.ny, S.pitch, kWaveWidth, 2));
                 L.maps.push_back(mu);
                 L.maps.push_back(mb);
                 L.maps.push_back(mc);
