@@ -261,11 +261,17 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     const bool interior_lane = lane >= kWaveHalo / 4 && lane < 32 - kWaveHalo / 4;
     StencilTab<T> tab;
     make_stencil_tab<T>(tab, k, alpha, sk);
-    bool xint = true;  // all 4 cells of the lane interior along x
+    // xint: the lane can use the interior stencil: all 4 cells interior along x, or all 4
+    // outside the level (their values are never written back and in-level cells give them
+    // zero weight, so any finite update will do)
+    bool xint = xlane + 3 < 0 || xlane >= nx;
+    if (!xint) {
+        xint = true;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const AxisCoef<T> q = axis_coef<T>(xlane + i, nx, L.n0x, k);
-        xint = xint && q.w == T(1) && q.gm == T(1) && q.gp == T(1);
+        for (int i = 0; i < 4; ++i) {
+            const AxisCoef<T> q = axis_coef<T>(xlane + i, nx, L.n0x, k);
+            xint = xint && q.w == T(1) && q.gm == T(1) && q.gp == T(1);
+        }
     }
 
     // prolongation geometry along x (UP): coarse columns cx0-1 .. cx0+2 around the lane

@@ -424,9 +424,10 @@ struct Solver {
                     want += (int64_t)S.fstrips * S.ny;
                 }
             }
-            // rows per work item: as tall as possible while keeping ~4 waves of warps
+            // rows per work item: tall chunks amortise the halo rows (about 2 nu + 3 pairs per
+            // chunk); shorter ones only while the level would otherwise leave SMs idle
             L.ch = 128;
-            while (L.ch > 16 && want / L.ch < (int64_t)kNumSMs * 16 * 4) L.ch /= 2;
+            while (L.ch > 32 && want / L.ch < (int64_t)kNumSMs * 16 * 2) L.ch /= 2;
             for (const auto& S : L.wsl) {
                 L.item_start.push_back(L.item_start.back() + (int64_t)S.fstrips * ceil_div(S.ny, L.ch));
                 // TMA maps: row pairs of u, b and uo (one 128 x 2 box per strip step) and the
