@@ -187,6 +187,15 @@ uint64_t emfuse_kernel_launches(void);
 void emfuse_profile_begin(void);
 int emfuse_profile_end(emfuse_kernel_profile* out, int max_entries);
 
+/*
+ * Solver plans (descriptor tables, TMA tensor maps, multigrid pyramids and the FP64 iterate)
+ * are kept between calls, one per (device, stream, precision), and reused while the slice
+ * geometry and schedule options stay the same.  emfuse_release_cache() frees them all (they
+ * are rebuilt by the next solve).  It synchronises the device and must not be called while
+ * another host thread is inside a solve.
+ */
+void emfuse_release_cache(void);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* emfuse_last_error(void);
 

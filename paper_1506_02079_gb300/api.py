@@ -19,7 +19,7 @@ from . import build as _build
 __all__ = [
     "EmfuseError", "EmfuseUnavailable", "SolveOpts", "SliceStats", "lib", "library_path",
     "default_opts", "emfuse_smooth_z", "emfuse_screened_poisson", "emfuse_correct_stack",
-    "emfuse_backward", "emfuse_version", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
+    "emfuse_backward", "emfuse_version", "emfuse_release_cache", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
     "PREC_FP64", "EXPORTED_SYMBOLS",
 ]
 
@@ -30,7 +30,7 @@ STATUS = {0: "EMFUSE_OK", 1: "EMFUSE_EINVAL", 2: "EMFUSE_ECUDA", 3: "EMFUSE_ENOM
 EXPORTED_SYMBOLS = ["emfuse_default_opts", "emfuse_smooth_z", "emfuse_screened_poisson",
                     "emfuse_correct_stack", "emfuse_backward", "emfuse_last_error",
                     "emfuse_version", "emfuse_kernel_launches", "emfuse_profile_begin",
-                    "emfuse_profile_end"]
+                    "emfuse_profile_end", "emfuse_release_cache"]
 
 
 class EmfuseError(RuntimeError):
@@ -91,12 +91,19 @@ def lib() -> ctypes.CDLL:
             L.emfuse_version.argtypes = []
             L.emfuse_kernel_launches.restype = ctypes.c_uint64
             L.emfuse_kernel_launches.argtypes = []
+            L.emfuse_release_cache.restype = None
+            L.emfuse_release_cache.argtypes = []
             _lib = L
         return _lib
 
 
 def emfuse_version() -> str:
     return lib().emfuse_version().decode()
+
+
+def emfuse_release_cache() -> None:
+    """Free the solver plans and workspaces kept between calls."""
+    lib().emfuse_release_cache()
 
 
 def default_opts(**kw) -> SolveOpts:

@@ -98,6 +98,11 @@ void emfuse_default_opts(emfuse_solve_opts* o) {
 
 const char* emfuse_last_error(void) { return last_error(); }
 
+void emfuse_release_cache(void) {
+    cudaDeviceSynchronize();
+    release_plans();
+}
+
 const char* emfuse_version(void) { return "emfuse 0.1 (sm_103a)"; }
 
 int emfuse_smooth_z(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,

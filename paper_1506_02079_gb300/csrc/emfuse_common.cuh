@@ -87,10 +87,29 @@ class DeviceBuffer {
         bytes_ = bytes;
         return EMFUSE_OK;
     }
+    // Allocation kept across calls (solver plans): plain cudaMalloc / cudaFree, so it is not
+    // tied to the lifetime of the caller's stream.
+    int alloc_persistent(size_t bytes) {
+        release();
+        persistent_ = true;
+        if (bytes == 0) return EMFUSE_OK;
+        cudaError_t e = cudaMalloc(&ptr_, bytes);
+        if (e != cudaSuccess) {
+            ptr_ = nullptr;
+            set_error(std::string("cudaMalloc(") + std::to_string(bytes) + " bytes): " + cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? EMFUSE_ENOMEM : EMFUSE_ECUDA;
+        }
+        bytes_ = bytes;
+        return EMFUSE_OK;
+    }
     void release() {
-        if (ptr_) cudaFreeAsync(ptr_, stream_);
+        if (ptr_) {
+            if (persistent_) cudaFree(ptr_);
+            else cudaFreeAsync(ptr_, stream_);
+        }
         ptr_ = nullptr;
         bytes_ = 0;
+        persistent_ = false;
     }
     template <class T>
     T* as() const { return reinterpret_cast<T*>(ptr_); }
@@ -100,6 +119,7 @@ class DeviceBuffer {
     void* ptr_ = nullptr;
     size_t bytes_ = 0;
     cudaStream_t stream_ = nullptr;
+    bool persistent_ = false;
 };
 
 // ---------------------------------------------------------------- multigrid geometry

@@ -42,6 +42,7 @@ struct SolveRequest {
     emfuse_slice_stats* stats = nullptr;  // host, may be null
 };
 int solve_batch(const SolveRequest& req, cudaStream_t st);
+void release_plans();
 
 // elementwise helpers used by the adjoint (multigrid.cu)
 int apply_laplacian_stack(const float* in, float* out, int64_t nx, int64_t ny, int64_t nz,

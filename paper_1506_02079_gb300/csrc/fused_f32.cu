@@ -8,8 +8,11 @@ template <class T>
 static int launch_wave_impl(const WaveArgs<T>& a, int S, bool zero_init, bool up, cudaStream_t st, double bytes) {
     if (a.nitems == 0) return EMFUSE_OK;
     const unsigned grid = (unsigned)ceil_div(a.nitems, kWaveWarps);
-    const char* name = up ? (a.k == 0 ? "wave_up_l0" : "wave_up_coarse")
-                          : (a.k == 0 ? "wave_down_l0" : "wave_down_coarse");
+    static const char* const kUp[] = {"wave_up_l0", "wave_up_l1", "wave_up_l2", "wave_up_l3", "wave_up_l4",
+                                      "wave_up_l5+"};
+    static const char* const kDown[] = {"wave_down_l0", "wave_down_l1", "wave_down_l2", "wave_down_l3",
+                                        "wave_down_l4", "wave_down_l5+"};
+    const char* name = up ? kUp[a.k < 5 ? a.k : 5] : kDown[a.k < 5 ? a.k : 5];
     KernelScope ks(name, st, bytes);
 #define EMF_WAVE_ONE(KERNEL, SMEM)                                                           \
     do {                                                                                     \

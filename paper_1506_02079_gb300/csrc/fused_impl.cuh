@@ -155,11 +155,27 @@ __device__ __forceinline__ Coef<T> edge_coef(const StencilTab<T>& tab, int x, in
     return k == 0 ? level0_coef<T>(tab, x, r, nx, ny) : coarse_cell_coef<T>(x, r, nx, ny, n0x, n0y, k, alpha, sk);
 }
 
+// Stencil of cell i of the lane on an interior row, from the lane's shared-memory cache
+// (cw, ce, cn = cs, D, 1/D per cell, as make_coef returns them on such a row).
+template <class T>
+__device__ __forceinline__ Coef<T> cached_coef(uint32_t cache, int i) {
+    Coef<T> c;
+    const uint32_t a = cache + i * 5 * (uint32_t)sizeof(T);
+    c.cw = lds1(a, T(0));
+    c.ce = lds1(a + sizeof(T), T(0));
+    c.cn = lds1(a + 2 * sizeof(T), T(0));
+    c.cs = c.cn;
+    c.D = lds1(a + 3 * sizeof(T), T(0));
+    c.iD = lds1(a + 4 * sizeof(T), T(0));
+    return c;
+}
+
 // Half-sweep of one colour on one row of the lane's 4 cells (cells f and f + 2).
 template <class T>
 __device__ __forceinline__ void sweep_row(T (&row)[4], const T (&brow)[4], const T (&nrow)[4], const T (&srow)[4],
-                                          int f, T west, T east, bool fast, const StencilTab<T>& tab, int xlane,
-                                          int r, int nx, int ny, int n0x, int n0y, int k, T alpha, T sk) {
+                                          int f, T west, T east, bool fast, bool irow, uint32_t cache,
+                                          const StencilTab<T>& tab, int xlane, int r, int nx, int ny, int n0x,
+                                          int n0y, int k, T alpha, T sk) {
     if (fast) {
         if (f == 0) {
             row[0] = gs_update<T>(tab.ci, brow[0], west, row[1], nrow[0], srow[0]);
@@ -174,7 +190,8 @@ __device__ __forceinline__ void sweep_row(T (&row)[4], const T (&brow)[4], const
             const int i = 2 * h + f;
             const T uw = i == 0 ? west : row[i - 1];
             const T ue = i == 3 ? east : row[i + 1];
-            const Coef<T> c = edge_coef<T>(tab, xlane + i, r, nx, ny, n0x, n0y, k, alpha, sk);
+            const Coef<T> c = irow ? cached_coef<T>(cache, i)
+                                   : edge_coef<T>(tab, xlane + i, r, nx, ny, n0x, n0y, k, alpha, sk);
             row[i] = gs_update<T>(c, brow[i], uw, ue, nrow[i], srow[i]);
         }
     }
@@ -183,13 +200,16 @@ __device__ __forceinline__ void sweep_row(T (&row)[4], const T (&brow)[4], const
 // Residuals of one row of the lane's 4 cells.
 template <class T>
 __device__ __forceinline__ void residual_row(T (&res)[4], const T (&row)[4], const T (&brow)[4], const T (&nrow)[4],
-                                             const T (&srow)[4], T west, T east, bool fast, const StencilTab<T>& tab,
-                                             int xlane, int r, int nx, int ny, int n0x, int n0y, int k, T alpha, T sk) {
+                                             const T (&srow)[4], T west, T east, bool fast, bool irow,
+                                             uint32_t cache, const StencilTab<T>& tab, int xlane, int r, int nx,
+                                             int ny, int n0x, int n0y, int k, T alpha, T sk) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const T uw = i == 0 ? west : row[i - 1];
         const T ue = i == 3 ? east : row[i + 1];
-        const Coef<T> c = fast ? tab.ci : edge_coef<T>(tab, xlane + i, r, nx, ny, n0x, n0y, k, alpha, sk);
+        const Coef<T> c = fast ? tab.ci
+                               : (irow ? cached_coef<T>(cache, i)
+                                       : edge_coef<T>(tab, xlane + i, r, nx, ny, n0x, n0y, k, alpha, sk));
         res[i] = residual_at<T>(c, brow[i], row[i], uw, ue, nrow[i], srow[i]);
     }
 }
@@ -218,7 +238,8 @@ struct WaveRing {
     static constexpr int kUSlotBytes = (ZERO ? 0 : kPairBytes) + kCoarseBytes;
     static constexpr int kBRingBytes = kNB * kPairBytes;
     static constexpr int kURingBytes = kAhead * kUSlotBytes;
-    static constexpr int kWarpBytes = kBRingBytes + kURingBytes + (kNB * 8 + 127) / 128 * 128;
+    static constexpr int kCoefBytes = 32 * 4 * 5 * (int)sizeof(T);       // per-lane stencil cache
+    static constexpr int kWarpBytes = kBRingBytes + kURingBytes + kCoefBytes + (kNB * 8 + 127) / 128 * 128;
 };
 
 template <class T, int S, bool ZERO, bool UP>
@@ -300,10 +321,25 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     unsigned char* ring = wave_smem + (size_t)warp * R::kWarpBytes;
     const uint32_t ring_s = smem_addr(ring);
     const uint32_t uring_s = ring_s + R::kBRingBytes;
-    const uint32_t bar_s = uring_s + R::kURingBytes;
+    const uint32_t coef_s = uring_s + R::kURingBytes + lane * 20 * (uint32_t)sizeof(T);
+    const uint32_t bar_s = uring_s + R::kURingBytes + R::kCoefBytes;
     if (lane == 0) {
         for (int q = 0; q < NB; ++q) mbar_init(bar_s + 8 * q, 1);
         mbar_init_fence();
+    }
+    {  // cache this lane's stencils for interior rows (read when the row pair is not all-interior)
+        AxisCoef<T> one;
+        one.w = T(1); one.gm = T(1); one.gp = T(1);
+        T* cc = reinterpret_cast<T*>(ring + (coef_s - ring_s));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const Coef<T> c = make_coef<T>(axis_coef<T>(xlane + i, nx, L.n0x, k), one, k, alpha, sk);
+            cc[5 * i + 0] = c.cw;
+            cc[5 * i + 1] = c.ce;
+            cc[5 * i + 2] = c.cn;
+            cc[5 * i + 3] = c.D;
+            cc[5 * i + 4] = c.iD;
+        }
     }
     __syncwarp();
     // TMA loads of pair P (lane 0): b (and u) rows 2P, 2P+1; coarse rows P-1 .. P+1 (UP)
@@ -428,11 +464,13 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
             const int d0 = f0 == 0 ? -1 : 1;
             const T x0 = __shfl_sync(0xffffffffu, f0 == 0 ? p0[3] : p0[0], lane + d0);
             const T x1 = __shfl_sync(0xffffffffu, f0 == 0 ? p1[0] : p1[3], lane - d0);
-            const bool fast = xint && interior_row(r0, ny, k) && interior_row(r1, ny, k);
-            sweep_row<T>(p0, b0, north, p1, f0, x0, x0, fast, tab, xlane, r0, nx, ny, L.n0x, L.n0y, k, alpha, sk);
+            const bool ir0 = interior_row(r0, ny, k), ir1 = interior_row(r1, ny, k);
+            const bool fast = xint && ir0 && ir1;
+            sweep_row<T>(p0, b0, north, p1, f0, x0, x0, fast, ir0, coef_s, tab, xlane, r0, nx, ny, L.n0x, L.n0y, k,
+                         alpha, sk);
             if (r1 < ny)
-                sweep_row<T>(p1, b1, p0, south, f0 ^ 1, x1, x1, fast, tab, xlane, r1, nx, ny, L.n0x, L.n0y, k, alpha,
-                             sk);
+                sweep_row<T>(p1, b1, p0, south, f0 ^ 1, x1, x1, fast, ir1, coef_s, tab, xlane, r1, nx, ny, L.n0x,
+                             L.n0y, k, alpha, sk);
         }
         // output of the pair that completed all half-sweeps
         {
@@ -470,14 +508,15 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                 T b0[4], b1[4];
                 load_b(bq, 0, b0);
                 load_b(bq, 1, b1);
-                const bool fast = xint && interior_row(r0, ny, k) && interior_row(r1, ny, k);
+                const bool ir0 = interior_row(r0, ny, k), ir1 = interior_row(r1, ny, k);
+                const bool fast = xint && ir0 && ir1;
                 T res0[4], res1[4] = {T(0), T(0), T(0), T(0)};
-                residual_row<T>(res0, q0, b0, w[0][1], q1, w0, e0, fast, tab, xlane, r0, nx, ny, L.n0x, L.n0y, k,
-                                alpha, sk);
+                residual_row<T>(res0, q0, b0, w[0][1], q1, w0, e0, fast, ir0, coef_s, tab, xlane, r0, nx, ny, L.n0x,
+                                L.n0y, k, alpha, sk);
                 const bool has_r1 = r1 < ny;
                 if (has_r1)
-                    residual_row<T>(res1, q1, b1, q0, w[2][0], w1, e1, fast, tab, xlane, r1, nx, ny, L.n0x, L.n0y, k,
-                                    alpha, sk);
+                    residual_row<T>(res1, q1, b1, q0, w[2][0], w1, e1, fast, ir1, coef_s, tab, xlane, r1, nx, ny,
+                                    L.n0x, L.n0y, k, alpha, sk);
                 // same summation order as the reference restriction: (((0 + r00) + r01) + r10) + r11
                 T c0 = T(0), c1 = T(0);
                 if (xlane + 0 < nx) c0 = c0 + res0[0];

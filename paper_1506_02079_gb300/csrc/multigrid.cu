@@ -26,6 +26,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include "emfuse_common.cuh"
@@ -316,7 +318,7 @@ struct Blob {
 
 template <class TF, class TV>
 struct Solver {
-    const SolveRequest& req;
+    const SolveRequest* rq = nullptr;  // the call being served
     cudaStream_t st;
     std::vector<LevelPlan<TV>> levels;
     DeviceBuffer ws_levels, ws_desc, ws_f, ws_norms, ws_active;
@@ -334,20 +336,56 @@ struct Solver {
     double tail_cells = 0;
     bool fused = true;
 
-    Solver(const SolveRequest& r, cudaStream_t s) : req(r), st(s) {}
+    explicit Solver(cudaStream_t s) : st(s) {}
+
+    // What the plan depends on: the slice geometry and the schedule options.
+    std::vector<int64_t> sig;
+    bool built = false;
+    static std::vector<int64_t> signature(const SolveRequest& r) {
+        std::vector<int64_t> v = {r.nslices, r.opts.fused, r.opts.nu_pre, r.opts.nu_post};
+        for (int64_t j = 0; j < r.nslices; ++j) {
+            v.push_back(r.nx[j]);
+            v.push_back(r.ny[j]);
+            v.push_back(r.offsets[j]);
+        }
+        return v;
+    }
 
     static bool wave_ok(int nu) { return nu == 1 || nu == 2; }
 
+    void reset() {
+        levels.clear();
+        ws_levels.release();
+        ws_desc.release();
+        ws_f.release();
+        ws_norms.release();
+        ws_active.release();
+        nlev.clear();
+        kc.clear();
+        Kmax = Kw = 0;
+        top_tiles = 0;
+        top_cells = tail_cells = 0;
+        tail = TailArgs<TV>{};
+        built = false;
+    }
+
     int build() {
-        const int64_t n = req.nslices;
-        fused = req.opts.fused != 0 && wave_ok(req.opts.nu_pre) && wave_ok(req.opts.nu_post);
+        std::vector<int64_t> want = signature(*rq);
+        if (built && want == sig) {
+            tail.alpha = TV(rq->alpha);  // the only planned value that depends on alpha
+            return EMFUSE_OK;
+        }
+        reset();
+        sig = std::move(want);
+        const int64_t n = rq->nslices;
+        fused = rq->opts.fused != 0 && wave_ok(rq->opts.nu_pre) && wave_ok(rq->opts.nu_post);
         nlev.resize(n);
         kc.resize(n);
         for (int64_t j = 0; j < n; ++j) {
-            nlev[j] = num_levels(req.nx[j], req.ny[j]);
+            nlev[j] = num_levels(rq->nx[j], rq->ny[j]);
             Kmax = std::max(Kmax, nlev[j]);
             int k = 0;  // first level small enough for the coarse tail
-            while (std::max(level_size((int)req.nx[j], k), level_size((int)req.ny[j], k)) > kTailMax) ++k;
+            while (std::max(level_size((int)rq->nx[j], k), level_size((int)rq->ny[j], k)) > kTailMax) ++k;
             kc[j] = fused ? k : nlev[j];
             Kw = std::max(Kw, kc[j]);
         }
@@ -360,17 +398,17 @@ struct Solver {
         for (int64_t j = 0; j < n; ++j) {
             off[j].resize(nlev[j]);
             for (int k = 0; k < nlev[j]; ++k) {
-                const int64_t lx = level_size((int)req.nx[j], k), ly = level_size((int)req.ny[j], k);
+                const int64_t lx = level_size((int)rq->nx[j], k), ly = level_size((int)rq->ny[j], k);
                 off[j][k] = total;
                 // u, b, and on wavefront levels the output iterate uo
                 total += (wave(j, k) ? 3 : 2) * round_up(lx, align) * ly;
             }
         }
-        EMF_TRY(ws_levels.alloc((size_t)total * sizeof(TV), st));
+        EMF_TRY(ws_levels.alloc_persistent((size_t)total * sizeof(TV)));
         TV* base = ws_levels.as<TV>();
         auto make = [&](int64_t j, int k) {
             LSlice<TV> S{};
-            const int n0x = (int)req.nx[j], n0y = (int)req.ny[j];
+            const int n0x = (int)rq->nx[j], n0y = (int)rq->ny[j];
             S.nx = level_size(n0x, k);
             S.ny = level_size(n0y, k);
             S.pitch = (int)round_up(S.nx, align);
@@ -452,10 +490,10 @@ struct Solver {
         std::vector<int64_t> top_ts(n + 1, 0);
         for (int64_t j = 0; j < n; ++j) {
             const LSlice<TV> S0 = table[level_off[j]];
-            top[j] = TopSlice{req.offsets[j], (int)req.nx[j], (int)req.ny[j],
-                              (int)ceil_div(req.nx[j], kTopTX), S0.pitch, S0.uo, S0.b};
-            top_ts[j + 1] = top_ts[j] + (int64_t)top[j].tiles_x * ceil_div(req.ny[j], kTopTY);
-            top_cells += (double)req.nx[j] * req.ny[j];
+            top[j] = TopSlice{rq->offsets[j], (int)rq->nx[j], (int)rq->ny[j],
+                              (int)ceil_div(rq->nx[j], kTopTX), S0.pitch, S0.uo, S0.b};
+            top_ts[j + 1] = top_ts[j] + (int64_t)top[j].tiles_x * ceil_div(rq->ny[j], kTopTY);
+            top_cells += (double)rq->nx[j] * rq->ny[j];
         }
         top_tiles = top_ts[n];
         std::vector<int> vkc(kc), vnlev(nlev);
@@ -476,7 +514,7 @@ struct Solver {
         const size_t pos_top = blob.add(top), pos_top_ts = blob.add(top_ts);
         const size_t pos_table = blob.add(table), pos_loff = blob.add(level_off);
         const size_t pos_nlev = blob.add(vnlev), pos_kc = blob.add(vkc);
-        EMF_TRY(ws_desc.alloc(blob.host.size(), st));
+        EMF_TRY(ws_desc.alloc_persistent(blob.host.size()));
         char* dbase = ws_desc.as<char>();
         EMF_CUDA(cudaMemcpyAsync(dbase, blob.host.data(), blob.host.size(), cudaMemcpyHostToDevice, st));
         for (int k = 0; k < Kmax; ++k) {
@@ -488,9 +526,9 @@ struct Solver {
         }
         d_top = reinterpret_cast<TopSlice*>(dbase + pos_top);
         d_top_ts = reinterpret_cast<int64_t*>(dbase + pos_top_ts);
-        EMF_TRY(ws_norms.alloc(2 * n * sizeof(double), st));
+        EMF_TRY(ws_norms.alloc_persistent(2 * n * sizeof(double)));
         d_norms = ws_norms.as<double>();
-        EMF_TRY(ws_active.alloc(n * sizeof(int), st));
+        EMF_TRY(ws_active.alloc_persistent(n * sizeof(int)));
         d_active = ws_active.as<int>();
         d_err = device_error_flag();
         if (!d_err) {
@@ -502,12 +540,13 @@ struct Solver {
         tail.nlev = reinterpret_cast<const int*>(dbase + pos_nlev);
         tail.kc = reinterpret_cast<const int*>(dbase + pos_kc);
         tail.nslices = (int)n;
-        tail.alpha = TV(req.alpha);
-        tail.nu_pre = req.opts.nu_pre;
-        tail.nu_post = req.opts.nu_post;
+        tail.alpha = TV(rq->alpha);
+        tail.nu_pre = rq->opts.nu_pre;
+        tail.nu_post = rq->opts.nu_post;
         tail.active = d_active;
         tail.cont = 0;
         EMF_CUDA(cudaStreamSynchronize(st));  // the host staging blob goes out of scope
+        built = true;
         return EMFUSE_OK;
     }
 
@@ -517,7 +556,7 @@ struct Solver {
         a.tile_start = levels[k].d_ts;
         a.nsl = (int)levels[k].sl.size();
         a.k = k;
-        a.alpha = TV(req.alpha);
+        a.alpha = TV(rq->alpha);
         a.sk = TV(std::ldexp(1.0, -2 * k));
         a.active = d_active;
         return a;
@@ -531,7 +570,7 @@ struct Solver {
         a.nitems = levels[k].nitems();
         a.k = k;
         a.ch = levels[k].ch;
-        a.alpha = TV(req.alpha);
+        a.alpha = TV(rq->alpha);
         a.sk = TV(std::ldexp(1.0, -2 * k));
         a.active = d_active;
         a.maps = levels[k].d_maps;
@@ -557,7 +596,7 @@ struct Solver {
     // Reference schedule: one kernel per half-sweep, restriction and prolongation.
     // cont = continue from the level-0 iterate of the previous V-cycle instead of zero.
     int vcycle_reference(bool cont) {
-        const int nu1 = req.opts.nu_pre, nu2 = req.opts.nu_post;
+        const int nu1 = rq->opts.nu_pre, nu2 = rq->opts.nu_post;
         if (!cont)
             for (const auto& S : levels[0].sl)
                 EMF_CUDA(cudaMemsetAsync(S.u, 0, (size_t)S.pitch * S.ny * sizeof(TV), st));
@@ -587,7 +626,7 @@ struct Solver {
     // Fused schedule: wavefront DOWN on large levels, one coarse-tail kernel, wavefront UP.
     // cont = continue from the previous V-cycle's level-0 result (read from uo).
     int vcycle_fused(bool cont) {
-        const int S1 = 2 * req.opts.nu_pre, S2 = 2 * req.opts.nu_post;
+        const int S1 = 2 * rq->opts.nu_pre, S2 = 2 * rq->opts.nu_post;
         for (int k = 0; k < Kw; ++k) {
             const auto& L = levels[k];
             const bool from_prev = cont && k == 0;
@@ -613,15 +652,15 @@ struct Solver {
     int top_pass(const To* o) {
         if (MODE == 2) {
             KernelScope ks("update_iterate", st, top_cells * (2.0 * sizeof(TF) + sizeof(TV)));
-            k_update<TF, TV><<<(unsigned)top_tiles, 256, 0, st>>>(d_top, d_top_ts, (int)req.nslices, d_active, d);
+            k_update<TF, TV><<<(unsigned)top_tiles, 256, 0, st>>>(d_top, d_top_ts, (int)rq->nslices, d_active, d);
             EMF_CHECK_LAUNCH();
         }
-        const double in_b = req.rhs ? 4.0 : 4.0 + sizeof(To);
+        const double in_b = rq->rhs ? 4.0 : 4.0 + sizeof(To);
         const double it_b = MODE == 0 ? 0.0 : (MODE == 1 ? sizeof(TV) + sizeof(TF) : sizeof(TF));
         const double bytes = top_cells * (in_b + it_b + sizeof(TV));
         KernelScope ks(MODE == 0 ? "residual_first" : "residual_update", st, bytes);
         k_top<TF, TV, To, MODE><<<(unsigned)top_tiles, 256, 0, st>>>(
-            d_top, d_top_ts, (int)req.nslices, d_active, req.s, o, req.rhs, d, req.alpha, d_norms);
+            d_top, d_top_ts, (int)rq->nslices, d_active, rq->s, o, rq->rhs, d, rq->alpha, d_norms);
         EMF_CHECK_LAUNCH();
         return EMFUSE_OK;
     }
@@ -629,13 +668,13 @@ struct Solver {
     template <class To>
     int run(const To* o) {
         EMF_TRY(build());
-        const int64_t n = req.nslices;
+        const int64_t n = rq->nslices;
         int64_t total = 0;
-        for (int64_t j = 0; j < n; ++j) total = std::max(total, req.offsets[j] + req.nx[j] * req.ny[j]);
+        for (int64_t j = 0; j < n; ++j) total = std::max(total, rq->offsets[j] + rq->nx[j] * rq->ny[j]);
         if (std::is_same<TF, float>::value) {
-            d = reinterpret_cast<TF*>(req.out);  // the correction lives in the output buffer
+            d = reinterpret_cast<TF*>(rq->out);  // the correction lives in the output buffer
         } else {
-            EMF_TRY(ws_f.alloc((size_t)total * sizeof(TF), st));
+            if (ws_f.bytes() < (size_t)total * sizeof(TF)) EMF_TRY(ws_f.alloc_persistent((size_t)total * sizeof(TF)));
             d = ws_f.as<TF>();
         }
         std::vector<int> active(n, 1), vcycles(n, 0);
@@ -643,7 +682,7 @@ struct Solver {
         std::vector<char> done(n, 0);
         EMF_CUDA(cudaMemcpyAsync(d_active, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
         EMF_CUDA(cudaMemsetAsync(d_norms, 0, 2 * n * sizeof(double), st));
-        const int maxit = std::max(0, req.opts.max_vcycles);
+        const int maxit = std::max(0, rq->opts.max_vcycles);
         int vdone = 0;
         bool all_done = false;
         int rc = EMFUSE_OK;
@@ -669,7 +708,7 @@ struct Solver {
                 if (it == 0) bnorm[j] = std::sqrt(norms[2 * j + 1]);
                 const double rr = norms[2 * j];
                 rel[j] = bnorm[j] > 0 ? std::sqrt(rr) / bnorm[j] : std::sqrt(rr);
-                if (rel[j] <= req.opts.tol || !std::isfinite(rel[j])) {
+                if (rel[j] <= rq->opts.tol || !std::isfinite(rel[j])) {
                     done[j] = 1;
                     active[j] = 0;
                 } else {
@@ -680,7 +719,7 @@ struct Solver {
             EMF_CUDA(cudaMemcpyAsync(d_active, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
             // the first outer iteration runs first_vcycles V-cycles in FP32, each continuing
             // from the previous one's correction, before the first FP64 residual
-            const int nv = it == 0 ? std::min(req.opts.first_vcycles, maxit - vdone) : 1;
+            const int nv = it == 0 ? std::min(rq->opts.first_vcycles, maxit - vdone) : 1;
             for (int v = 0; v < nv; ++v) {
                 EMF_TRY(fused ? vcycle_fused(v > 0) : vcycle_reference(v > 0));
                 for (int64_t j = 0; j < n; ++j)
@@ -694,23 +733,23 @@ struct Solver {
         std::vector<char> never(n, 0);
         for (int64_t j = 0; j < n; ++j) never[j] = vcycles[j] == 0;
         for (int64_t j = 0; j < n; ++j)
-            if (never[j]) EMF_CUDA(cudaMemsetAsync(d + req.offsets[j], 0, (size_t)(req.nx[j] * req.ny[j]) * sizeof(TF), st));
+            if (never[j]) EMF_CUDA(cudaMemsetAsync(d + rq->offsets[j], 0, (size_t)(rq->nx[j] * rq->ny[j]) * sizeof(TF), st));
         {
-            KernelScope ks("store_output", st, (double)total * (sizeof(TF) + (req.rhs ? 0 : sizeof(To)) + 4.0));
-            const To* oo = req.rhs ? nullptr : o;
+            KernelScope ks("store_output", st, (double)total * (sizeof(TF) + (rq->rhs ? 0 : sizeof(To)) + 4.0));
+            const To* oo = rq->rhs ? nullptr : o;
             if (std::is_same<TV, double>::value)
-                k_store<TF, To, true><<<grid_for(total, 256), 256, 0, st>>>(d, oo, req.out, total);
+                k_store<TF, To, true><<<grid_for(total, 256), 256, 0, st>>>(d, oo, rq->out, total);
             else
-                k_store<TF, To, false><<<grid_for(total, 256), 256, 0, st>>>(d, oo, req.out, total);
+                k_store<TF, To, false><<<grid_for(total, 256), 256, 0, st>>>(d, oo, rq->out, total);
             EMF_CHECK_LAUNCH();
         }
         bool nonfinite = false;
-        if (req.stats) {
+        if (rq->stats) {
             for (int64_t j = 0; j < n; ++j) {
-                req.stats[j].vcycles = vcycles[j];
-                req.stats[j].rel_residual = rel[j];
-                req.stats[j].b_norm = bnorm[j];
-                req.stats[j].converged = rel[j] <= req.opts.tol ? 1 : 0;
+                rq->stats[j].vcycles = vcycles[j];
+                rq->stats[j].rel_residual = rel[j];
+                rq->stats[j].b_norm = bnorm[j];
+                rq->stats[j].converged = rel[j] <= rq->opts.tol ? 1 : 0;
             }
         }
         for (int64_t j = 0; j < n; ++j) nonfinite |= !std::isfinite(rel[j]);
@@ -727,11 +766,49 @@ struct Solver {
     }
 };
 
+// Solver plans (descriptor tables, TMA tensor maps, multigrid pyramids, FP64 iterate) are
+// kept between calls, one per (device, stream, precision), and rebuilt when the slice
+// geometry or the schedule options change.  A plan is used by one call at a time.
+struct PlanEntry {
+    int dev;
+    cudaStream_t st;
+    int prec;
+    std::shared_ptr<void> solver;
+    std::shared_ptr<std::mutex> mu;
+};
+std::mutex g_plans_mu;
+// heap-allocated and never destroyed: no CUDA call from a static destructor at process exit
+std::vector<PlanEntry>& g_plans = *new std::vector<PlanEntry>();
+constexpr size_t kMaxPlans = 4;
+
 template <class TF, class TV>
 int run_precision(const SolveRequest& req, cudaStream_t st) {
-    Solver<TF, TV> solver(req, st);
-    if (req.rhs || req.o_dtype == EMFUSE_F32) return solver.run(static_cast<const float*>(req.o));
-    return solver.run(static_cast<const uint8_t*>(req.o));
+    int dev = 0;
+    EMF_CUDA(cudaGetDevice(&dev));
+    const int prec = req.opts.precision;
+    std::shared_ptr<Solver<TF, TV>> solver;
+    std::shared_ptr<std::mutex> mu;
+    {
+        std::lock_guard<std::mutex> lk(g_plans_mu);
+        for (auto& e : g_plans)
+            if (e.dev == dev && e.st == st && e.prec == prec) {
+                solver = std::static_pointer_cast<Solver<TF, TV>>(e.solver);
+                mu = e.mu;
+            }
+        if (!solver) {
+            if (g_plans.size() >= kMaxPlans) g_plans.erase(g_plans.begin());
+            solver = std::make_shared<Solver<TF, TV>>(st);
+            mu = std::make_shared<std::mutex>();
+            g_plans.push_back(PlanEntry{dev, st, prec, solver, mu});
+        }
+    }
+    std::lock_guard<std::mutex> lk(*mu);
+    solver->rq = &req;
+    int rc;
+    if (req.rhs || req.o_dtype == EMFUSE_F32) rc = solver->run(static_cast<const float*>(req.o));
+    else rc = solver->run(static_cast<const uint8_t*>(req.o));
+    if (rc != EMFUSE_OK && rc != EMFUSE_ENOCONV) solver->built = false;  // rebuild after an error
+    return rc;
 }
 
 // ---------------------------------------------------------------- adjoint helpers
@@ -781,6 +858,11 @@ int solve_batch(const SolveRequest& req, cudaStream_t st) {
         case EMFUSE_PREC_FP64: return run_precision<double, double>(req, st);
         default: set_error("unknown precision mode"); return EMFUSE_EINVAL;
     }
+}
+
+void release_plans() {
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    g_plans.clear();
 }
 
 int apply_laplacian_stack(const float* in, float* out, int64_t nx, int64_t ny, int64_t nz,
