@@ -146,7 +146,7 @@ constexpr int kTopTY = 16;
 // Tiles read d on a one-cell halo, so d is never written by a kernel that reads it on a
 // halo (MODE 1 reads e and writes d).  Arithmetic on d and r in TF (FP64 when mixed); the
 // FP64 work per cell is the 5-point operator on d and the squared residual.
-template <class TF, class TV, class To, int MODE>
+template <class TF, class TV, class To, int MODE, bool EXACT>
 __global__ void __launch_bounds__(256)
 k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, int nslices,
       const int* __restrict__ active, const float* __restrict__ s, const To* __restrict__ o,
@@ -206,19 +206,26 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
                 bbf = fmaf(b, b, bbf);
             }
         }
-        TF r;
+        TV rv;
         if (MODE == 0) {
-            r = TF(bc);
+            rv = TV(bc);
         } else {
             const TF c = dsm[ly + 1][lx + 1];
             const TF nsum = (dsm[ly + 1][lx] + dsm[ly + 1][lx + 2]) + (dsm[ly][lx + 1] + dsm[ly + 2][lx + 1]);
             const int deg = int(hw) + int(he) + int(hn) + int(hs);
             const TF adeg = deg == 4 ? ad4 : (deg == 3 ? ad3 : (deg == 2 ? ad2 : (deg == 1 ? ad1 : TF(alpha))));
+            // A d in TF (FP64 when mixed): the operator on the high-precision iterate, where
+            // the cancellation between alpha d + L d and the right-hand side happens
             const TF Ad = fma_t(adeg, c, -nsum);
-            r = TF(bc) - Ad;
+            // r = bc - A d.  bc = alpha (s - o) is formed in FP32, so its own rounding (~6e-8
+            // |bc|) bounds what FP64 could add here: unless EXACT, A d is rounded to the
+            // V-cycle type before the subtraction (same order of error, FP64 work 5 ops per
+            // cell instead of 7).  That caps the reachable relative residual near
+            // 6e-8 ||bc|| / ||b||; tolerances below 1e-7 select EXACT.
+            if (!EXACT && sizeof(TV) < sizeof(TF)) rv = TV(bc) - TV(Ad);
+            else rv = TV(TF(bc) - Ad);
             if (MODE == 1) d[p] = c;
         }
-        const TV rv = TV(r);
         r0[(int64_t)y * G.pitch0 + x] = rv;
         const float rf = float(rv);
         rrf = fmaf(rf, rf, rrf);
@@ -659,8 +666,12 @@ struct Solver {
         const double it_b = MODE == 0 ? 0.0 : (MODE == 1 ? sizeof(TV) + sizeof(TF) : sizeof(TF));
         const double bytes = top_cells * (in_b + it_b + sizeof(TV));
         KernelScope ks(MODE == 0 ? "residual_first" : "residual_update", st, bytes);
-        k_top<TF, TV, To, MODE><<<(unsigned)top_tiles, 256, 0, st>>>(
-            d_top, d_top_ts, (int)rq->nslices, d_active, rq->s, o, rq->rhs, d, rq->alpha, d_norms);
+        if (rq->opts.tol < 1e-7)
+            k_top<TF, TV, To, MODE, true><<<(unsigned)top_tiles, 256, 0, st>>>(
+                d_top, d_top_ts, (int)rq->nslices, d_active, rq->s, o, rq->rhs, d, rq->alpha, d_norms);
+        else
+            k_top<TF, TV, To, MODE, false><<<(unsigned)top_tiles, 256, 0, st>>>(
+                d_top, d_top_ts, (int)rq->nslices, d_active, rq->s, o, rq->rhs, d, rq->alpha, d_norms);
         EMF_CHECK_LAUNCH();
         return EMFUSE_OK;
     }
