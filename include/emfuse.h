@@ -105,6 +105,30 @@ int emfuse_smooth_z(const void* in, int dt, float* out, int64_t nx, int64_t ny, 
                     void* stream);
 
 /*
+ * Allocation-free smoothing.  The paper has no counterpart: this is a deployment variant of
+ * emfuse_smooth_z for callers that cannot allocate device memory while they run (a host whose
+ * device memory all belongs to its own pool or a fixed budget, or a latency-critical loop in
+ * which cudaMalloc / cudaFree would synchronise the device).
+ *
+ * Same arguments, layout and result as emfuse_smooth_z (within float rounding: it always runs
+ * the plain-load fused kernel).  Its only scratch, the per-axis normaliser tables, lives in a
+ * static device array of 3 * 32768 floats (384 KiB) that every GPU loading this library holds
+ * until the process exits; it calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ *   Limits: nx + ny + nz <= 98304, floor(3 sigma_xy) <= 8, floor(3 sigma_z) <= 9; beyond
+ *           them it returns EMFUSE_EINVAL with a message naming the limit.
+ *   Set-up: the first call on each device looks up the array's device address (with that
+ *           device current).  Make that first call before capturing any stream into a graph.
+ *   Sharing: all calls share the one array, and each call rewrites the whole table it reads,
+ *           stream-ordered on `stream`.  Calls that can overlap on the GPU (different streams
+ *           without ordering between them, or different host threads) race on it.
+ * Asynchronous on `stream`.
+ */
+int emfuse_smooth_z_noalloc(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                            int64_t pitch, int64_t z0, int64_t z1, float sigma_xy, float sigma_z,
+                            void* stream);
+
+/*
  * Phase 2: per-slice screened-Poisson solve, Eq. (1): (alpha I + L) f_j = alpha s_j + L o_j
  * (Sec. 3 "Screened-Poisson Blending"), by multigrid V-cycles (Sec. 3 "Implementation").
  *

@@ -18,7 +18,7 @@ from . import build as _build
 
 __all__ = [
     "EmfuseError", "EmfuseUnavailable", "SolveOpts", "SliceStats", "lib", "library_path",
-    "default_opts", "emfuse_smooth_z", "emfuse_screened_poisson", "emfuse_correct_stack",
+    "default_opts", "emfuse_smooth_z", "emfuse_smooth_z_noalloc", "emfuse_screened_poisson", "emfuse_correct_stack",
     "emfuse_backward", "emfuse_version", "emfuse_release_cache", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
     "PREC_FP64", "EXPORTED_SYMBOLS",
 ]
@@ -30,7 +30,7 @@ STATUS = {0: "EMFUSE_OK", 1: "EMFUSE_EINVAL", 2: "EMFUSE_ECUDA", 3: "EMFUSE_ENOM
 EXPORTED_SYMBOLS = ["emfuse_default_opts", "emfuse_smooth_z", "emfuse_screened_poisson",
                     "emfuse_correct_stack", "emfuse_backward", "emfuse_last_error",
                     "emfuse_version", "emfuse_kernel_launches", "emfuse_profile_begin",
-                    "emfuse_profile_end", "emfuse_release_cache"]
+                    "emfuse_profile_end", "emfuse_release_cache", "emfuse_smooth_z_noalloc"]
 
 
 class EmfuseError(RuntimeError):
@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
             L.emfuse_default_opts.argtypes = [ctypes.POINTER(SolveOpts)]
             L.emfuse_default_opts.restype = None
             L.emfuse_smooth_z.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
+            L.emfuse_smooth_z_noalloc.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
             L.emfuse_screened_poisson.argtypes = [vp, vp, vp, i64, vp, vp, vp, db,
                                                   ctypes.POINTER(SolveOpts), vp, vp]
             L.emfuse_correct_stack.argtypes = [vp, ci, ci, vp, i64, i64, i64, fl, fl, db,
@@ -83,7 +84,7 @@ def lib() -> ctypes.CDLL:
             L.emfuse_backward.argtypes = [vp, vp, vp, vp, ci, i64, i64, i64, fl, fl, db, vp, vp, vp,
                                           vp, vp, ctypes.POINTER(SolveOpts), vp]
             for name in ("emfuse_smooth_z", "emfuse_screened_poisson", "emfuse_correct_stack",
-                         "emfuse_backward"):
+                         "emfuse_backward", "emfuse_smooth_z_noalloc"):
                 getattr(L, name).restype = ci
             L.emfuse_last_error.restype = ctypes.c_char_p
             L.emfuse_last_error.argtypes = []
@@ -158,6 +159,20 @@ def emfuse_smooth_z(stack: torch.Tensor, sigma_xy: float = 1.0, sigma_z: float =
     _require_cuda(out)
     _check(lib().emfuse_smooth_z(stack.data_ptr(), _dtype_code(stack), out.data_ptr(), nx, ny, nz,
                                  nx, z0, z1, float(sigma_xy), float(sigma_z), _stream_ptr(stack.device)))
+    return out
+
+
+def emfuse_smooth_z_noalloc(stack: torch.Tensor, sigma_xy: float, sigma_z: float, out: torch.Tensor,
+                            z0: int = 0, z1: int | None = None) -> torch.Tensor:
+    """Allocation-free variant of :func:`emfuse_smooth_z` (the library allocates no device
+    memory; ``out`` is the caller's).  Calls that overlap on the GPU race on its shared scratch."""
+    _require_cuda(stack)
+    _require_cuda(out)
+    nz, ny, nx = stack.shape
+    z1 = nz if z1 is None else z1
+    _check(lib().emfuse_smooth_z_noalloc(stack.data_ptr(), _dtype_code(stack), out.data_ptr(), nx, ny,
+                                         nz, nx, z0, z1, float(sigma_xy), float(sigma_z),
+                                         _stream_ptr(stack.device)))
     return out
 
 

@@ -22,6 +22,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "emfuse_common.cuh"
@@ -568,4 +570,123 @@ int smooth_dsigma_z(const void* in, int dt, float* out, int64_t nx, int64_t ny, 
     return EMFUSE_OK;
 }
 
+// ---------------------------------------------------------------- allocation-free variant
+// emfuse_smooth_z_noalloc runs smooth_fused_kernel with its only scratch, the three per-axis
+// tables of inverse normalisers, in a file-scope device array instead of memory from the CUDA
+// allocator.  It exists for callers that cannot allocate device memory while they run: a host
+// that has handed all device memory to its own pool or works under a fixed memory budget, and
+// code on a latency-critical path where cudaMalloc / cudaFree would synchronise the device.
+// Every GPU that loads this library holds the array (kNoAllocMaxNorms floats, 384 KiB) until
+// the process exits.
+constexpr int64_t kNoAllocMaxNorms = 3 * 32768;  // nx + ny + nz of one call
+static __device__ __align__(256) float g_noalloc_norms[kNoAllocMaxNorms];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[64] = {nullptr};
+
+// Device address of g_noalloc_norms on the current device, looked up once per device with
+// that device current (in host code the array's name is only a host-side stand-in).
+int noalloc_norms(float** out) {
+    int dev = 0;
+    EMF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("emfuse_smooth_z_noalloc: device ordinal out of range");
+        return EMFUSE_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_norms);
+        if (e != cudaSuccess || !p) {
+            set_error(std::string("emfuse_smooth_z_noalloc: cudaGetSymbolAddress failed: ") +
+                      cudaGetErrorString(e));
+            return EMFUSE_ECUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<float*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return EMFUSE_OK;
+}
+
+}  // namespace
+
 }  // namespace emfuse
+
+extern "C" int emfuse_smooth_z_noalloc(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                                       int64_t pitch, int64_t z0, int64_t z1, float sigma_xy, float sigma_z,
+                                       void* stream) {
+    using namespace emfuse;
+    set_error("");
+    if (!in || !out) {
+        set_error("emfuse_smooth_z_noalloc: null pointer");
+        return EMFUSE_EINVAL;
+    }
+    if (dt != EMFUSE_U8 && dt != EMFUSE_F32) {
+        set_error("emfuse_smooth_z_noalloc: dtype must be EMFUSE_U8 or EMFUSE_F32");
+        return EMFUSE_EINVAL;
+    }
+    if (nx < 1 || ny < 1 || nz < 1 || pitch < nx || z0 < 0 || z1 > nz || z0 >= z1) {
+        set_error("emfuse_smooth_z_noalloc: need sizes >= 1, pitch >= nx and 0 <= z0 < z1 <= nz");
+        return EMFUSE_EINVAL;
+    }
+    if (nx + ny + nz > kNoAllocMaxNorms) {
+        set_error("emfuse_smooth_z_noalloc: nx + ny + nz = " + std::to_string(nx + ny + nz) +
+                  " exceeds the static scratch of " + std::to_string(kNoAllocMaxNorms) +
+                  " entries; use emfuse_smooth_z");
+        return EMFUSE_EINVAL;
+    }
+    if (!std::isfinite(sigma_xy) || !std::isfinite(sigma_z) || sigma_xy < 0.f || sigma_z < 0.f) {
+        set_error("emfuse_smooth_z_noalloc: sigma_xy and sigma_z must be finite and >= 0");
+        return EMFUSE_EINVAL;
+    }
+    const int Rxy = support_radius(sigma_xy), Rz = support_radius(sigma_z);
+    if (Rxy > kMaxRxy || Rz > 9) {
+        set_error("emfuse_smooth_z_noalloc: needs floor(3 sigma_xy) <= 8 and floor(3 sigma_z) <= 9; wider "
+                  "supports need temporaries, use emfuse_smooth_z");
+        return EMFUSE_EINVAL;
+    }
+    const cudaStream_t st = (cudaStream_t)stream;
+    float* norms = nullptr;
+    EMF_TRY(noalloc_norms(&norms));
+    const auto wxy = gaussian_taps(sigma_xy, Rxy);
+    const auto wz = gaussian_taps(sigma_z, Rz);
+    std::vector<float> host = inverse_norms(wxy, (int)nx);
+    const auto iy = inverse_norms(wxy, (int)ny), iz = inverse_norms(wz, (int)nz);
+    host.insert(host.end(), iy.begin(), iy.end());
+    host.insert(host.end(), iz.begin(), iz.end());
+    // Stream-ordered after earlier work on `st`; a copy from pageable memory has read `host`
+    // by the time it returns.  Every entry of the table that the kernel reads is written here.
+    EMF_CUDA(cudaMemcpyAsync(norms, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    const float* inv_x = norms;
+    const float* inv_y = inv_x + nx;
+    const float* inv_z = inv_y + ny;
+    SmoothParams prm{};
+    prm.Rxy = Rxy;
+    prm.Rz = Rz;
+    for (int d = 0; d < 2 * Rxy + 1; ++d) prm.wxy[d] = wxy[d];
+    for (int j = 0; j < 2 * Rz + 1; ++j) prm.wz[j] = wz[2 * Rz - j];
+    const dim3 grid((unsigned)ceil_div(nx, kTX), (unsigned)ceil_div(ny, kTY));
+    const int P = 2 * Rz + 1;
+    const int64_t zin0 = std::max<int64_t>(0, z0 - Rz), zin1 = std::min<int64_t>(nz, z1 + Rz);
+    KernelScope ks("smooth_noalloc", st,
+                   (double)nx * ny * ((zin1 - zin0) * (dt == EMFUSE_U8 ? 1.0 : 4.0) + (z1 - z0) * 4.0));
+#define EMF_NOALLOC_LAUNCH(PP)                                                               \
+    do {                                                                                     \
+        if (dt == EMFUSE_U8)                                                                 \
+            smooth_fused_kernel<uint8_t, PP><<<grid, kThreads, 0, st>>>(                     \
+                (const uint8_t*)in, out, (int)nx, (int)ny, (int)nz, pitch, (int)z0, (int)z1, \
+                inv_x, inv_y, inv_z, prm);                                                   \
+        else                                                                                 \
+            smooth_fused_kernel<float, PP><<<grid, kThreads, 0, st>>>(                       \
+                (const float*)in, out, (int)nx, (int)ny, (int)nz, pitch, (int)z0, (int)z1,   \
+                inv_x, inv_y, inv_z, prm);                                                   \
+    } while (0)
+    if (P <= 1) EMF_NOALLOC_LAUNCH(1);
+    else if (P <= 7) EMF_NOALLOC_LAUNCH(7);
+    else EMF_NOALLOC_LAUNCH(19);
+#undef EMF_NOALLOC_LAUNCH
+    EMF_CHECK_LAUNCH();
+    return EMFUSE_OK;
+}
