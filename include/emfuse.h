@@ -220,6 +220,17 @@ int emfuse_profile_end(emfuse_kernel_profile* out, int max_entries);
  */
 void emfuse_release_cache(void);
 
+/*
+ * Self-test of the integer-pipe binary32 <-> binary64 conversions used by the FP64 residual
+ * kernels (no counterpart in the paper: an implementation check).  Runs on the current device,
+ * synchronously: every binary32 bit pattern is widened and compared with the hardware
+ * conversion, and 7 x 2^32 binary64 values (rounding-critical low bits around every binary32
+ * value, plus pseudo-random bit patterns) are rounded and compared.  Writes the mismatch
+ * counts (0 and 0 expected; NaNs match any NaN) to the two HOST pointers.  Allocates and frees
+ * 16 bytes of device memory.  Takes well under a second on one GPU.
+ */
+int emfuse_selftest_fpconv(int64_t* f2d_mismatches, int64_t* d2f_mismatches);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* emfuse_last_error(void);
 

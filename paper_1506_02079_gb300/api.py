@@ -30,7 +30,8 @@ STATUS = {0: "EMFUSE_OK", 1: "EMFUSE_EINVAL", 2: "EMFUSE_ECUDA", 3: "EMFUSE_ENOM
 EXPORTED_SYMBOLS = ["emfuse_default_opts", "emfuse_smooth_z", "emfuse_screened_poisson",
                     "emfuse_correct_stack", "emfuse_backward", "emfuse_last_error",
                     "emfuse_version", "emfuse_kernel_launches", "emfuse_profile_begin",
-                    "emfuse_profile_end", "emfuse_release_cache", "emfuse_smooth_z_noalloc"]
+                    "emfuse_profile_end", "emfuse_release_cache", "emfuse_smooth_z_noalloc",
+                    "emfuse_selftest_fpconv"]
 
 
 class EmfuseError(RuntimeError):
@@ -77,6 +78,8 @@ def lib() -> ctypes.CDLL:
             L.emfuse_default_opts.restype = None
             L.emfuse_smooth_z.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
             L.emfuse_smooth_z_noalloc.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
+            L.emfuse_selftest_fpconv.argtypes = [vp, vp]
+            L.emfuse_selftest_fpconv.restype = ci
             L.emfuse_screened_poisson.argtypes = [vp, vp, vp, i64, vp, vp, vp, db,
                                                   ctypes.POINTER(SolveOpts), vp, vp]
             L.emfuse_correct_stack.argtypes = [vp, ci, ci, vp, i64, i64, i64, fl, fl, db,
@@ -174,6 +177,14 @@ def emfuse_smooth_z_noalloc(stack: torch.Tensor, sigma_xy: float, sigma_z: float
                                          nz, nx, z0, z1, float(sigma_xy), float(sigma_z),
                                          _stream_ptr(stack.device)))
     return out
+
+
+def emfuse_selftest_fpconv() -> tuple[int, int]:
+    """Mismatch counts (widening, rounding) of the library's integer-pipe float/double
+    conversions against the hardware conversions on the current CUDA device."""
+    a, b = ctypes.c_int64(-1), ctypes.c_int64(-1)
+    _check(lib().emfuse_selftest_fpconv(ctypes.byref(a), ctypes.byref(b)))
+    return int(a.value), int(b.value)
 
 
 def _pack_slices(s, o):

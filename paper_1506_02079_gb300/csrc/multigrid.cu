@@ -32,6 +32,7 @@
 
 #include "emfuse_common.cuh"
 #include "emfuse_internal.cuh"
+#include "fpconv.cuh"
 #include "mg_fused.cuh"
 #include "tma.cuh"
 
@@ -140,17 +141,21 @@ struct TopSlice {
 constexpr int kTopTX = 64;
 constexpr int kTopTY = 16;
 
-// MODE 0: d = 0, r = alpha (s - o) (first residual; also accumulates ||b||^2)
-// MODE 1: d = e, written back       (first correction)
-// MODE 2: d read only               (later corrections: k_update has added e to d)
-// Tiles read d on a one-cell halo, so d is never written by a kernel that reads it on a
-// halo (MODE 1 reads e and writes d).  Arithmetic on d and r in TF (FP64 when mixed); the
-// FP64 work per cell is the 5-point operator on d and the squared residual.
+// MODE 0: d = 0, r = alpha (s - o)          (first residual; also accumulates ||b||^2)
+// MODE 1: d_new = e                          (first correction)
+// MODE 2: d_new = d_old + e                  (later corrections)
+// and in MODE 1 and 2: r = b - A d_new, out = o + d_new (the solution for the iterate whose
+// residual this pass measures, so the output is always the latest iterate).
+// d_old and d_new are different buffers (they alternate between passes): a tile reads d_old
+// and e on a one-cell halo while its neighbours write d_new.  Arithmetic on d and r in TF
+// (FP64 when mixed); the FP64 work per cell is the 5-point operator on d (and in MODE 2 the
+// update d_old + e).  Conversions between TV and TF run on the integer pipe (fpconv.cuh).
 template <class TF, class TV, class To, int MODE, bool EXACT>
 __global__ void __launch_bounds__(256)
 k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, int nslices,
       const int* __restrict__ active, const float* __restrict__ s, const To* __restrict__ o,
-      const float* __restrict__ rhs, TF* __restrict__ d, double alpha, double* __restrict__ norms) {
+      const float* __restrict__ rhs, const TF* __restrict__ d_old, TF* __restrict__ d_new,
+      float* __restrict__ out, double alpha, double* __restrict__ norms) {
     const int64_t t = blockIdx.x;
     const int j = find_item(tile_start, nslices, t);
     if (active && !active[j]) return;
@@ -167,8 +172,10 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
             const int rr = q / (kTopTX + 2), cc = q - rr * (kTopTX + 2);
             const int gx = tx0 - 1 + cc, gy = ty0 - 1 + rr;
             TF v = TF(0);
-            if (gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny)
-                v = MODE == 1 ? TF(e[(int64_t)gy * G.pitch0 + gx]) : d[G.off + (int64_t)gy * G.nx + gx];
+            if (gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny) {
+                const TF ev = cvt<TF>(e[(int64_t)gy * G.pitch0 + gx]);
+                v = MODE == 1 ? ev : d_old[G.off + (int64_t)gy * G.nx + gx] + ev;
+            }
             dsm[rr][cc] = v;
         }
         __syncthreads();
@@ -188,12 +195,13 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
         if (x >= G.nx || y >= G.ny) continue;
         const int64_t p = G.off + (int64_t)y * G.nx + x;
         const bool hw = x > 0, he = x + 1 < G.nx, hn = y > 0, hs = y + 1 < G.ny;
-        float bc;
+        float bc, ov = 0.f;
         if (rhs) {
             bc = rhs[p];
             if (MODE == 0) bbf = fmaf(bc, bc, bbf);
         } else {
-            const float sv = s[p], ov = float(o[p]);
+            const float sv = s[p];
+            ov = float(o[p]);
             bc = af * (sv - ov);
             if (MODE == 0) {
                 // ||b||^2 with b = alpha s + L o, for the relative-residual denominator
@@ -208,7 +216,7 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
         }
         TV rv;
         if (MODE == 0) {
-            rv = TV(bc);
+            rv = cvt<TV>(bc);
         } else {
             const TF c = dsm[ly + 1][lx + 1];
             const TF nsum = (dsm[ly + 1][lx] + dsm[ly + 1][lx + 2]) + (dsm[ly][lx + 1] + dsm[ly + 2][lx + 1]);
@@ -219,15 +227,21 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
             const TF Ad = fma_t(adeg, c, -nsum);
             // r = bc - A d.  bc = alpha (s - o) is formed in FP32, so its own rounding (~6e-8
             // |bc|) bounds what FP64 could add here: unless EXACT, A d is rounded to the
-            // V-cycle type before the subtraction (same order of error, FP64 work 5 ops per
-            // cell instead of 7).  That caps the reachable relative residual near
-            // 6e-8 ||bc|| / ||b||; tolerances below 1e-7 select EXACT.
-            if (!EXACT && sizeof(TV) < sizeof(TF)) rv = TV(bc) - TV(Ad);
-            else rv = TV(TF(bc) - Ad);
-            if (MODE == 1) d[p] = c;
+            // V-cycle type before the subtraction (same order of error, one FP64 operation per
+            // cell less).  That caps the reachable relative residual near 6e-8 ||bc|| / ||b||;
+            // tolerances below 1e-7 select EXACT.
+            if constexpr (!EXACT && sizeof(TV) < sizeof(TF)) rv = bc - cvt<TV>(Ad);
+            else rv = cvt<TV>(cvt<TF>(bc) - Ad);
+            d_new[p] = c;
+            // output: d alone in the adjoint mode, else o + d (in FP64 when TV is FP64)
+            float f;
+            if (rhs) f = cvt<float>(c);
+            else if constexpr (sizeof(TV) == 8) f = cvt<float>(cvt<double>(ov) + c);
+            else f = ov + cvt<float>(c);
+            out[p] = f;
         }
         r0[(int64_t)y * G.pitch0 + x] = rv;
-        const float rf = float(rv);
+        const float rf = cvt<float>(rv);
         rrf = fmaf(rf, rf, rrf);
     }
 #pragma unroll
@@ -246,38 +260,12 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
     }
 }
 
-// d += e on every cell of the active slices (elementwise; the residual kernel then reads d).
-template <class TF, class TV>
-__global__ void __launch_bounds__(256)
-k_update(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, int nslices,
-         const int* __restrict__ active, TF* __restrict__ d) {
-    const int64_t t = blockIdx.x;
-    const int j = find_item(tile_start, nslices, t);
-    if (active && !active[j]) return;
-    const TopSlice G = top[j];
-    const int lt = int(t - tile_start[j]);
-    const int tx0 = (lt % G.tiles_x) * kTopTX;
-    const int ty0 = (lt / G.tiles_x) * kTopTY;
-    const TV* e = static_cast<const TV*>(G.u0);
-    const int y = ty0 + threadIdx.x / 16;
-    if (y >= G.ny) return;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int x = tx0 + (threadIdx.x % 16) + 16 * i;
-        if (x >= G.nx) continue;
-        const int64_t p = G.off + (int64_t)y * G.nx + x;
-        d[p] = d[p] + TF(e[(int64_t)y * G.pitch0 + x]);
-    }
-}
-
-// out = o + d (or d in the adjoint mode), one pass over the packed slices.
-template <class TF, class To, bool FULL64>
-__global__ void k_store(const TF* __restrict__ d, const To* __restrict__ o, float* __restrict__ out, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (!o) out[i] = float(d[i]);
-        else if (FULL64) out[i] = float(double(o[i]) + double(d[i]));
-        else out[i] = float(o[i]) + float(d[i]);
-    }
+// out = o (or 0 in the adjoint mode) on one slice that was never iterated (it met the
+// tolerance at the initial iterate f = o).
+template <class To>
+__global__ void k_fill_initial(const To* __restrict__ o, float* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = o ? float(o[i]) : 0.f;
 }
 
 inline unsigned grid_for(int64_t n, int threads) {
@@ -331,7 +319,7 @@ struct Solver {
     DeviceBuffer ws_levels, ws_desc, ws_f, ws_norms, ws_active;
     std::vector<int> nlev, kc;
     int Kmax = 0, Kw = 0;       // levels, and levels with wavefront work
-    TF* d = nullptr;
+    TF* dbuf[2] = {nullptr, nullptr};  // FP64 iterates d, alternating between passes
     double* d_norms = nullptr;
     int* d_active = nullptr;
     int* d_err = nullptr;
@@ -655,23 +643,26 @@ struct Solver {
         return EMFUSE_OK;
     }
 
+    // Pass `it` of the outer loop: MODE 0 at it == 0, MODE 1 at it == 1, MODE 2 after that.
+    // The FP64 iterates alternate between the two halves of ws_f (written: it & 1).
     template <class To, int MODE>
-    int top_pass(const To* o) {
-        if (MODE == 2) {
-            KernelScope ks("update_iterate", st, top_cells * (2.0 * sizeof(TF) + sizeof(TV)));
-            k_update<TF, TV><<<(unsigned)top_tiles, 256, 0, st>>>(d_top, d_top_ts, (int)rq->nslices, d_active, d);
-            EMF_CHECK_LAUNCH();
-        }
+    int top_pass(const To* o, int it) {
+        const TF* d_old = dbuf[(it + 1) & 1];
+        TF* d_new = dbuf[it & 1];
+        // algorithmic bytes: s and o (or rhs) read, r written; MODE >= 1 also reads e (and
+        // d_old in MODE 2) and writes d_new and the output
         const double in_b = rq->rhs ? 4.0 : 4.0 + sizeof(To);
-        const double it_b = MODE == 0 ? 0.0 : (MODE == 1 ? sizeof(TV) + sizeof(TF) : sizeof(TF));
+        const double it_b = MODE == 0 ? 0.0 : sizeof(TV) + sizeof(TF) + 4.0 + (MODE == 2 ? sizeof(TF) : 0.0);
         const double bytes = top_cells * (in_b + it_b + sizeof(TV));
         KernelScope ks(MODE == 0 ? "residual_first" : "residual_update", st, bytes);
         if (rq->opts.tol < 1e-7)
             k_top<TF, TV, To, MODE, true><<<(unsigned)top_tiles, 256, 0, st>>>(
-                d_top, d_top_ts, (int)rq->nslices, d_active, rq->s, o, rq->rhs, d, rq->alpha, d_norms);
+                d_top, d_top_ts, (int)rq->nslices, d_active, rq->s, o, rq->rhs, d_old, d_new, rq->out,
+                rq->alpha, d_norms);
         else
             k_top<TF, TV, To, MODE, false><<<(unsigned)top_tiles, 256, 0, st>>>(
-                d_top, d_top_ts, (int)rq->nslices, d_active, rq->s, o, rq->rhs, d, rq->alpha, d_norms);
+                d_top, d_top_ts, (int)rq->nslices, d_active, rq->s, o, rq->rhs, d_old, d_new, rq->out,
+                rq->alpha, d_norms);
         EMF_CHECK_LAUNCH();
         return EMFUSE_OK;
     }
@@ -682,12 +673,11 @@ struct Solver {
         const int64_t n = rq->nslices;
         int64_t total = 0;
         for (int64_t j = 0; j < n; ++j) total = std::max(total, rq->offsets[j] + rq->nx[j] * rq->ny[j]);
-        if (std::is_same<TF, float>::value) {
-            d = reinterpret_cast<TF*>(rq->out);  // the correction lives in the output buffer
-        } else {
-            if (ws_f.bytes() < (size_t)total * sizeof(TF)) EMF_TRY(ws_f.alloc_persistent((size_t)total * sizeof(TF)));
-            d = ws_f.as<TF>();
-        }
+        const int64_t half = round_up(total, 64);
+        if (ws_f.bytes() < (size_t)(2 * half) * sizeof(TF))
+            EMF_TRY(ws_f.alloc_persistent((size_t)(2 * half) * sizeof(TF)));
+        dbuf[0] = ws_f.as<TF>();
+        dbuf[1] = ws_f.as<TF>() + half;
         std::vector<int> active(n, 1), vcycles(n, 0);
         std::vector<double> norms(2 * n), rel(n, 0.0), bnorm(n, 0.0);
         std::vector<char> done(n, 0);
@@ -699,9 +689,9 @@ struct Solver {
         int rc = EMFUSE_OK;
         for (int it = 0;; ++it) {
             if (it > 0) EMF_CUDA(cudaMemsetAsync(d_norms, 0, n * 2 * sizeof(double), st));
-            if (it == 0) rc = top_pass<To, 0>(o);
-            else if (it == 1) rc = top_pass<To, 1>(o);
-            else rc = top_pass<To, 2>(o);
+            if (it == 0) rc = top_pass<To, 0>(o, it);
+            else if (it == 1) rc = top_pass<To, 1>(o, it);
+            else rc = top_pass<To, 2>(o, it);
             if (rc != EMFUSE_OK) return rc;
             EMF_CUDA(cudaMemcpyAsync(norms.data(), d_norms, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
             int err_flag = 0;
@@ -738,20 +728,14 @@ struct Solver {
             }
             vdone += nv;
         }
-        // Slices that converged at the first residual kept d = 0; the others hold d in the
-        // d buffer, except in MODE 1/2 only active slices were written.  Slices done at it == 0
-        // never had d written: clear them before the store.
-        std::vector<char> never(n, 0);
-        for (int64_t j = 0; j < n; ++j) never[j] = vcycles[j] == 0;
-        for (int64_t j = 0; j < n; ++j)
-            if (never[j]) EMF_CUDA(cudaMemsetAsync(d + rq->offsets[j], 0, (size_t)(rq->nx[j] * rq->ny[j]) * sizeof(TF), st));
-        {
-            KernelScope ks("store_output", st, (double)total * (sizeof(TF) + (rq->rhs ? 0 : sizeof(To)) + 4.0));
-            const To* oo = rq->rhs ? nullptr : o;
-            if (std::is_same<TV, double>::value)
-                k_store<TF, To, true><<<grid_for(total, 256), 256, 0, st>>>(d, oo, rq->out, total);
-            else
-                k_store<TF, To, false><<<grid_for(total, 256), 256, 0, st>>>(d, oo, rq->out, total);
+        // Every residual pass after the first wrote the output of the slices it covered; slices
+        // that met the tolerance at the initial iterate get f = o here.
+        for (int64_t j = 0; j < n; ++j) {
+            if (vcycles[j] != 0) continue;
+            const int64_t cells = rq->nx[j] * rq->ny[j];
+            KernelScope ks("store_initial", st, (double)cells * ((rq->rhs ? 0 : sizeof(To)) + 4.0));
+            k_fill_initial<To><<<grid_for(cells, 256), 256, 0, st>>>(rq->rhs ? nullptr : o + rq->offsets[j],
+                                                                     rq->out + rq->offsets[j], cells);
             EMF_CHECK_LAUNCH();
         }
         bool nonfinite = false;

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "emfuse_common.cuh"
+#include "fpconv.cuh"
 #include "tma.cuh"
 
 namespace emfuse {
@@ -137,6 +138,52 @@ int* device_error_flag() {
     return flags[dev];
 }
 
+// ---------------------------------------------------------------- conversion self-test
+namespace {
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    // SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number generators", 2014)
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+__device__ __forceinline__ bool same_double(double a, double b) {
+    return (a != a) ? (b != b) : __double_as_longlong(a) == __double_as_longlong(b);
+}
+__device__ __forceinline__ bool same_float(float a, float b) {
+    return (a != a) ? (b != b) : __float_as_uint(a) == __float_as_uint(b);
+}
+
+// Every binary32 bit pattern u: f2d_ieee against the hardware widening; d2f_ieee against the
+// hardware rounding on the widened value with the 29 bits below binary32 precision set to
+// rounding-critical patterns (just above zero, just below / at / just above the half, all
+// ones, a quarter), and on one SplitMix64 bit pattern per u (every binary64 exponent,
+// including the ranges that underflow to subnormals or overflow).
+__global__ void k_selftest_fpconv(unsigned long long* bad) {
+    unsigned long long nf = 0, nd = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (1ull << 32); i += stride) {
+        const float f = __uint_as_float((uint32_t)i);
+        const double w = f2d_ieee(f);
+        nf += !same_double(w, (double)f);
+        const uint32_t hi = (uint32_t)__double2hiint(w), lo = (uint32_t)__double2loint(w);
+        const uint32_t lows[6] = {1u, 0x0fffffffu, 0x10000000u, 0x10000001u, 0x1fffffffu, 0x08000000u};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const double x = __hiloint2double((int)hi, (int)((lo & 0xe0000000u) | lows[k]));
+            nd += !same_float(d2f_ieee(x), (float)x);
+        }
+        const double r = __longlong_as_double((long long)splitmix64(i));
+        nd += !same_float(d2f_ieee(r), (float)r);
+    }
+    if (nf) atomicAdd(&bad[0], nf);
+    if (nd) atomicAdd(&bad[1], nd);
+}
+
+}  // namespace
+
 }  // namespace emfuse
 
 using namespace emfuse;
@@ -187,6 +234,31 @@ int emfuse_profile_end(emfuse_kernel_profile* out, int max_entries) {
         out[i].bytes = v[i].second.bytes;
     }
     return (int)v.size();
+}
+
+int emfuse_selftest_fpconv(int64_t* f2d_mismatches, int64_t* d2f_mismatches) {
+    set_error("");
+    if (!f2d_mismatches || !d2f_mismatches) {
+        set_error("emfuse_selftest_fpconv: null pointer");
+        return EMFUSE_EINVAL;
+    }
+    unsigned long long* bad = nullptr;
+    EMF_CUDA(cudaMalloc(&bad, 2 * sizeof(unsigned long long)));
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemset(bad, 0, sizeof(h));
+    if (e == cudaSuccess) {
+        k_selftest_fpconv<<<kNumSMs * 8, 256>>>(bad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h, bad, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(bad);
+    if (e != cudaSuccess) {
+        set_error(std::string("emfuse_selftest_fpconv: ") + cudaGetErrorString(e));
+        return EMFUSE_ECUDA;
+    }
+    *f2d_mismatches = (int64_t)h[0];
+    *d2f_mismatches = (int64_t)h[1];
+    return EMFUSE_OK;
 }
 
 }  // extern "C"

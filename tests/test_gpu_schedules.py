@@ -81,3 +81,23 @@ def test_vcycle_contraction(dev):
         res.append(max(x["rel_residual"] for x in st))
     rates = [res[i + 1] / res[i] for i in range(len(res) - 1)]
     assert max(rates) < 0.1, rates
+
+
+def test_integer_pipe_conversions_match_hardware(dev):
+    """The residual kernels widen and round between FP32 and FP64 with integer operations;
+    every binary32 pattern and 7 x 2^32 binary64 patterns must match the hardware bit for bit."""
+    assert api.emfuse_selftest_fpconv() == (0, 0)
+
+
+def test_slices_met_at_initial_iterate_return_o(dev):
+    """A slice with s = o has r = 0 at f = o and is never iterated; its output must still be
+    written (f = o) while the other slices of the batch iterate, in every precision."""
+    I0 = make_stack(3, 96, 80, seed=4).to(dev)
+    s = api.emfuse_smooth_z(I0, 1.0, 3.0)
+    s[1] = I0[1]
+    for prec in (api.PREC_FP32, api.PREC_MIXED, api.PREC_FP64):
+        f, st = solve(s, I0, 1e-2, precision=prec)
+        assert st[1]["vcycles"] == 0 and st[0]["vcycles"] > 0
+        assert torch.equal(f[1], I0[1])
+        f0, _ = solve(s, I0, 1e-2, precision=prec, max_vcycles=0)
+        assert torch.equal(f0, I0)
