@@ -27,6 +27,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "emfuse_common.cuh"
 #include "mg_fused.cuh"
 #include "tma.cuh"
@@ -171,12 +173,12 @@ __device__ __forceinline__ Coef<T> cached_coef(uint32_t cache, int i) {
 }
 
 // Half-sweep of one colour on one row of the lane's 4 cells (cells f and f + 2).
-template <class T>
+template <class T, bool FAST>
 __device__ __forceinline__ void sweep_row(T (&row)[4], const T (&brow)[4], const T (&nrow)[4], const T (&srow)[4],
                                           int f, T west, T east, bool fast, bool irow, uint32_t cache,
                                           const StencilTab<T>& tab, int xlane, int r, int nx, int ny, int n0x,
                                           int n0y, int k, T alpha, T sk) {
-    if (fast) {
+    if (FAST || fast) {
         if (f == 0) {
             row[0] = gs_update<T>(tab.ci, brow[0], west, row[1], nrow[0], srow[0]);
             row[2] = gs_update<T>(tab.ci, brow[2], row[1], row[3], nrow[2], srow[2]);
@@ -198,7 +200,7 @@ __device__ __forceinline__ void sweep_row(T (&row)[4], const T (&brow)[4], const
 }
 
 // Residuals of one row of the lane's 4 cells.
-template <class T>
+template <class T, bool FAST>
 __device__ __forceinline__ void residual_row(T (&res)[4], const T (&row)[4], const T (&brow)[4], const T (&nrow)[4],
                                              const T (&srow)[4], T west, T east, bool fast, bool irow,
                                              uint32_t cache, const StencilTab<T>& tab, int xlane, int r, int nx,
@@ -207,7 +209,7 @@ __device__ __forceinline__ void residual_row(T (&res)[4], const T (&row)[4], con
     for (int i = 0; i < 4; ++i) {
         const T uw = i == 0 ? west : row[i - 1];
         const T ue = i == 3 ? east : row[i + 1];
-        const Coef<T> c = fast ? tab.ci
+        const Coef<T> c = (FAST || fast) ? tab.ci
                                : (irow ? cached_coef<T>(cache, i)
                                        : edge_coef<T>(tab, xlane + i, r, nx, ny, n0x, n0y, k, alpha, sk));
         res[i] = residual_at<T>(c, brow[i], row[i], uw, ue, nrow[i], srow[i]);
@@ -265,8 +267,11 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     const CUtensorMap* map_c = a.maps + 4 * j + 2;
     const CUtensorMap* map_u = a.maps + 4 * j + a.u_map;
     const int li = int(item - a.item_start[j]);
-    const int strip = li % L.fstrips;
-    const int chunk = li / L.fstrips;
+    // consecutive items walk down one strip, so the warps of a CTA share a strip (edge strips,
+    // which take the general step body, then share CTAs with each other)
+    const int nchunks = (L.ny + a.ch - 1) / a.ch;
+    const int strip = li / nchunks;
+    const int chunk = li - strip * nchunks;
     const int X0 = strip * kWaveIW - kWaveHalo;
     const int Y0 = chunk * a.ch;                  // even
     const int Y1 = min(Y0 + a.ch, L.ny);
@@ -369,12 +374,175 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
         lds4(ring_s + bslot * R::kPairBytes + h * kRowB + 4 * lane * (uint32_t)sizeof(T), v);
     };
 
+    // Steps whose every updated row is an interior row, in a strip whose lanes all take the
+    // interior stencil along x (and for UP the regular 1/4-3/4 prolongation pattern), run a
+    // step body specialised to the interior stencil; the others the general one.  The choice
+    // is warp-uniform, so each step executes exactly one of the two bodies.
+    const bool x_fast = __all_sync(0xffffffffu, xint && lane_in && (!UP || (std_lane && xlane + 3 < nx)));
+
     int bs = 0, us = 0;  // ring slots of pair T
     uint32_t phase = 0;  // parity of the b-slot barriers in the current lap
+    auto step = [&](auto fast_tag, const int T_) {
+        constexpr bool FAST = decltype(fast_tag)::value;
+        {
+            // shift the window and bring in pair T
+#pragma unroll
+            for (int q = 0; q < NR - 1; ++q)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) w[q][h][i] = w[q + 1][h][i];
+            const uint32_t us_addr = uring_s + us * R::kUSlotBytes;
+            if (ZERO) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) w[NR - 1][h][i] = T(0);
+            } else {
+                lds4(us_addr + 4 * lane * (uint32_t)sizeof(T), w[NR - 1][0]);
+                lds4(us_addr + kRowB + 4 * lane * (uint32_t)sizeof(T), w[NR - 1][1]);
+            }
+            // UP: add the interpolated coarse correction to rows 2T and 2T+1
+            if (has_coarse && 2 * T_ < ny && 2 * T_ + 1 >= 0) {
+                const uint32_t cb = us_addr + (ZERO ? 0 : R::kPairBytes);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = 2 * T_ + h;
+                    if (r < 0 || r >= ny) continue;
+                    int Iy, Jy;
+                    T wy;
+                    interp_axis<T>(r, L.n0y, k, L.ncy, Iy, Jy, wy);
+                    // coarse row q sits at box row q - (T - 1); columns cx0-1 .. cx0+2 at 2l+3 .. 2l+6
+                    const uint32_t c0 = cb + ((Iy - T_ + 1) * kWaveCoarseW + 2 * lane + 2) * (uint32_t)sizeof(T);
+                    const uint32_t c1 = cb + ((Jy - T_ + 1) * kWaveCoarseW + 2 * lane + 2) * (uint32_t)sizeof(T);
+                    T a0[6], a1[6];  // columns 2l+2 .. 2l+7 of the box (8-byte aligned pairs)
+#pragma unroll
+                    for (int m = 0; m < 6; m += 2) {
+                        lds2(c0 + m * sizeof(T), a0[m], a0[m + 1]);
+                        lds2(c1 + m * sizeof(T), a1[m], a1[m + 1]);
+                    }
+                    const T v0[4] = {a0[1], a0[2], a0[3], a0[4]};
+                    const T v1[4] = {a1[1], a1[2], a1[3], a1[4]};
+                    if (!FAST && !lane_in) continue;
+                    T(&row)[4] = w[NR - 1][h];
+                    if (FAST || (std_lane && xlane + 3 < nx)) {
+                        const T q4 = T(0.25);
+                        row[0] = row[0] + bilinear<T>(v0[1], v0[0], v1[1], v1[0], q4, wy);
+                        row[1] = row[1] + bilinear<T>(v0[1], v0[2], v1[1], v1[2], q4, wy);
+                        row[2] = row[2] + bilinear<T>(v0[2], v0[1], v1[2], v1[1], q4, wy);
+                        row[3] = row[3] + bilinear<T>(v0[2], v0[3], v1[2], v1[3], q4, wy);
+                    } else {
+                        prolong_generic<T>(row, v0, v1, oI, oJ, cwx, wy, xlane, nx);
+                    }
+                }
+            }
+            // refill: pair T + AHEAD into the b slot of pair T + AHEAD - NB (no longer needed)
+            // and the u/coarse slot of pair T (just consumed)
+            __syncwarp();
+            {
+                int nbs = bs + AHEAD;
+                if (nbs >= NB) nbs -= NB;
+                if (lane == 0 && T_ + AHEAD <= te) issue(T_ + AHEAD, nbs, us);
+            }
+
+            // half-sweeps: stage s updates pair T - s (window slot NR-1-s) with colour (s - 1) & 1
+#pragma unroll
+            for (int s = 1; s <= S; ++s) {
+                const int m = T_ - s;
+                const int r0 = 2 * m, r1 = 2 * m + 1;
+                if (m < pb || r0 >= ny || r1 < 0) continue;
+                T(&p0)[4] = w[NR - 1 - s][0];
+                T(&p1)[4] = w[NR - 1 - s][1];
+                const T(&north)[4] = w[NR - 2 - s][1];  // row 2m - 1
+                const T(&south)[4] = w[NR - s][0];      // row 2m + 2
+                const int bq = bslot_of(bs, s);
+                T b0[4], b1[4];
+                load_b(bq, 0, b0);
+                load_b(bq, 1, b1);
+                const int f0 = (r0 + ((s - 1) & 1)) & 1;  // first cell of the colour on row r0
+                // Row r0 updates cells {0, 2} (needs cell 3 of lane-1) when f0 == 0, else {1, 3}
+                // (needs cell 0 of lane+1); row r1 the other way round.  One shuffle per row.
+                const int d0 = f0 == 0 ? -1 : 1;
+                const T x0 = __shfl_sync(0xffffffffu, f0 == 0 ? p0[3] : p0[0], lane + d0);
+                const T x1 = __shfl_sync(0xffffffffu, f0 == 0 ? p1[0] : p1[3], lane - d0);
+                const bool ir0 = FAST || interior_row(r0, ny, k), ir1 = FAST || interior_row(r1, ny, k);
+                const bool fast = FAST || (xint && ir0 && ir1);
+                sweep_row<T, FAST>(p0, b0, north, p1, f0, x0, x0, fast, ir0, coef_s, tab, xlane, r0, nx, ny, L.n0x,
+                                   L.n0y, k, alpha, sk);
+                if (FAST || r1 < ny)
+                    sweep_row<T, FAST>(p1, b1, p0, south, f0 ^ 1, x1, x1, fast, ir1, coef_s, tab, xlane, r1, nx, ny,
+                                       L.n0x, L.n0y, k, alpha, sk);
+            }
+            // output of the pair that completed all half-sweeps
+            {
+                const int m = T_ - S;
+                if (m >= P0 && m < P1 && interior_lane && (FAST || lane_in)) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int r = 2 * m + h;
+                        if (r >= Y1) continue;
+                        const T(&orow)[4] = w[NR - 1 - S][h];
+                        T* dst = (UP ? L.uo : L.u) + (int64_t)r * L.pitch + xlane;
+                        if (FAST || xlane + 3 < nx) {
+                            Vec4<T>::store(dst, orow);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                if (xlane + i < nx) dst[i] = orow[i];
+                        }
+                    }
+                }
+            }
+            if (!UP) {
+                // residual of pair m = T - S - 1 (slot 1; neighbours in slots 0 and 2) and its
+                // 2x2 restriction: rows 2m and 2m+1 form coarse row m
+                const int m = T_ - S - 1;
+                const T(&q0)[4] = w[1][0];
+                const T(&q1)[4] = w[1][1];
+                const T w0 = __shfl_up_sync(0xffffffffu, q0[3], 1);
+                const T e0 = __shfl_down_sync(0xffffffffu, q0[0], 1);
+                const T w1 = __shfl_up_sync(0xffffffffu, q1[3], 1);
+                const T e1 = __shfl_down_sync(0xffffffffu, q1[0], 1);
+                if (m >= P0 && m < P1 && L.bc && (FAST || lane_in)) {
+                    const int r0 = 2 * m, r1 = 2 * m + 1;
+                    const int bq = bslot_of(bs, S + 1);
+                    T b0[4], b1[4];
+                    load_b(bq, 0, b0);
+                    load_b(bq, 1, b1);
+                    const bool ir0 = FAST || interior_row(r0, ny, k), ir1 = FAST || interior_row(r1, ny, k);
+                    const bool fast = FAST || (xint && ir0 && ir1);
+                    T res0[4], res1[4] = {T(0), T(0), T(0), T(0)};
+                    residual_row<T, FAST>(res0, q0, b0, w[0][1], q1, w0, e0, fast, ir0, coef_s, tab, xlane, r0, nx,
+                                          ny, L.n0x, L.n0y, k, alpha, sk);
+                    const bool has_r1 = FAST || r1 < ny;
+                    if (has_r1)
+                        residual_row<T, FAST>(res1, q1, b1, q0, w[2][0], w1, e1, fast, ir1, coef_s, tab, xlane, r1,
+                                              nx, ny, L.n0x, L.n0y, k, alpha, sk);
+                    // same summation order as the reference restriction: (((0 + r00) + r01) + r10) + r11
+                    T c0 = T(0), c1 = T(0);
+                    if (FAST || xlane + 0 < nx) c0 = c0 + res0[0];
+                    if (FAST || xlane + 1 < nx) c0 = c0 + res0[1];
+                    if (FAST || xlane + 2 < nx) c1 = c1 + res0[2];
+                    if (FAST || xlane + 3 < nx) c1 = c1 + res0[3];
+                    if (has_r1) {
+                        if (FAST || xlane + 0 < nx) c0 = c0 + res1[0];
+                        if (FAST || xlane + 1 < nx) c0 = c0 + res1[1];
+                        if (FAST || xlane + 2 < nx) c1 = c1 + res1[2];
+                        if (FAST || xlane + 3 < nx) c1 = c1 + res1[3];
+                    }
+                    if (interior_lane && m < L.ncy) {
+                        T* dst = L.bc + (int64_t)m * L.pitchc + cx0;
+                        const T v0 = c0 * T(0.25), v1 = c1 * T(0.25);
+                        if (cx0 + 1 < L.ncx) Vec2<T>::store(dst, v0, v1);
+                        else if (cx0 < L.ncx) dst[0] = v0;
+                    }
+                }
+            }
+        }
+    };
 #pragma unroll 1
     for (int T_ = pb; T_ <= te; ++T_) {
-        const uint32_t bar = bar_s + 8 * bs;
-        if (!mbar_wait_warp(bar, phase)) {
+        if (!mbar_wait_warp(bar_s + 8 * bs, phase)) {
             // give up: flag the host, let the copies already issued land, leave
             if (lane == 0) atomicExch(a.err, 1);
             int b2 = bs, ph2 = phase;
@@ -384,159 +552,13 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
             }
             return;
         }
-        // shift the window and bring in pair T
-#pragma unroll
-        for (int q = 0; q < NR - 1; ++q)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) w[q][h][i] = w[q + 1][h][i];
-        const uint32_t us_addr = uring_s + us * R::kUSlotBytes;
-        if (ZERO) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) w[NR - 1][h][i] = T(0);
-        } else {
-            lds4(us_addr + 4 * lane * (uint32_t)sizeof(T), w[NR - 1][0]);
-            lds4(us_addr + kRowB + 4 * lane * (uint32_t)sizeof(T), w[NR - 1][1]);
-        }
-        // UP: add the interpolated coarse correction to rows 2T and 2T+1
-        if (has_coarse && 2 * T_ < ny && 2 * T_ + 1 >= 0) {
-            const uint32_t cb = us_addr + (ZERO ? 0 : R::kPairBytes);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = 2 * T_ + h;
-                if (r < 0 || r >= ny) continue;
-                int Iy, Jy;
-                T wy;
-                interp_axis<T>(r, L.n0y, k, L.ncy, Iy, Jy, wy);
-                // coarse row q sits at box row q - (T - 1); columns cx0-1 .. cx0+2 at 2l+3 .. 2l+6
-                const uint32_t c0 = cb + ((Iy - T_ + 1) * kWaveCoarseW + 2 * lane + 2) * (uint32_t)sizeof(T);
-                const uint32_t c1 = cb + ((Jy - T_ + 1) * kWaveCoarseW + 2 * lane + 2) * (uint32_t)sizeof(T);
-                T a0[6], a1[6];  // columns 2l+2 .. 2l+7 of the box (8-byte aligned pairs)
-#pragma unroll
-                for (int m = 0; m < 6; m += 2) {
-                    lds2(c0 + m * sizeof(T), a0[m], a0[m + 1]);
-                    lds2(c1 + m * sizeof(T), a1[m], a1[m + 1]);
-                }
-                const T v0[4] = {a0[1], a0[2], a0[3], a0[4]};
-                const T v1[4] = {a1[1], a1[2], a1[3], a1[4]};
-                if (!lane_in) continue;
-                T(&row)[4] = w[NR - 1][h];
-                if (std_lane && xlane + 3 < nx) {
-                    const T q4 = T(0.25);
-                    row[0] = row[0] + bilinear<T>(v0[1], v0[0], v1[1], v1[0], q4, wy);
-                    row[1] = row[1] + bilinear<T>(v0[1], v0[2], v1[1], v1[2], q4, wy);
-                    row[2] = row[2] + bilinear<T>(v0[2], v0[1], v1[2], v1[1], q4, wy);
-                    row[3] = row[3] + bilinear<T>(v0[2], v0[3], v1[2], v1[3], q4, wy);
-                } else {
-                    prolong_generic<T>(row, v0, v1, oI, oJ, cwx, wy, xlane, nx);
-                }
-            }
-        }
-        // refill: pair T + AHEAD into the b slot of pair T + AHEAD - NB (no longer needed) and
-        // the u/coarse slot of pair T (just consumed)
-        __syncwarp();
-        {
-            int nbs = bs + AHEAD;
-            if (nbs >= NB) nbs -= NB;
-            if (lane == 0 && T_ + AHEAD <= te) issue(T_ + AHEAD, nbs, us);
-        }
-
-        // half-sweeps: stage s updates pair T - s (window slot NR-1-s) with colour (s - 1) & 1
-#pragma unroll
-        for (int s = 1; s <= S; ++s) {
-            const int m = T_ - s;
-            const int r0 = 2 * m, r1 = 2 * m + 1;
-            if (m < pb || r0 >= ny || r1 < 0) continue;
-            T(&p0)[4] = w[NR - 1 - s][0];
-            T(&p1)[4] = w[NR - 1 - s][1];
-            const T(&north)[4] = w[NR - 2 - s][1];  // row 2m - 1
-            const T(&south)[4] = w[NR - s][0];      // row 2m + 2
-            const int bq = bslot_of(bs, s);
-            T b0[4], b1[4];
-            load_b(bq, 0, b0);
-            load_b(bq, 1, b1);
-            const int f0 = (r0 + ((s - 1) & 1)) & 1;  // first cell of the colour on row r0
-            // Row r0 updates cells {0, 2} (needs cell 3 of lane-1) when f0 == 0, else {1, 3}
-            // (needs cell 0 of lane+1); row r1 the other way round.  One shuffle per row.
-            const int d0 = f0 == 0 ? -1 : 1;
-            const T x0 = __shfl_sync(0xffffffffu, f0 == 0 ? p0[3] : p0[0], lane + d0);
-            const T x1 = __shfl_sync(0xffffffffu, f0 == 0 ? p1[0] : p1[3], lane - d0);
-            const bool ir0 = interior_row(r0, ny, k), ir1 = interior_row(r1, ny, k);
-            const bool fast = xint && ir0 && ir1;
-            sweep_row<T>(p0, b0, north, p1, f0, x0, x0, fast, ir0, coef_s, tab, xlane, r0, nx, ny, L.n0x, L.n0y, k,
-                         alpha, sk);
-            if (r1 < ny)
-                sweep_row<T>(p1, b1, p0, south, f0 ^ 1, x1, x1, fast, ir1, coef_s, tab, xlane, r1, nx, ny, L.n0x,
-                             L.n0y, k, alpha, sk);
-        }
-        // output of the pair that completed all half-sweeps
-        {
-            const int m = T_ - S;
-            if (m >= P0 && m < P1 && interior_lane && lane_in) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int r = 2 * m + h;
-                    if (r >= Y1) continue;
-                    const T(&orow)[4] = w[NR - 1 - S][h];
-                    T* dst = (UP ? L.uo : L.u) + (int64_t)r * L.pitch + xlane;
-                    if (xlane + 3 < nx) {
-                        Vec4<T>::store(dst, orow);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            if (xlane + i < nx) dst[i] = orow[i];
-                    }
-                }
-            }
-        }
-        if (!UP) {
-            // residual of pair m = T - S - 1 (slot 1; neighbours in slots 0 and 2) and its 2x2
-            // restriction: rows 2m and 2m+1 form coarse row m
-            const int m = T_ - S - 1;
-            const T(&q0)[4] = w[1][0];
-            const T(&q1)[4] = w[1][1];
-            const T w0 = __shfl_up_sync(0xffffffffu, q0[3], 1);
-            const T e0 = __shfl_down_sync(0xffffffffu, q0[0], 1);
-            const T w1 = __shfl_up_sync(0xffffffffu, q1[3], 1);
-            const T e1 = __shfl_down_sync(0xffffffffu, q1[0], 1);
-            if (m >= P0 && m < P1 && L.bc && lane_in) {
-                const int r0 = 2 * m, r1 = 2 * m + 1;
-                const int bq = bslot_of(bs, S + 1);
-                T b0[4], b1[4];
-                load_b(bq, 0, b0);
-                load_b(bq, 1, b1);
-                const bool ir0 = interior_row(r0, ny, k), ir1 = interior_row(r1, ny, k);
-                const bool fast = xint && ir0 && ir1;
-                T res0[4], res1[4] = {T(0), T(0), T(0), T(0)};
-                residual_row<T>(res0, q0, b0, w[0][1], q1, w0, e0, fast, ir0, coef_s, tab, xlane, r0, nx, ny, L.n0x,
-                                L.n0y, k, alpha, sk);
-                const bool has_r1 = r1 < ny;
-                if (has_r1)
-                    residual_row<T>(res1, q1, b1, q0, w[2][0], w1, e1, fast, ir1, coef_s, tab, xlane, r1, nx, ny,
-                                    L.n0x, L.n0y, k, alpha, sk);
-                // same summation order as the reference restriction: (((0 + r00) + r01) + r10) + r11
-                T c0 = T(0), c1 = T(0);
-                if (xlane + 0 < nx) c0 = c0 + res0[0];
-                if (xlane + 1 < nx) c0 = c0 + res0[1];
-                if (xlane + 2 < nx) c1 = c1 + res0[2];
-                if (xlane + 3 < nx) c1 = c1 + res0[3];
-                if (has_r1) {
-                    if (xlane + 0 < nx) c0 = c0 + res1[0];
-                    if (xlane + 1 < nx) c0 = c0 + res1[1];
-                    if (xlane + 2 < nx) c1 = c1 + res1[2];
-                    if (xlane + 3 < nx) c1 = c1 + res1[3];
-                }
-                if (interior_lane && m < L.ncy) {
-                    T* dst = L.bc + (int64_t)m * L.pitchc + cx0;
-                    const T v0 = c0 * T(0.25), v1 = c1 * T(0.25);
-                    if (cx0 + 1 < L.ncx) Vec2<T>::store(dst, v0, v1);
-                    else if (cx0 < L.ncx) dst[0] = v0;
-                }
-            }
-        }
+        // rows updated at this step: pairs T - S .. T - 1 (DOWN also the residual pair T - S - 1);
+        // interior rows form one contiguous range
+        const int rlo = 2 * (T_ - S - (UP ? 0 : 1)), rhi = 2 * T_ - 1;
+        if (x_fast && interior_row(rlo, ny, k) && interior_row(rhi, ny, k))
+            step(std::true_type{}, T_);
+        else
+            step(std::false_type{}, T_);
         if (++bs == NB) { bs = 0; phase ^= 1; }
         if (++us == AHEAD) us = 0;
     }
