@@ -403,12 +403,12 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                 lds4(us_addr + kRowB + 4 * lane * (uint32_t)sizeof(T), w[NR - 1][1]);
             }
             // UP: add the interpolated coarse correction to rows 2T and 2T+1
-            if (has_coarse && 2 * T_ < ny && 2 * T_ + 1 >= 0) {
+            if (has_coarse && (FAST || (2 * T_ < ny && 2 * T_ + 1 >= 0))) {
                 const uint32_t cb = us_addr + (ZERO ? 0 : R::kPairBytes);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int r = 2 * T_ + h;
-                    if (r < 0 || r >= ny) continue;
+                    if (!FAST && (r < 0 || r >= ny)) continue;
                     int Iy, Jy;
                     T wy;
                     interp_axis<T>(r, L.n0y, k, L.ncy, Iy, Jy, wy);
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
             for (int s = 1; s <= S; ++s) {
                 const int m = T_ - s;
                 const int r0 = 2 * m, r1 = 2 * m + 1;
-                if (m < pb || r0 >= ny || r1 < 0) continue;
+                if (!FAST && (m < pb || r0 >= ny || r1 < 0)) continue;
                 T(&p0)[4] = w[NR - 1 - s][0];
                 T(&p1)[4] = w[NR - 1 - s][1];
                 const T(&north)[4] = w[NR - 2 - s][1];  // row 2m - 1
@@ -476,11 +476,11 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
             // output of the pair that completed all half-sweeps
             {
                 const int m = T_ - S;
-                if (m >= P0 && m < P1 && interior_lane && (FAST || lane_in)) {
+                if (interior_lane && (FAST || (m >= P0 && m < P1 && lane_in))) {
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int r = 2 * m + h;
-                        if (r >= Y1) continue;
+                        if (!FAST && r >= Y1) continue;
                         const T(&orow)[4] = w[NR - 1 - S][h];
                         T* dst = (UP ? L.uo : L.u) + (int64_t)r * L.pitch + xlane;
                         if (FAST || xlane + 3 < nx) {
@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                 const T e0 = __shfl_down_sync(0xffffffffu, q0[0], 1);
                 const T w1 = __shfl_up_sync(0xffffffffu, q1[3], 1);
                 const T e1 = __shfl_down_sync(0xffffffffu, q1[0], 1);
-                if (m >= P0 && m < P1 && L.bc && (FAST || lane_in)) {
+                if (L.bc && (FAST || (m >= P0 && m < P1 && lane_in))) {
                     const int r0 = 2 * m, r1 = 2 * m + 1;
                     const int bq = bslot_of(bs, S + 1);
                     T b0[4], b1[4];
@@ -552,10 +552,15 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
             }
             return;
         }
-        // rows updated at this step: pairs T - S .. T - 1 (DOWN also the residual pair T - S - 1);
-        // interior rows form one contiguous range
+        // The interior body also drops the range checks of a march step, so it is taken where
+        // every stage has its pair (T - S >= first pair of the march), the output pair T - S
+        // and the residual pair T - S - 1 (DOWN) lie in this chunk, the prolongation rows 2T,
+        // 2T + 1 (UP) in the level, and every row the step updates is an interior row
+        // (pairs T - S - 1 .. T - 1; interior rows form one contiguous range).
         const int rlo = 2 * (T_ - S - (UP ? 0 : 1)), rhi = 2 * T_ - 1;
-        if (x_fast && interior_row(rlo, ny, k) && interior_row(rhi, ny, k))
+        const bool steady = T_ >= P0 + S + (UP ? 0 : 1) && 2 * (T_ - S) + 1 < Y1 && T_ - S < P1 &&
+                            (!UP || 2 * T_ + 1 < ny);
+        if (x_fast && steady && interior_row(rlo, ny, k) && interior_row(rhi, ny, k))
             step(std::true_type{}, T_);
         else
             step(std::false_type{}, T_);

@@ -138,6 +138,13 @@ struct TopSlice {
     void* b0;      // level-0 right-hand side (the residual r)
 };
 
+// alpha + deg in the iterate type for deg = 0..4 (the diagonal of A), formed once on the host
+// (IEEE addition gives the same values there as on the device)
+template <class TF>
+struct AlphaDeg {
+    TF v[5];
+};
+
 constexpr int kTopTX = 64;
 constexpr int kTopTY = 16;
 
@@ -155,7 +162,7 @@ __global__ void __launch_bounds__(256)
 k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, int nslices,
       const int* __restrict__ active, const float* __restrict__ s, const To* __restrict__ o,
       const float* __restrict__ rhs, const TF* __restrict__ d_old, TF* __restrict__ d_new,
-      float* __restrict__ out, double alpha, double* __restrict__ norms) {
+      float* __restrict__ out, double alpha, AlphaDeg<TF> ad, double* __restrict__ norms) {
     const int64_t t = blockIdx.x;
     const int j = find_item(tile_start, nslices, t);
     if (active && !active[j]) return;
@@ -181,8 +188,6 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
         __syncthreads();
     }
     const float af = float(alpha);
-    // alpha + deg for deg = 1..4, selected without indexing (deg 0 only for 1 x 1 slices)
-    const TF ad1 = TF(alpha) + TF(1), ad2 = TF(alpha) + TF(2), ad3 = TF(alpha) + TF(3), ad4 = TF(alpha) + TF(4);
     // squared norms: FP32 partial sums over a warp's 128 cells, FP64 from there on (per-block
     // sums, per-slice atomics); this keeps the FP64 pipe for the residual itself
     float rrf = 0.f, bbf = 0.f;
@@ -221,7 +226,7 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
             const TF c = dsm[ly + 1][lx + 1];
             const TF nsum = (dsm[ly + 1][lx] + dsm[ly + 1][lx + 2]) + (dsm[ly][lx + 1] + dsm[ly + 2][lx + 1]);
             const int deg = int(hw) + int(he) + int(hn) + int(hs);
-            const TF adeg = deg == 4 ? ad4 : (deg == 3 ? ad3 : (deg == 2 ? ad2 : (deg == 1 ? ad1 : TF(alpha))));
+            const TF adeg = deg == 4 ? ad.v[4] : (deg == 3 ? ad.v[3] : (deg == 2 ? ad.v[2] : (deg == 1 ? ad.v[1] : ad.v[0])));
             // A d in TF (FP64 when mixed): the operator on the high-precision iterate, where
             // the cancellation between alpha d + L d and the right-hand side happens
             const TF Ad = fma_t(adeg, c, -nsum);
@@ -655,14 +660,16 @@ struct Solver {
         const double it_b = MODE == 0 ? 0.0 : sizeof(TV) + sizeof(TF) + 4.0 + (MODE == 2 ? sizeof(TF) : 0.0);
         const double bytes = top_cells * (in_b + it_b + sizeof(TV));
         KernelScope ks(MODE == 0 ? "residual_first" : "residual_update", st, bytes);
+        AlphaDeg<TF> ad;
+        for (int q = 0; q < 5; ++q) ad.v[q] = TF(rq->alpha) + TF(q);
         if (rq->opts.tol < 1e-7)
             k_top<TF, TV, To, MODE, true><<<(unsigned)top_tiles, 256, 0, st>>>(
                 d_top, d_top_ts, (int)rq->nslices, d_active, rq->s, o, rq->rhs, d_old, d_new, rq->out,
-                rq->alpha, d_norms);
+                rq->alpha, ad, d_norms);
         else
             k_top<TF, TV, To, MODE, false><<<(unsigned)top_tiles, 256, 0, st>>>(
                 d_top, d_top_ts, (int)rq->nslices, d_active, rq->s, o, rq->rhs, d_old, d_new, rq->out,
-                rq->alpha, d_norms);
+                rq->alpha, ad, d_norms);
         EMF_CHECK_LAUNCH();
         return EMFUSE_OK;
     }
