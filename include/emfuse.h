@@ -214,8 +214,10 @@ int emfuse_profile_end(emfuse_kernel_profile* out, int max_entries);
 /*
  * Solver plans (descriptor tables, TMA tensor maps, multigrid pyramids and the FP64 iterate)
  * are kept between calls, one per (device, stream, precision), and reused while the slice
- * geometry and schedule options stay the same.  emfuse_release_cache() frees them all (they
- * are rebuilt by the next solve).  It synchronises the device and must not be called while
+ * geometry and schedule options stay the same.  Per-call temporaries come from a memory pool
+ * of the library's own (one per device) that keeps freed pages mapped for the next call.
+ * emfuse_release_cache() frees the plans and returns the pool's unused pages (plans are rebuilt
+ * by the next solve).  It synchronises the device and must not be called while
  * another host thread is inside a solve.
  */
 void emfuse_release_cache(void);

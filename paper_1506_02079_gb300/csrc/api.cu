@@ -78,6 +78,150 @@ static int solve_stack(const float* s, const void* o, int dt, float* out, int64_
     return solve_batch(req, st);
 }
 
+
+// Host-resident stack, streamed through the device in z-chunks of C output slices.  Chunk i
+// needs input planes [a_i, b_i) = [z0 - R, z1 + R) clipped to the stack (R = floor(3 sigma_z)),
+// so that smoothing the slab alone gives exactly the stack's slices.  Three streams overlap:
+//   copy-in  (side stream): the planes chunk i shares with chunk i - 1 device to device from
+//            the previous slab, the new planes from the host, into slab buffer i mod 2;
+//   compute  (the caller's stream): smoothing and the batched solve of chunk i into output
+//            buffer i mod 2 (the solve's host-side convergence checks block this thread, so
+//            the copy of slab i + 1 is queued before it starts);
+//   copy-out (side stream): output buffer i mod 2 to the host.
+// Events order the reuse of the two slab and two output buffers.
+static int correct_stack_host(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                              float sigma_xy, float sigma_z, double alpha, const emfuse_solve_opts& o2,
+                              emfuse_slice_stats* stats, cudaStream_t st) {
+    const int64_t R = support_radius(sigma_z);
+    const int64_t plane = nx * ny;
+    const size_t esz = dtype_size(dt);
+    size_t free_b = 0, total_b = 0;
+    EMF_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    // device bytes per output slice of a chunk: two slabs of input, s, two output buffers, and
+    // the solver's pyramids (about 16 B/px) and FP64 iterates (16 B/px)
+    const double per_slice = (double)plane * (2.0 * esz + 4.0 + 8.0 + 32.0);
+    const double halo = (double)plane * 2.0 * esz * 2.0 * (double)R;
+    int64_t cmax = (int64_t)std::floor((0.7 * (double)free_b - halo) / per_slice);
+    if (cmax < 1) {
+        set_error("emfuse_correct_stack: not enough free device memory for one slice of " +
+                  std::to_string(ny) + " x " + std::to_string(nx) + " plus halo planes");
+        return EMFUSE_ENOMEM;
+    }
+    // at least four chunks when the stack allows it, so that copies overlap compute; equal
+    // chunk sizes (but the last) keep the solver's cached plan valid from chunk to chunk
+    cmax = std::min<int64_t>({cmax, 64, std::max<int64_t>(1, (nz + 3) / 4)});
+    const int64_t nchunks = (nz + cmax - 1) / cmax;
+    const int64_t C = (nz + nchunks - 1) / nchunks;
+    const int64_t slab_cap = std::min<int64_t>(nz, C + 2 * R);
+
+    DeviceBuffer din[2], dout[2], ds;
+    for (int q = 0; q < 2; ++q) {
+        EMF_TRY(din[q].alloc((size_t)(slab_cap * plane) * esz, st));
+        EMF_TRY(dout[q].alloc((size_t)(C * plane) * sizeof(float), st));
+    }
+    EMF_TRY(ds.alloc((size_t)(C * plane) * sizeof(float), st));
+    // the buffers come from the caller's stream's pool: make them valid for the side streams
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_alloc = nullptr, ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
+                ev_out[2] = {nullptr, nullptr};
+    int rc_all = EMFUSE_OK;
+    auto cleanup = [&]() {
+        for (int q = 0; q < 2; ++q) {
+            if (ev_in[q]) cudaEventDestroy(ev_in[q]);
+            if (ev_comp[q]) cudaEventDestroy(ev_comp[q]);
+            if (ev_out[q]) cudaEventDestroy(ev_out[q]);
+        }
+        if (ev_alloc) cudaEventDestroy(ev_alloc);
+        if (s_in) cudaStreamDestroy(s_in);
+        if (s_out) cudaStreamDestroy(s_out);
+    };
+    auto body = [&]() -> int {
+        EMF_CUDA(cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking));
+        EMF_CUDA(cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking));
+        EMF_CUDA(cudaEventCreateWithFlags(&ev_alloc, cudaEventDisableTiming));
+        for (int q = 0; q < 2; ++q) {
+            EMF_CUDA(cudaEventCreateWithFlags(&ev_in[q], cudaEventDisableTiming));
+            EMF_CUDA(cudaEventCreateWithFlags(&ev_comp[q], cudaEventDisableTiming));
+            EMF_CUDA(cudaEventCreateWithFlags(&ev_out[q], cudaEventDisableTiming));
+        }
+        EMF_CUDA(cudaEventRecord(ev_alloc, st));
+        EMF_CUDA(cudaStreamWaitEvent(s_in, ev_alloc, 0));
+        EMF_CUDA(cudaStreamWaitEvent(s_out, ev_alloc, 0));
+        auto slab = [&](int64_t i, int64_t& a, int64_t& b, int64_t& z0, int64_t& z1) {
+            z0 = i * C;
+            z1 = std::min(nz, z0 + C);
+            a = std::max<int64_t>(0, z0 - R);
+            b = std::min<int64_t>(nz, z1 + R);
+        };
+        // queue the copy of slab i into din[i & 1]
+        auto copy_in = [&](int64_t i) -> int {
+            const int q = int(i & 1);
+            int64_t a, b, z0, z1;
+            slab(i, a, b, z0, z1);
+            if (i >= 2) EMF_CUDA(cudaStreamWaitEvent(s_in, ev_comp[q], 0));  // chunk i-2 done with it
+            int64_t have = a;  // planes [a, have) come from the previous slab
+            if (i >= 1) {
+                int64_t pa, pb, pz0, pz1;
+                slab(i - 1, pa, pb, pz0, pz1);
+                if (pb > a) {
+                    EMF_CUDA(cudaMemcpyAsync(din[q].as<char>(), din[q ^ 1].as<char>() + (size_t)((a - pa) * plane) * esz,
+                                             (size_t)((pb - a) * plane) * esz, cudaMemcpyDeviceToDevice, s_in));
+                    have = pb;
+                }
+            }
+            if (b > have)
+                EMF_CUDA(cudaMemcpyAsync(din[q].as<char>() + (size_t)((have - a) * plane) * esz,
+                                         (const char*)in + (size_t)(have * plane) * esz,
+                                         (size_t)((b - have) * plane) * esz, cudaMemcpyHostToDevice, s_in));
+            EMF_CUDA(cudaEventRecord(ev_in[q], s_in));
+            return EMFUSE_OK;
+        };
+        EMF_TRY(copy_in(0));
+        for (int64_t i = 0; i < nchunks; ++i) {
+            const int q = int(i & 1);
+            int64_t a, b, z0, z1;
+            slab(i, a, b, z0, z1);
+            if (i + 1 < nchunks) EMF_TRY(copy_in(i + 1));
+            EMF_CUDA(cudaStreamWaitEvent(st, ev_in[q], 0));
+            if (i >= 2) EMF_CUDA(cudaStreamWaitEvent(st, ev_out[q], 0));  // dout[q] drained
+            EMF_TRY(smooth_stack(din[q].as<char>(), dt, ds.as<float>(), nx, ny, b - a, nx, z0 - a, z1 - a,
+                                 sigma_xy, sigma_z, st, 0));
+            const char* o_chunk = din[q].as<char>() + (size_t)((z0 - a) * plane) * esz;
+            const int rc = solve_stack(ds.as<float>(), o_chunk, dt, dout[q].as<float>(), nx, ny, z1 - z0, alpha,
+                                       o2, stats ? stats + z0 : nullptr, nullptr, st);
+            if (rc != EMFUSE_OK && rc != EMFUSE_ENOCONV) return rc;
+            if (rc == EMFUSE_ENOCONV) rc_all = rc;
+            EMF_CUDA(cudaEventRecord(ev_comp[q], st));
+            EMF_CUDA(cudaStreamWaitEvent(s_out, ev_comp[q], 0));
+            EMF_CUDA(cudaMemcpyAsync(out + z0 * plane, dout[q].as<float>(), (size_t)((z1 - z0) * plane) * sizeof(float),
+                                     cudaMemcpyDeviceToHost, s_out));
+            EMF_CUDA(cudaEventRecord(ev_out[q], s_out));
+        }
+        // the buffers go back to the caller's stream's pool after the side streams are done
+        for (int q = 0; q < 2; ++q) {
+            EMF_CUDA(cudaStreamWaitEvent(st, ev_out[q], 0));
+            EMF_CUDA(cudaStreamWaitEvent(st, ev_in[q], 0));
+        }
+        return EMFUSE_OK;
+    };
+    int rc = body();
+    if (rc != EMFUSE_OK) {
+        // a failure part-way: let queued copies finish before the buffers are released
+        if (s_in) cudaStreamSynchronize(s_in);
+        if (s_out) cudaStreamSynchronize(s_out);
+        cudaStreamSynchronize(st);
+        cleanup();
+        return rc;
+    }
+    const cudaError_t e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) {
+        set_error(std::string("emfuse_correct_stack: ") + cudaGetErrorString(e));
+        return EMFUSE_ECUDA;
+    }
+    return rc_all;
+}
+
 }  // namespace emfuse
 
 using namespace emfuse;
@@ -101,6 +245,7 @@ const char* emfuse_last_error(void) { return last_error(); }
 void emfuse_release_cache(void) {
     cudaDeviceSynchronize();
     release_plans();
+    trim_library_pools();
 }
 
 const char* emfuse_version(void) { return "emfuse 0.1 (sm_103a)"; }
@@ -172,41 +317,7 @@ int emfuse_correct_stack(const void* in, int dt, int in_is_host, float* out, int
         EMF_TRY(smooth_stack(in, dt, sbuf.as<float>(), nx, ny, nz, nx, 0, nz, sigma_xy, sigma_z, st, 0));
         return solve_stack(sbuf.as<float>(), in, dt, out, nx, ny, nz, alpha, o2, stats, nullptr, st);
     }
-    // Host-resident stack: z-chunks of C output slices with R halo planes on each side.
-    const int R = support_radius(sigma_z);
-    size_t free_b = 0, total_b = 0;
-    EMF_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    // per output slice: input (dt) + s (4) + out (4) + solver workspace (~8 + 8 mixed)
-    const double per_slice = (double)plane * (dtype_size(dt) + 4 + 4 + 24);
-    int64_t C = (int64_t)std::max(1.0, std::floor(0.5 * (double)free_b / per_slice) - 2 * R);
-    C = std::min<int64_t>(C, nz);
-    C = std::min<int64_t>(C, 64);
-    const size_t esz = dtype_size(dt);
-    DeviceBuffer din, dout, ds;
-    const int64_t in_cap = std::min<int64_t>(nz, C + 2 * R);
-    EMF_TRY(din.alloc((size_t)(in_cap * plane) * esz, st));
-    EMF_TRY(dout.alloc((size_t)(C * plane) * sizeof(float), st));
-    EMF_TRY(ds.alloc((size_t)(C * plane) * sizeof(float), st));
-    int rc_all = EMFUSE_OK;
-    for (int64_t z0 = 0; z0 < nz; z0 += C) {
-        const int64_t z1 = std::min(nz, z0 + C);
-        const int64_t a = std::max<int64_t>(0, z0 - R), b = std::min<int64_t>(nz, z1 + R);
-        EMF_CUDA(cudaMemcpyAsync(din.as<char>(), (const char*)in + (size_t)(a * plane) * esz,
-                                 (size_t)((b - a) * plane) * esz, cudaMemcpyHostToDevice, st));
-        // Every tap of an output plane in [z0, z1) lies inside the slab [a, b) or outside the
-        // stack, so smoothing the slab on its own gives exactly the stack's slices.
-        EMF_TRY(smooth_stack(din.as<char>(), dt, ds.as<float>(), nx, ny, b - a, nx, z0 - a, z1 - a,
-                             sigma_xy, sigma_z, st, 0));
-        const char* o_chunk = din.as<char>() + (size_t)((z0 - a) * plane) * esz;
-        int rc = solve_stack(ds.as<float>(), o_chunk, dt, dout.as<float>(), nx, ny, z1 - z0, alpha,
-                             o2, stats ? stats + z0 : nullptr, nullptr, st);
-        if (rc != EMFUSE_OK && rc != EMFUSE_ENOCONV) return rc;
-        if (rc == EMFUSE_ENOCONV) rc_all = rc;
-        EMF_CUDA(cudaMemcpyAsync(out + z0 * plane, dout.as<float>(), (size_t)((z1 - z0) * plane) * sizeof(float),
-                                 cudaMemcpyDeviceToHost, st));
-    }
-    EMF_CUDA(cudaStreamSynchronize(st));
-    return rc_all;
+    return correct_stack_host(in, dt, out, nx, ny, nz, sigma_xy, sigma_z, alpha, o2, stats, st);
 }
 
 int emfuse_backward(const float* grad_f, const float* f, const float* s, const void* o, int dt,

@@ -65,8 +65,14 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (grids are sized from the device query)
 
 // ---------------------------------------------------------------- device-memory scratch
-// Stream-ordered allocation from the device's default memory pool; freed stream-ordered
-// at scope exit (the pool keeps the pages for reuse by later calls).
+// The library's memory pool on the current device (runtime.cu): created on first use with no
+// release threshold, so pages freed by one call stay mapped for the next instead of going back
+// to the driver at every synchronisation; trim_library_pools() returns them.  nullptr if the
+// pool cannot be created (the device's default pool is used then).
+cudaMemPool_t library_pool();
+void trim_library_pools();
+
+// Stream-ordered allocation from the library's pool; freed stream-ordered at scope exit.
 class DeviceBuffer {
   public:
     DeviceBuffer() = default;
@@ -77,7 +83,8 @@ class DeviceBuffer {
         release();
         stream_ = s;
         if (bytes == 0) return EMFUSE_OK;
-        cudaError_t e = cudaMallocAsync(&ptr_, bytes, s);
+        cudaMemPool_t pool = library_pool();
+        cudaError_t e = pool ? cudaMallocFromPoolAsync(&ptr_, bytes, pool, s) : cudaMallocAsync(&ptr_, bytes, s);
         if (e != cudaSuccess) {
             ptr_ = nullptr;
             set_error(std::string("cudaMallocAsync(") + std::to_string(bytes) +

@@ -258,11 +258,28 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     extern __shared__ __align__(128) unsigned char wave_smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int64_t item = (int64_t)blockIdx.x * kWaveWarps + warp;
-    if (item >= a.nitems) return;
+    // ---- rings and barriers of this warp, set up once: the warp runs work items back to back
+    // through them, taking the next item from the launch's work counter (items are independent,
+    // so the order does not change any result)
+    unsigned char* ring = wave_smem + (size_t)warp * R::kWarpBytes;
+    const uint32_t ring_s = smem_addr(ring);
+    const uint32_t uring_s = ring_s + R::kBRingBytes;
+    const uint32_t coef_s = uring_s + R::kURingBytes + lane * 20 * (uint32_t)sizeof(T);
+    const uint32_t bar_s = uring_s + R::kURingBytes + R::kCoefBytes;
+    if (lane == 0) {
+        for (int q = 0; q < NB; ++q) mbar_init(bar_s + 8 * q, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    int bs = 0, us = 0;  // ring slots of the next pair
+    uint32_t phase = 0;  // parity of the b-slot barriers in the current lap
+
+    // One work item: a strip of 128 columns and a chunk of rows of one slice.  Returns false
+    // when a bounded wait gave up.
+    auto run_item = [&](const int64_t item) -> bool {
     const int j = find_item(a.item_start, a.nsl, item);
     const LSlice<T> L = a.sl[j];
-    if (a.active && !a.active[L.slice]) return;
+    if (a.active && !a.active[L.slice]) return true;
     const CUtensorMap* map_b = a.maps + 4 * j + 1;
     const CUtensorMap* map_c = a.maps + 4 * j + 2;
     const CUtensorMap* map_u = a.maps + 4 * j + a.u_map;
@@ -322,16 +339,6 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                    cwx[2] == T(0.25) && cwx[3] == T(0.25);
     }
 
-    // ---- rings and barriers
-    unsigned char* ring = wave_smem + (size_t)warp * R::kWarpBytes;
-    const uint32_t ring_s = smem_addr(ring);
-    const uint32_t uring_s = ring_s + R::kBRingBytes;
-    const uint32_t coef_s = uring_s + R::kURingBytes + lane * 20 * (uint32_t)sizeof(T);
-    const uint32_t bar_s = uring_s + R::kURingBytes + R::kCoefBytes;
-    if (lane == 0) {
-        for (int q = 0; q < NB; ++q) mbar_init(bar_s + 8 * q, 1);
-        mbar_init_fence();
-    }
     {  // cache this lane's stencils for interior rows (read when the row pair is not all-interior)
         AxisCoef<T> one;
         one.w = T(1); one.gm = T(1); one.gp = T(1);
@@ -359,8 +366,14 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
         if (!ZERO) tma_load_2d(udst, map_u, X0, 2 * P, bar);
         if (coarse) tma_load_2d(udst + (ZERO ? 0 : R::kPairBytes), map_c, cbox_x, P - 1, bar);
     };
+    // the ring's slots were last read by the previous item: order those reads before the
+    // copies that overwrite them
+    fence_proxy_async();
     if (lane == 0)
-        for (int p = 0; p < AHEAD && pb + p <= te; ++p) issue(pb + p, p, p);
+        for (int p = 0; p < AHEAD && pb + p <= te; ++p) {
+            const int b2 = bs + p, u2 = us + p;
+            issue(pb + p, b2 >= NB ? b2 - NB : b2, u2 >= AHEAD ? u2 - AHEAD : u2);
+        }
 
     T w[NR][2][4];  // window of u pairs in registers
 #pragma unroll
@@ -380,8 +393,6 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     // is warp-uniform, so each step executes exactly one of the two bodies.
     const bool x_fast = __all_sync(0xffffffffu, xint && lane_in && (!UP || (std_lane && xlane + 3 < nx)));
 
-    int bs = 0, us = 0;  // ring slots of pair T
-    uint32_t phase = 0;  // parity of the b-slot barriers in the current lap
     auto step = [&](auto fast_tag, const int T_) {
         constexpr bool FAST = decltype(fast_tag)::value;
         {
@@ -550,7 +561,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                 if (++b2 == NB) { b2 = 0; ph2 ^= 1; }
                 mbar_wait_warp(bar_s + 8 * b2, ph2);
             }
-            return;
+            return false;
         }
         // The interior body also drops the range checks of a march step, so it is taken where
         // every stage has its pair (T - S >= first pair of the march), the output pair T - S
@@ -566,6 +577,24 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
             step(std::false_type{}, T_);
         if (++bs == NB) { bs = 0; phase ^= 1; }
         if (++us == AHEAD) us = 0;
+    }
+    return true;
+    };
+
+    for (;;) {
+        unsigned int item = 0;
+        if (lane == 0) item = atomicAdd(a.work, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if ((int64_t)item >= a.nitems) break;
+        if (!run_item((int64_t)item)) return;  // the host sees the error word and resets the counters
+    }
+    // the last warp of the launch to finish resets the counters for the next launch on this stream
+    if (lane == 0) {
+        const unsigned int total = gridDim.x * (unsigned int)kWaveWarps;
+        if (atomicAdd(a.work + 1, 1u) == total - 1) {
+            atomicExch(a.work, 0u);
+            atomicExch(a.work + 1, 0u);
+        }
     }
 }
 

@@ -237,6 +237,7 @@ struct WaveArgs {
     int u_map;                   // map the initial u is read from: 0 (u) or 3 (uo, to continue
                                  // from the previous V-cycle's result)
     int* err;                    // set to 1 when a bounded wait gives up
+    unsigned int* work;          // [0]: next work item, [1]: warps finished (both 0 at launch)
 };
 
 template <class T>

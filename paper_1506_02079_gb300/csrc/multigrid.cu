@@ -328,6 +328,7 @@ struct Solver {
     double* d_norms = nullptr;
     int* d_active = nullptr;
     int* d_err = nullptr;
+    unsigned int* d_work = nullptr;  // wavefront work counters (reset by each launch's last warp)
     TopSlice* d_top = nullptr;
     int64_t* d_top_ts = nullptr;
     int64_t top_tiles = 0;
@@ -464,8 +465,9 @@ struct Solver {
             }
             // rows per work item: tall chunks amortise the halo rows (about 2 nu + 3 pairs per
             // chunk); shorter ones only while the level would otherwise leave SMs idle
+            // (down to 8 rows on small levels, where a march's latency, not its work, is the cost)
             L.ch = 128;
-            while (L.ch > 32 && want / L.ch < (int64_t)kNumSMs * 16 * 2) L.ch /= 2;
+            while (L.ch > 8 && want / L.ch < (int64_t)kNumSMs * 16 * 2) L.ch /= 2;
             for (const auto& S : L.wsl) {
                 L.item_start.push_back(L.item_start.back() + (int64_t)S.fstrips * ceil_div(S.ny, L.ch));
                 // TMA maps: row pairs of u, b and uo (one 128 x 2 box per strip step) and the
@@ -528,8 +530,11 @@ struct Solver {
         d_top_ts = reinterpret_cast<int64_t*>(dbase + pos_top_ts);
         EMF_TRY(ws_norms.alloc_persistent(2 * n * sizeof(double)));
         d_norms = ws_norms.as<double>();
-        EMF_TRY(ws_active.alloc_persistent(n * sizeof(int)));
+        // active flags of the slices, then the two work counters of the wavefront kernels
+        EMF_TRY(ws_active.alloc_persistent((n + 2) * sizeof(int)));
         d_active = ws_active.as<int>();
+        d_work = reinterpret_cast<unsigned int*>(d_active + n);
+        EMF_CUDA(cudaMemsetAsync(d_work, 0, 2 * sizeof(unsigned int), st));
         d_err = device_error_flag();
         if (!d_err) {
             set_error("could not allocate the device error word");
@@ -576,6 +581,7 @@ struct Solver {
         a.maps = levels[k].d_maps;
         a.u_map = 0;
         a.err = d_err;
+        a.work = d_work;
         return a;
     }
 
@@ -690,6 +696,7 @@ struct Solver {
         std::vector<char> done(n, 0);
         EMF_CUDA(cudaMemcpyAsync(d_active, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
         EMF_CUDA(cudaMemsetAsync(d_norms, 0, 2 * n * sizeof(double), st));
+        EMF_CUDA(cudaMemsetAsync(d_work, 0, 2 * sizeof(unsigned int), st));  // after an aborted launch
         const int maxit = std::max(0, rq->opts.max_vcycles);
         int vdone = 0;
         bool all_done = false;

@@ -121,6 +121,41 @@ KernelScope::~KernelScope() {
     }
 }
 
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {nullptr};
+bool g_pool_failed[64] = {false};
+}  // namespace
+
+cudaMemPool_t library_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev] && !g_pool_failed[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+            cudaGetLastError();
+            g_pool_failed[dev] = true;
+            return nullptr;
+        }
+        uint64_t keep = ~uint64_t(0);
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = p;
+    }
+    return g_pools[dev];
+}
+
+void trim_library_pools() {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (int d = 0; d < 64; ++d)
+        if (g_pools[d]) cudaMemPoolTrimTo(g_pools[d], 0);
+}
+
 // One int per device, allocated on first use and kept for the life of the process: kernels
 // whose bounded waits give up set it; solves read and clear it when they synchronise.
 int* device_error_flag() {

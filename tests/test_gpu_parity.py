@@ -176,3 +176,15 @@ def test_backward_matches_oracle(dev):
     assert gr["alpha"] == pytest.approx(dalpha, rel=2e-3)
     assert gr["sigma_z"] == pytest.approx(dsig, rel=2e-3)
     assert s_np.shape == (nz, ny, nx)
+
+
+@pytest.mark.parametrize("nz,dtype", [(7, torch.uint8), (13, torch.float32), (2, torch.float32), (40, torch.uint8)])
+def test_streamed_host_path_equals_device_path(dev, nz, dtype):
+    """The host-resident path (z-chunks with floor(3 sigma_z) halo planes, copies on side
+    streams) must give exactly the device-resident result: every chunk's slab holds all taps
+    of its output planes, and the batched solve does not depend on how slices are grouped."""
+    I0 = make_stack(nz, 72, 100, seed=17, out_dtype=dtype)
+    ref = api.emfuse_correct_stack(I0.to(dev), 1.0, 3.0, 0.01)
+    got = api.emfuse_correct_stack(I0.pin_memory(), 1.0, 3.0, 0.01)
+    assert got.device.type == "cpu"
+    assert torch.equal(got, ref.cpu())
