@@ -188,3 +188,17 @@ def test_streamed_host_path_equals_device_path(dev, nz, dtype):
     got = api.emfuse_correct_stack(I0.pin_memory(), 1.0, 3.0, 0.01)
     assert got.device.type == "cpu"
     assert torch.equal(got, ref.cpu())
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.uint8])
+def test_sharded_slabs_equal_whole_stack(dev, dtype):
+    """Ranks of a z-sharded run (emulated one after another on one GPU: no rank waits on
+    another) produce exactly the slices of the whole-stack correction."""
+    from paper_1506_02079_gb300 import sharding
+    I0 = make_stack(20, 64, 80, seed=8, out_dtype=dtype).to(dev)
+    full = api.emfuse_correct_stack(I0, 1.0, 3.0, 0.01)
+    parts = []
+    for r in range(3):
+        s = sharding.slab_bounds(20, 3, r, 3.0)
+        parts.append(sharding.correct_slab(I0[s.a:s.b].contiguous(), s, 1.0, 3.0, 0.01))
+    assert torch.equal(torch.cat(parts), full)
