@@ -157,7 +157,7 @@ def run_gpu(args):
     import numpy as np
     import torch
     from paper_1506_02079_gb300 import api
-    from paper_1506_02079_gb300.profiling import profile_steps, kernel_roofline
+    from paper_1506_02079_gb300.profiling import profile_steps, kernel_roofline, relaxation_roofline
 
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
@@ -205,6 +205,7 @@ def run_gpu(args):
         prof = profile_steps(step, args.steps)
         extras["kernels"] = prof
         roof = kernel_roofline(prof)
+        extras["roofline_relaxation"] = relaxation_roofline(prof)
         # end to end through the public API with host buffers
         I0_h = I0.cpu().pin_memory()
         out_h = torch.empty_like(I0_h).pin_memory()

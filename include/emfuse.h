@@ -205,6 +205,7 @@ typedef struct {
     int64_t launches;
     double total_ms;         /* sum of event-measured launch durations */
     double bytes;            /* sum of algorithmic bytes over the launches */
+    double fp64_flops;       /* sum of algorithmic FP64 flops (add = 1, fma = 2), if any */
 } emfuse_kernel_profile;
 
 uint64_t emfuse_kernel_launches(void);

@@ -47,7 +47,7 @@ struct Status {
 // Construct immediately before the launch; the scope's end records the stop event.
 class KernelScope {
   public:
-    KernelScope(const char* name, cudaStream_t s, double bytes);
+    KernelScope(const char* name, cudaStream_t s, double bytes, double fp64_flops = 0.0);
     ~KernelScope();
     KernelScope(const KernelScope&) = delete;
     KernelScope& operator=(const KernelScope&) = delete;
@@ -56,6 +56,7 @@ class KernelScope {
     const char* name_;
     cudaStream_t s_;
     double bytes_;
+    double flops_;
     cudaEvent_t a_ = nullptr, b_ = nullptr;
 };
 

@@ -665,7 +665,10 @@ struct Solver {
         const double in_b = rq->rhs ? 4.0 : 4.0 + sizeof(To);
         const double it_b = MODE == 0 ? 0.0 : sizeof(TV) + sizeof(TF) + 4.0 + (MODE == 2 ? sizeof(TF) : 0.0);
         const double bytes = top_cells * (in_b + it_b + sizeof(TV));
-        KernelScope ks(MODE == 0 ? "residual_first" : "residual_update", st, bytes);
+        // FP64 work of the pass (when the iterate is FP64): the 5-point operator on d, three
+        // adds and one fma per cell, plus the update d_old + e in MODE 2
+        const double flops = sizeof(TF) == 8 && MODE > 0 ? top_cells * (MODE == 2 ? 6.0 : 5.0) : 0.0;
+        KernelScope ks(MODE == 0 ? "residual_first" : "residual_update", st, bytes, flops);
         AlphaDeg<TF> ad;
         for (int q = 0; q < 5; ++q) ad.v[q] = TF(rq->alpha) + TF(q);
         if (rq->opts.tol < 1e-7)

@@ -86,6 +86,7 @@ struct Rec {
     const char* name;
     cudaEvent_t a, b;
     double bytes;
+    double flops;
 };
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
@@ -102,8 +103,8 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
-KernelScope::KernelScope(const char* name, cudaStream_t s, double bytes)
-    : name_(name), s_(s), bytes_(bytes) {
+KernelScope::KernelScope(const char* name, cudaStream_t s, double bytes, double fp64_flops)
+    : name_(name), s_(s), bytes_(bytes), flops_(fp64_flops) {
     if (g_profiling.load(std::memory_order_relaxed)) {
         std::lock_guard<std::mutex> lk(g_mu);
         a_ = take_event();
@@ -117,7 +118,7 @@ KernelScope::~KernelScope() {
     if (a_ && b_) {
         cudaEventRecord(b_, s_);
         std::lock_guard<std::mutex> lk(g_mu);
-        g_recs.push_back(Rec{name_, a_, b_, bytes_});
+        g_recs.push_back(Rec{name_, a_, b_, bytes_, flops_});
     }
 }
 
@@ -240,7 +241,7 @@ void emfuse_profile_begin(void) {
 int emfuse_profile_end(emfuse_kernel_profile* out, int max_entries) {
     g_profiling.store(false);
     std::lock_guard<std::mutex> lk(g_mu);
-    struct Acc { int64_t n = 0; double ms = 0, bytes = 0; };
+    struct Acc { int64_t n = 0; double ms = 0, bytes = 0, flops = 0; };
     std::map<std::string, Acc> acc;
     int rc = 0;
     for (auto& r : g_recs) {
@@ -251,6 +252,7 @@ int emfuse_profile_end(emfuse_kernel_profile* out, int max_entries) {
         x.n += 1;
         x.ms += ms;
         x.bytes += r.bytes;
+        x.flops += r.flops;
         g_pool.push_back(r.a);
         g_pool.push_back(r.b);
     }
@@ -267,6 +269,7 @@ int emfuse_profile_end(emfuse_kernel_profile* out, int max_entries) {
         out[i].launches = v[i].second.n;
         out[i].total_ms = v[i].second.ms;
         out[i].bytes = v[i].second.bytes;
+        out[i].fp64_flops = v[i].second.flops;
     }
     return (int)v.size();
 }

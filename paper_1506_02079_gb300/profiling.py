@@ -21,7 +21,7 @@ FALLBACK_HBM_GBS = 6800.0
 
 class _Prof(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
-                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double), ("fp64_flops", ctypes.c_double)]
 
 
 def profile_steps(step, n: int) -> list[dict]:
@@ -46,7 +46,9 @@ def profile_steps(step, n: int) -> list[dict]:
         out.append({"name": p.name.decode(), "launches": int(p.launches) // max(n, 1),
                     "ms_per_step": p.total_ms / n, "share": p.total_ms / total,
                     "gbs": (p.bytes / (p.total_ms * 1e-3) / 1e9) if p.total_ms > 0 else None,
-                    "bytes_per_launch": p.bytes / max(p.launches, 1)})
+                    "bytes_per_launch": p.bytes / max(p.launches, 1),
+                    "fp64_tflops": (p.fp64_flops / (p.total_ms * 1e-3) / 1e12) if p.total_ms > 0 else None,
+                    "fp64_flops_per_launch": p.fp64_flops / max(p.launches, 1)})
     return out
 
 
@@ -86,10 +88,33 @@ def stored_traffic(name: str):
     return e.get("dram_bytes_per_launch")
 
 
-def kernel_roofline(prof: list[dict]) -> dict:
-    top = max(prof, key=lambda p: p["share"])
+# FP64 peak of GB300 derived from its unit counts and clock: 152 SMs x 2 DFMA per clock per SM
+# x 2 flops x 2.07 GHz (the nominal 1.25 TFLOP/s); no measured FP64 peak is provided.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def _hbm_roofline(p: dict) -> dict:
     peak, kind = measured_hbm_peak()
-    return {"kernel": top["name"], "bound": "hbm", "achieved": top["gbs"], "peak": peak,
-            "unit": "GB/s", "frac": (top["gbs"] / peak) if top["gbs"] else None,
-            "peak_source": f"hbm_gbs of {kind}", "share_of_step": top["share"],
-            "bytes_per_launch": top["bytes_per_launch"], "traffic": stored_traffic(top["name"])}
+    return {"kernel": p["name"], "bound": "hbm", "achieved": p["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": (p["gbs"] / peak) if p["gbs"] else None, "peak_source": f"hbm_gbs of {kind}",
+            "share_of_step": p["share"], "bytes_per_launch": p["bytes_per_launch"],
+            "traffic": stored_traffic(p["name"])}
+
+
+def kernel_roofline(prof: list[dict]) -> dict:
+    """Roofline of the dominant kernel (largest share of the step): FP64-pipe bound ("alu")
+    when it does FP64 work, else HBM bound."""
+    top = max(prof, key=lambda p: p["share"])
+    if top.get("fp64_flops_per_launch"):
+        return {"kernel": top["name"], "bound": "alu", "achieved": top["fp64_tflops"],
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": top["fp64_tflops"] / FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 derived from unit counts and clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "share_of_step": top["share"], "flops_per_launch": top["fp64_flops_per_launch"],
+                "bytes_per_launch": top["bytes_per_launch"], "traffic": stored_traffic(top["name"])}
+    return _hbm_roofline(top)
+
+
+def relaxation_roofline(prof: list[dict]) -> dict | None:
+    """HBM roofline of the relaxation (wavefront V-cycle) kernel with the largest share."""
+    waves = [p for p in prof if p["name"].startswith("wave_")]
+    return _hbm_roofline(max(waves, key=lambda p: p["share"])) if waves else None
