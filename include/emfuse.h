@@ -70,7 +70,17 @@ typedef struct {
     int first_vcycles;   /* V-cycles in the first outer iteration (the second continues from
                             the first's correction in FP32 before the first FP64 residual).
                             0 = default (2).                                               */
-    int reserved[5];     /* must be zero                                                   */
+    int tile_rows;       /* rows of one work item (a 128-column strip) of the fused kernels
+                            on the finest level: 0 = chosen from the batch size, else a
+                            power of two in [8, 256].                                      */
+    int autotune;        /* 1: before solving, time complete solves of this batch for
+                            tile_rows in {32, 64, 128, 256} and (nu_pre, nu_post) in
+                            {1, 2}^2 (fused schedule), keep the fastest for this batch
+                            geometry, alpha, precision and tol, and solve with it (see
+                            emfuse_autotune_result).  Default 0.                           */
+    int no_graphs;       /* 1: launch every V-cycle kernel directly instead of replaying
+                            the V-cycle as a captured CUDA graph.  Default 0.              */
+    int reserved[2];     /* must be zero                                                   */
 } emfuse_solve_opts;
 
 /* Per-slice result of a solve. */
@@ -147,6 +157,19 @@ int emfuse_screened_poisson(const float* s, const float* o, float* f, int64_t ns
                             const int64_t* nx, const int64_t* ny, const int64_t* offsets,
                             double alpha, const emfuse_solve_opts* opts,
                             emfuse_slice_stats* stats, void* stream);
+
+/*
+ * Table of the last autotuning run on this host thread (opts.autotune = 1): one entry per
+ * candidate schedule, the chosen one first.  Not in the paper: its multigrid has no tunable
+ * schedule.  Writes min(count, max_entries) entries to the HOST array `out` (may be NULL)
+ * and returns count (0 if this thread has not autotuned).
+ */
+typedef struct {
+    int nu_pre, nu_post, tile_rows;
+    int vcycles;          /* V-cycles the batch needed with this schedule (max over slices) */
+    double ms;            /* time of the complete solve (CUDA events); -1 if it missed tol  */
+} emfuse_tune_entry;
+int emfuse_autotune_result(emfuse_tune_entry* out, int max_entries);
 
 /*
  * Both phases on a stack: s = smooth(I0), then f_j = solve(s_j, o_j = I0_j) for every j.

@@ -18,7 +18,8 @@ from . import build as _build
 
 __all__ = [
     "EmfuseError", "EmfuseUnavailable", "SolveOpts", "SliceStats", "lib", "library_path",
-    "default_opts", "emfuse_smooth_z", "emfuse_smooth_z_noalloc", "emfuse_screened_poisson", "emfuse_correct_stack",
+    "default_opts", "emfuse_smooth_z", "emfuse_smooth_z_noalloc", "emfuse_screened_poisson",
+    "emfuse_autotune_result", "TuneEntry", "emfuse_correct_stack",
     "emfuse_backward", "emfuse_version", "emfuse_release_cache", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
     "PREC_FP64", "EXPORTED_SYMBOLS",
 ]
@@ -31,7 +32,7 @@ EXPORTED_SYMBOLS = ["emfuse_default_opts", "emfuse_smooth_z", "emfuse_screened_p
                     "emfuse_correct_stack", "emfuse_backward", "emfuse_last_error",
                     "emfuse_version", "emfuse_kernel_launches", "emfuse_profile_begin",
                     "emfuse_profile_end", "emfuse_release_cache", "emfuse_smooth_z_noalloc",
-                    "emfuse_selftest_fpconv"]
+                    "emfuse_selftest_fpconv", "emfuse_autotune_result"]
 
 
 class EmfuseError(RuntimeError):
@@ -47,7 +48,13 @@ class EmfuseUnavailable(RuntimeError):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_vcycles", ctypes.c_int), ("nu_pre", ctypes.c_int),
                 ("nu_post", ctypes.c_int), ("precision", ctypes.c_int), ("fused", ctypes.c_int),
-                ("first_vcycles", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("first_vcycles", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("no_graphs", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("tile_rows", ctypes.c_int),
+                ("vcycles", ctypes.c_int), ("ms", ctypes.c_double)]
 
 
 class SliceStats(ctypes.Structure):
@@ -79,6 +86,8 @@ def lib() -> ctypes.CDLL:
             L.emfuse_smooth_z.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
             L.emfuse_smooth_z_noalloc.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
             L.emfuse_selftest_fpconv.argtypes = [vp, vp]
+            L.emfuse_autotune_result.argtypes = [vp, ci]
+            L.emfuse_autotune_result.restype = ci
             L.emfuse_selftest_fpconv.restype = ci
             L.emfuse_screened_poisson.argtypes = [vp, vp, vp, i64, vp, vp, vp, db,
                                                   ctypes.POINTER(SolveOpts), vp, vp]
@@ -185,6 +194,15 @@ def emfuse_selftest_fpconv() -> tuple[int, int]:
     a, b = ctypes.c_int64(-1), ctypes.c_int64(-1)
     _check(lib().emfuse_selftest_fpconv(ctypes.byref(a), ctypes.byref(b)))
     return int(a.value), int(b.value)
+
+
+def emfuse_autotune_result() -> list[dict]:
+    """Candidates timed by the last autotuning solve on this thread, the chosen one first."""
+    n = lib().emfuse_autotune_result(None, 0)
+    buf = (TuneEntry * max(n, 1))()
+    n = lib().emfuse_autotune_result(ctypes.addressof(buf), n)
+    return [{"nu_pre": e.nu_pre, "nu_post": e.nu_post, "tile_rows": e.tile_rows, "vcycles": e.vcycles,
+             "ms": e.ms} for e in buf[:n]]
 
 
 def _pack_slices(s, o):

@@ -33,6 +33,11 @@ static int resolve_opts(const emfuse_solve_opts* in, emfuse_solve_opts* out) {
         return einval("opts.precision must be EMFUSE_PREC_FP32, _MIXED or _FP64");
     if (out->first_vcycles == 0) out->first_vcycles = 2;
     if (out->first_vcycles < 1 || out->first_vcycles > 8) return einval("opts.first_vcycles must be in [1, 8]");
+    const int tr = out->tile_rows;
+    if (tr != 0 && (tr < 8 || tr > 256 || (tr & (tr - 1)) != 0))
+        return einval("opts.tile_rows must be 0 or a power of two in [8, 256]");
+    if (out->autotune != 0 && out->autotune != 1) return einval("opts.autotune must be 0 or 1");
+    if (out->no_graphs != 0 && out->no_graphs != 1) return einval("opts.no_graphs must be 0 or 1");
     return EMFUSE_OK;
 }
 
@@ -241,6 +246,12 @@ void emfuse_default_opts(emfuse_solve_opts* o) {
 }
 
 const char* emfuse_last_error(void) { return last_error(); }
+
+int emfuse_autotune_result(emfuse_tune_entry* out, int max_entries) {
+    const auto& v = last_autotune();
+    for (int i = 0; out && i < max_entries && i < (int)v.size(); ++i) out[i] = v[i];
+    return (int)v.size();
+}
 
 void emfuse_release_cache(void) {
     cudaDeviceSynchronize();

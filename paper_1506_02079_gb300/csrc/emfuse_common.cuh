@@ -65,6 +65,12 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (grids are sized from the device query)
 
+// Instrumentation state (runtime.cu): whether per-launch event timing is on, and the count
+// of kernel launches (a replayed CUDA graph adds the kernels it holds).
+bool profiling_active();
+uint64_t launch_count();
+void add_launches(int64_t n);
+
 // ---------------------------------------------------------------- device-memory scratch
 // The library's memory pool on the current device (runtime.cu): created on first use with no
 // release threshold, so pages freed by one call stay mapped for the next instead of going back

@@ -42,6 +42,8 @@ struct SolveRequest {
     emfuse_slice_stats* stats = nullptr;  // host, may be null
 };
 int solve_batch(const SolveRequest& req, cudaStream_t st);
+// candidates timed by the last autotuning solve on this host thread, the chosen one first
+const std::vector<emfuse_tune_entry>& last_autotune();
 void release_plans();
 
 // elementwise helpers used by the adjoint (multigrid.cu)

@@ -233,7 +233,7 @@ __device__ __forceinline__ void prolong_generic(T (&uu)[4], const T (&v0)[4], co
 // flight; u and the coarse rows (UP) are consumed when their pair arrives, so kAhead slots.
 template <class T, int S, bool ZERO, bool UP>
 struct WaveRing {
-    static constexpr int kAhead = 3;                                         // pairs in flight
+    static constexpr int kAhead = 2;                                         // pairs in flight
     static constexpr int kNB = kAhead + S + (UP ? 1 : 2);                    // b slots = barriers
     static constexpr int kPairBytes = 2 * kWaveWidth * (int)sizeof(T);
     static constexpr int kCoarseBytes = UP ? (kWaveCoarseW * 3 * (int)sizeof(T) + 127) / 128 * 128 : 0;
@@ -284,11 +284,12 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     const CUtensorMap* map_c = a.maps + 4 * j + 2;
     const CUtensorMap* map_u = a.maps + 4 * j + a.u_map;
     const int li = int(item - a.item_start[j]);
-    // consecutive items walk down one strip, so the warps of a CTA share a strip (edge strips,
-    // which take the general step body, then share CTAs with each other)
+    // consecutive items walk down one strip; the two edge strips (slower: per-cell stencils on
+    // all their lanes) are handed out first, so that they do not finish last
     const int nchunks = (L.ny + a.ch - 1) / a.ch;
-    const int strip = li / nchunks;
-    const int chunk = li - strip * nchunks;
+    const int sidx = li / nchunks;
+    const int strip = L.fstrips < 2 || sidx == 0 ? sidx : (sidx == 1 ? L.fstrips - 1 : sidx - 1);
+    const int chunk = li - sidx * nchunks;
     const int X0 = strip * kWaveIW - kWaveHalo;
     const int Y0 = chunk * a.ch;                  // even
     const int Y1 = min(Y0 + a.ch, L.ny);
@@ -477,7 +478,9 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                 const T x0 = __shfl_sync(0xffffffffu, f0 == 0 ? p0[3] : p0[0], lane + d0);
                 const T x1 = __shfl_sync(0xffffffffu, f0 == 0 ? p1[0] : p1[3], lane - d0);
                 const bool ir0 = FAST || interior_row(r0, ny, k), ir1 = FAST || interior_row(r1, ny, k);
-                const bool fast = FAST || (xint && ir0 && ir1);
+                // warp-uniform: in a strip with edge lanes every lane reads its cached stencil
+                // (an interior lane's cached stencil is the interior one), so no lane diverges
+                const bool fast = FAST || (x_fast && ir0 && ir1);
                 sweep_row<T, FAST>(p0, b0, north, p1, f0, x0, x0, fast, ir0, coef_s, tab, xlane, r0, nx, ny, L.n0x,
                                    L.n0y, k, alpha, sk);
                 if (FAST || r1 < ny)
@@ -521,7 +524,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                     load_b(bq, 0, b0);
                     load_b(bq, 1, b1);
                     const bool ir0 = FAST || interior_row(r0, ny, k), ir1 = FAST || interior_row(r1, ny, k);
-                    const bool fast = FAST || (xint && ir0 && ir1);
+                    const bool fast = FAST || (x_fast && ir0 && ir1);
                     T res0[4], res1[4] = {T(0), T(0), T(0), T(0)};
                     residual_row<T, FAST>(res0, q0, b0, w[0][1], q1, w0, e0, fast, ir0, coef_s, tab, xlane, r0, nx,
                                           ny, L.n0x, L.n0y, k, alpha, sk);

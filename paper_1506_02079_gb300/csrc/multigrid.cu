@@ -26,7 +26,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <tuple>
 #include <mutex>
 #include <vector>
 
@@ -337,13 +339,30 @@ struct Solver {
     double tail_cells = 0;
     bool fused = true;
 
+    // V-cycles replayed as CUDA graphs, one per starting mode (from zero / continuing),
+    // captured on a private stream for the alpha they were captured with
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int64_t gnodes[2] = {0, 0};
+    double galpha[2] = {0.0, 0.0};
+    cudaStream_t cap_st = nullptr;
+
     explicit Solver(cudaStream_t s) : st(s) {}
+    ~Solver() {
+        drop_graphs();
+        if (cap_st) cudaStreamDestroy(cap_st);
+    }
+    void drop_graphs() {
+        for (int q = 0; q < 2; ++q) {
+            if (gexec[q]) cudaGraphExecDestroy(gexec[q]);
+            gexec[q] = nullptr;
+        }
+    }
 
     // What the plan depends on: the slice geometry and the schedule options.
     std::vector<int64_t> sig;
     bool built = false;
     static std::vector<int64_t> signature(const SolveRequest& r) {
-        std::vector<int64_t> v = {r.nslices, r.opts.fused, r.opts.nu_pre, r.opts.nu_post};
+        std::vector<int64_t> v = {r.nslices, r.opts.fused, r.opts.nu_pre, r.opts.nu_post, r.opts.tile_rows};
         for (int64_t j = 0; j < r.nslices; ++j) {
             v.push_back(r.nx[j]);
             v.push_back(r.ny[j]);
@@ -354,11 +373,12 @@ struct Solver {
 
     static bool wave_ok(int nu) { return nu == 1 || nu == 2; }
 
+    // Drops the plan but keeps the two large buffers (pyramids, FP64 iterates): their layout
+    // is recomputed by build() and they are only reallocated when a batch needs more.
     void reset() {
+        drop_graphs();
         levels.clear();
-        ws_levels.release();
         ws_desc.release();
-        ws_f.release();
         ws_norms.release();
         ws_active.release();
         nlev.clear();
@@ -405,7 +425,8 @@ struct Solver {
                 total += (wave(j, k) ? 3 : 2) * round_up(lx, align) * ly;
             }
         }
-        EMF_TRY(ws_levels.alloc_persistent((size_t)total * sizeof(TV)));
+        if (ws_levels.bytes() < (size_t)total * sizeof(TV))
+            EMF_TRY(ws_levels.alloc_persistent((size_t)total * sizeof(TV)));
         TV* base = ws_levels.as<TV>();
         auto make = [&](int64_t j, int k) {
             LSlice<TV> S{};
@@ -468,6 +489,7 @@ struct Solver {
             // (down to 8 rows on small levels, where a march's latency, not its work, is the cost)
             L.ch = 128;
             while (L.ch > 8 && want / L.ch < (int64_t)kNumSMs * 16 * 2) L.ch /= 2;
+            if (k == 0 && rq->opts.tile_rows > 0) L.ch = rq->opts.tile_rows;
             for (const auto& S : L.wsl) {
                 L.item_start.push_back(L.item_start.back() + (int64_t)S.fstrips * ceil_div(S.ny, L.ch));
                 // TMA maps: row pairs of u, b and uo (one 128 x 2 box per strip step) and the
@@ -654,6 +676,52 @@ struct Solver {
         return EMFUSE_OK;
     }
 
+    // One V-cycle.  The fused schedule is captured once per (plan, starting mode, alpha) as a
+    // CUDA graph and replayed; instrumented runs (per-launch events) and opts.no_graphs launch
+    // directly.
+    int vcycle(bool cont) {
+        if (!fused) return vcycle_reference(cont);
+        if (rq->opts.no_graphs || profiling_active()) return vcycle_fused(cont);
+        const int q = cont ? 1 : 0;
+        if (gexec[q] && galpha[q] != rq->alpha) {
+            cudaGraphExecDestroy(gexec[q]);
+            gexec[q] = nullptr;
+        }
+        if (!gexec[q]) {
+            if (!cap_st) EMF_CUDA(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
+            const uint64_t n0 = launch_count();
+            EMF_CUDA(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
+            cudaStream_t user = st;
+            st = cap_st;
+            const int rc = vcycle_fused(cont);
+            st = user;
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(cap_st, &g);
+            const int64_t nodes = (int64_t)(launch_count() - n0);
+            add_launches(-nodes);  // captured, not run
+            if (rc != EMFUSE_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) {
+                set_error(std::string("V-cycle graph capture: ") + cudaGetErrorString(e));
+                return EMFUSE_ECUDA;
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&gexec[q], g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                gexec[q] = nullptr;
+                set_error(std::string("V-cycle graph instantiation: ") + cudaGetErrorString(ei));
+                return EMFUSE_ECUDA;
+            }
+            gnodes[q] = nodes;
+            galpha[q] = rq->alpha;
+        }
+        EMF_CUDA(cudaGraphLaunch(gexec[q], st));
+        add_launches(gnodes[q]);
+        return EMFUSE_OK;
+    }
+
     // Pass `it` of the outer loop: MODE 0 at it == 0, MODE 1 at it == 1, MODE 2 after that.
     // The FP64 iterates alternate between the two halves of ws_f (written: it & 1).
     template <class To, int MODE>
@@ -739,7 +807,7 @@ struct Solver {
             // from the previous one's correction, before the first FP64 residual
             const int nv = it == 0 ? std::min(rq->opts.first_vcycles, maxit - vdone) : 1;
             for (int v = 0; v < nv; ++v) {
-                EMF_TRY(fused ? vcycle_fused(v > 0) : vcycle_reference(v > 0));
+                EMF_TRY(vcycle(v > 0));
                 for (int64_t j = 0; j < n; ++j)
                     if (active[j]) ++vcycles[j];
             }
@@ -863,7 +931,7 @@ __global__ void k_axpy(const float* __restrict__ x, float* __restrict__ y, int64
 
 }  // namespace
 
-int solve_batch(const SolveRequest& req, cudaStream_t st) {
+static int solve_batch_once(const SolveRequest& req, cudaStream_t st) {
     switch (req.opts.precision) {
         case EMFUSE_PREC_FP32: return run_precision<float, float>(req, st);
         case EMFUSE_PREC_MIXED: return run_precision<double, float>(req, st);
@@ -871,6 +939,125 @@ int solve_batch(const SolveRequest& req, cudaStream_t st) {
         default: set_error("unknown precision mode"); return EMFUSE_EINVAL;
     }
 }
+
+// ---------------------------------------------------------------- autotuner
+// Schedules are compared by the time of a complete solve to the requested tolerance (a
+// schedule with fewer sweeps is cheaper per V-cycle but may need more V-cycles).  The search
+// is staged: rows per work item on the finest level in {32, 64, 128, 256} with nu = (2, 2),
+// then nu in {(1, 1), (1, 2), (2, 1)} with the best rows.  Each candidate runs twice (the
+// first run builds its plan and captures its graphs) and the second run is timed.  The winner
+// is cached per batch geometry, alpha, precision and tol.
+namespace {
+struct TuneKey {
+    std::vector<int64_t> geom;
+    int precision;
+    double tol, alpha;
+    int first_vcycles, max_vcycles;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(geom, precision, tol, alpha, first_vcycles, max_vcycles) <
+               std::tie(o.geom, o.precision, o.tol, o.alpha, o.first_vcycles, o.max_vcycles);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, emfuse_tune_entry>& g_tune_cache = *new std::map<TuneKey, emfuse_tune_entry>();
+thread_local std::vector<emfuse_tune_entry> t_last_tune;
+
+int time_solve(const SolveRequest& req, cudaStream_t st, emfuse_tune_entry& e) {
+    std::vector<emfuse_slice_stats> stats((size_t)req.nslices);
+    SolveRequest r = req;
+    r.stats = stats.data();
+    cudaEvent_t a = nullptr, b = nullptr;
+    EMF_CUDA(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        set_error("autotune: cudaEventCreate failed");
+        return EMFUSE_ECUDA;
+    }
+    cudaEventRecord(a, st);
+    const int rc = solve_batch_once(r, st);
+    cudaEventRecord(b, st);
+    float ms = 0.f;
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) ms = -1.f;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    e.ms = ms;
+    e.vcycles = 0;
+    for (const auto& s : stats) e.vcycles = std::max(e.vcycles, s.vcycles);
+    return rc;
+}
+}  // namespace
+
+int solve_batch(const SolveRequest& req, cudaStream_t st) {
+    if (!req.opts.autotune || !req.opts.fused) return solve_batch_once(req, st);
+    TuneKey key;
+    key.geom.reserve(3 * (size_t)req.nslices);
+    for (int64_t j = 0; j < req.nslices; ++j) {
+        key.geom.push_back(req.nx[j]);
+        key.geom.push_back(req.ny[j]);
+        key.geom.push_back(req.offsets[j]);
+    }
+    key.precision = req.opts.precision;
+    key.tol = req.opts.tol;
+    key.alpha = req.alpha;
+    key.first_vcycles = req.opts.first_vcycles;
+    key.max_vcycles = req.opts.max_vcycles;
+    SolveRequest r = req;
+    r.opts.autotune = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            r.opts.nu_pre = it->second.nu_pre;
+            r.opts.nu_post = it->second.nu_post;
+            r.opts.tile_rows = it->second.tile_rows;
+            return solve_batch_once(r, st);
+        }
+    }
+    std::vector<emfuse_tune_entry> table;
+    auto trial = [&](int np, int nq, int rows) -> int {
+        SolveRequest c = r;
+        c.stats = nullptr;
+        c.opts.nu_pre = np;
+        c.opts.nu_post = nq;
+        c.opts.tile_rows = rows;
+        emfuse_tune_entry e{np, nq, rows, 0, 0.0};
+        int rc = solve_batch_once(c, st);  // builds the plan and its graphs
+        if (rc != EMFUSE_OK && rc != EMFUSE_ENOCONV) return rc;
+        rc = time_solve(c, st, e);
+        if (rc != EMFUSE_OK && rc != EMFUSE_ENOCONV) return rc;
+        if (rc == EMFUSE_ENOCONV) e.ms = -1.0;  // did not reach tol: never chosen
+        table.push_back(e);
+        return EMFUSE_OK;
+    };
+    auto best_of = [&]() {
+        int b = -1;
+        for (int i = 0; i < (int)table.size(); ++i)
+            if (table[i].ms >= 0 && (b < 0 || table[i].ms < table[b].ms)) b = i;
+        return b;
+    };
+    for (int rows : {32, 64, 128, 256}) EMF_TRY(trial(2, 2, rows));
+    int b = best_of();
+    const int rows = b >= 0 ? table[b].tile_rows : 128;
+    for (auto nu : {std::pair<int, int>{1, 1}, {1, 2}, {2, 1}}) EMF_TRY(trial(nu.first, nu.second, rows));
+    b = best_of();
+    if (b < 0) {
+        t_last_tune = table;
+        set_error("autotune: no candidate schedule reached the tolerance");
+        return EMFUSE_ENOCONV;
+    }
+    std::swap(table[0], table[b]);
+    t_last_tune = table;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = table[0];
+    }
+    r.opts.nu_pre = table[0].nu_pre;
+    r.opts.nu_post = table[0].nu_post;
+    r.opts.tile_rows = table[0].tile_rows;
+    return solve_batch_once(r, st);
+}
+
+const std::vector<emfuse_tune_entry>& last_autotune() { return t_last_tune; }
 
 void release_plans() {
     std::lock_guard<std::mutex> lk(g_plans_mu);

@@ -103,6 +103,10 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+bool profiling_active() { return g_profiling.load(std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(int64_t n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
 KernelScope::KernelScope(const char* name, cudaStream_t s, double bytes, double fp64_flops)
     : name_(name), s_(s), bytes_(bytes), flops_(fp64_flops) {
     if (g_profiling.load(std::memory_order_relaxed)) {

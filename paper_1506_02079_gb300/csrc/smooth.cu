@@ -150,6 +150,9 @@ struct SmTile {
     static constexpr int BY = kTY + 2 * R;
     static constexpr int kPlaneBytes = BX * BY * (int)sizeof(Tin);
     static constexpr int kPlaneStride = (kPlaneBytes + 127) / 128 * 128;  // TMA destinations 128-B aligned
+    // plane buffers: NBUF - 1 copies in flight while one plane is blurred (enough bytes in
+    // flight per SM to cover the HBM latency with two CTAs per SM)
+    static constexpr int NBUF = sizeof(Tin) == 1 ? 8 : 5;
 };
 
 template <class Tin>
@@ -172,28 +175,31 @@ smooth_tma_kernel(const __grid_constant__ CUtensorMap map, float* __restrict__ o
                   const float* __restrict__ inv_ny, const float* __restrict__ inv_nz, SmoothParams prm,
                   int* __restrict__ err) {
     using G = SmTile<Tin, R>;
-    constexpr int P = 19;  // z ring: supports floor(3 sigma_z) <= 9
-    __shared__ __align__(128) unsigned char s_raw[2 * G::kPlaneStride];
+    constexpr int P = 19;  // z taps: supports floor(3 sigma_z) <= 9
+    constexpr int NB = G::NBUF;
+    constexpr int AHEAD = NB - 1;
+    __shared__ __align__(128) unsigned char s_raw[NB * G::kPlaneStride];
     __shared__ __align__(16) float s_x[G::BY][kTX];
-    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ __align__(8) uint64_t s_bar[NB];
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int Rz = prm.Rz;
     const int zin_lo = max(0, z0 - Rz), zin_hi = min(nz, z1 + Rz), zi_end = z1 + Rz;
-    const uint32_t bar[2] = {smem_addr(&s_bar[0]), smem_addr(&s_bar[1])};
+    const uint32_t bar0 = smem_addr(&s_bar[0]);
     if (tid == 0) {
-        mbar_init(bar[0], 1);
-        mbar_init(bar[1], 1);
+        for (int q = 0; q < NB; ++q) mbar_init(bar0 + 8 * q, 1);
         mbar_init_fence();
     }
     __syncthreads();
-    auto issue = [&](int zi) {  // thread 0: plane zi into buffer (zi - zin_lo) & 1
-        const int bf = (zi - zin_lo) & 1;
+    // thread 0: plane zi into buffer slot (slots advance with zi; a slot is refilled only after
+    // the __syncthreads that ended the iteration which last read it)
+    auto issue = [&](int zi, int slot) {
         fence_proxy_async();
-        mbar_expect_tx(bar[bf], G::kPlaneBytes);
-        tma_load_3d(smem_addr(s_raw + bf * G::kPlaneStride), &map, x0 - G::HX, y0 - R, zi, bar[bf]);
+        mbar_expect_tx(bar0 + 8 * slot, G::kPlaneBytes);
+        tma_load_3d(smem_addr(s_raw + slot * G::kPlaneStride), &map, x0 - G::HX, y0 - R, zi, bar0 + 8 * slot);
     };
-    if (tid == 0 && zin_lo < zin_hi) issue(zin_lo);
+    if (tid == 0)
+        for (int q = 0; q < AHEAD && zin_lo + q < zin_hi; ++q) issue(zin_lo + q, q);
 
     float w[2 * R + 1];
 #pragma unroll
@@ -201,93 +207,111 @@ smooth_tma_kernel(const __grid_constant__ CUtensorMap map, float* __restrict__ o
     const int tx = tid % 16, ty = tid / 16;
     const int gy = y0 + ty;
     const float iny = inv_ny[min(gy, ny - 1)];
-    float ring[P][4];
+    // x-blur items of this thread all have the same column group (kThreads is a multiple of 16)
+    float inx[4];
 #pragma unroll
-    for (int q = 0; q < P; ++q)
+    for (int i = 0; i < 4; ++i) inx[i] = inv_nx[min(x0 + 4 * (tid & 15) + i, nx - 1)];
+    // z ring: slots 0 .. P-2 hold the P-1 planes before the current block of U planes, slots
+    // P-1 .. P-2+U the block; the ring moves by U slots once per block (the loop over a block is
+    // unrolled, so every slot index is a constant)
+    constexpr int U = 4;
+    float ring[P - 1 + U][4];
+#pragma unroll
+    for (int q = 0; q < P - 1 + U; ++q)
 #pragma unroll
         for (int i = 0; i < 4; ++i) ring[q][i] = 0.f;
     const int64_t plane = pitch * (int64_t)ny;
 
+    int slot = 0;        // buffer slot of plane zi
+    uint32_t phase = 0;  // barrier parity of the current lap over the slots
 #pragma unroll 1
-    for (int zi = zin_lo; zi < zi_end; ++zi) {
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        if (zi < zin_hi) {
-            const int bf = (zi - zin_lo) & 1;
-            if (tid == 0 && zi + 1 < zin_hi) issue(zi + 1);
-            bool ok = false;
-            for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(bar[bf], ((zi - zin_lo) >> 1) & 1);
-            if (!__syncthreads_and(ok)) {
-                // give up: flag the host, let the copy in flight land, leave
-                if (tid == 0) {
-                    atomicExch(err, 1);
-                    if (zi + 1 < zin_hi)
-                        for (int it = 0; it < kWaitLimit; ++it)
-                            if (mbar_try_wait(bar[bf ^ 1], ((zi + 1 - zin_lo) >> 1) & 1)) break;
+    for (int zb = zin_lo; zb < zi_end; zb += U) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int zi = zb + u;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            if (zi < zin_hi) {
+                if (tid == 0 && zi + AHEAD < zin_hi) issue(zi + AHEAD, slot == 0 ? NB - 1 : slot - 1);
+                bool ok = false;
+                for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(bar0 + 8 * slot, phase);
+                if (!__syncthreads_and(ok)) {
+                    // give up: flag the host, let the copies in flight land, leave
+                    if (tid == 0) {
+                        atomicExch(err, 1);
+                        int s2 = slot;
+                        uint32_t ph2 = phase;
+                        for (int zz = zi + 1; zz < zin_hi && zz <= zi + AHEAD; ++zz) {
+                            if (++s2 == NB) { s2 = 0; ph2 ^= 1u; }
+                            for (int it = 0; it < kWaitLimit; ++it)
+                                if (mbar_try_wait(bar0 + 8 * s2, ph2)) break;
+                        }
+                    }
+                    __syncthreads();
+                    return;
+                }
+                // x blur: (row, group of 4 columns) items; the span of a group is 3 aligned words
+                const Tin(*s_in)[G::BX] = reinterpret_cast<const Tin(*)[G::BX]>(s_raw + slot * G::kPlaneStride);
+                for (int item = tid; item < G::BY * 16; item += kThreads) {
+                    const int r = item >> 4, g = item & 15;
+                    float s0[4], s1[4], s2[4];
+                    load_word<Tin>(&s_in[r][4 * g + G::HX - 4], s0);
+                    load_word<Tin>(&s_in[r][4 * g + G::HX], s1);
+                    load_word<Tin>(&s_in[r][4 * g + G::HX + 4], s2);
+                    const float s[12] = {s0[0], s0[1], s0[2], s0[3], s1[0], s1[1], s1[2], s1[3],
+                                         s2[0], s2[1], s2[2], s2[3]};
+                    float o[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int d = -R; d <= R; ++d) acc = fmaf(w[d + R], s[4 + i + d], acc);
+                        o[i] = acc * inx[i];
+                    }
+                    *reinterpret_cast<float4*>(&s_x[r][4 * g]) = make_float4(o[0], o[1], o[2], o[3]);
                 }
                 __syncthreads();
-                return;
-            }
-            // x blur: (row, group of 4 columns) items; the span of a group is 3 aligned words
-            const Tin(*s_in)[G::BX] = reinterpret_cast<const Tin(*)[G::BX]>(s_raw + bf * G::kPlaneStride);
-            for (int item = tid; item < G::BY * 16; item += kThreads) {
-                const int r = item >> 4, g = item & 15;
-                float s0[4], s1[4], s2[4];
-                load_word<Tin>(&s_in[r][4 * g + G::HX - 4], s0);
-                load_word<Tin>(&s_in[r][4 * g + G::HX], s1);
-                load_word<Tin>(&s_in[r][4 * g + G::HX + 4], s2);
-                const float s[12] = {s0[0], s0[1], s0[2], s0[3], s1[0], s1[1], s1[2], s1[3],
-                                     s2[0], s2[1], s2[2], s2[3]};
-                float o[4];
+                // y blur of this thread's 4 columns on row ty
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    float acc = 0.f;
-#pragma unroll
-                    for (int d = -R; d <= R; ++d) acc = fmaf(w[d + R], s[4 + i + d], acc);
-                    o[i] = acc * inv_nx[min(x0 + 4 * g + i, nx - 1)];
+                for (int d = -R; d <= R; ++d) {
+                    const float4 q = *reinterpret_cast<const float4*>(&s_x[ty + R + d][4 * tx]);
+                    v[0] = fmaf(w[d + R], q.x, v[0]);
+                    v[1] = fmaf(w[d + R], q.y, v[1]);
+                    v[2] = fmaf(w[d + R], q.z, v[2]);
+                    v[3] = fmaf(w[d + R], q.w, v[3]);
                 }
-                *reinterpret_cast<float4*>(&s_x[r][4 * g]) = make_float4(o[0], o[1], o[2], o[3]);
-            }
-            __syncthreads();
-            // y blur of this thread's 4 columns on row ty
 #pragma unroll
-            for (int d = -R; d <= R; ++d) {
-                const float4 q = *reinterpret_cast<const float4*>(&s_x[ty + R + d][4 * tx]);
-                v[0] = fmaf(w[d + R], q.x, v[0]);
-                v[1] = fmaf(w[d + R], q.y, v[1]);
-                v[2] = fmaf(w[d + R], q.z, v[2]);
-                v[3] = fmaf(w[d + R], q.w, v[3]);
+                for (int i = 0; i < 4; ++i) v[i] *= iny;
+                if (++slot == NB) { slot = 0; phase ^= 1u; }
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) v[i] *= iny;
+            for (int i = 0; i < 4; ++i) ring[P - 1 + u][i] = v[i];
+            // emit plane zi - Rz from ring slots u .. u + P - 1 (slot u + P - 1 = plane zi)
+            const int zo = zi - Rz;
+            if (zo >= z0 && zo < z1 && gy < ny) {
+                float o4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int jj = 0; jj < P; ++jj) {
+                    const float wz = prm.wz[jj];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) o4[i] = fmaf(wz, ring[u + P - 1 - jj][i], o4[i]);
+                }
+                const float inz = inv_nz[zo];
+                float* dst = out + (int64_t)(zo - z0) * plane + (int64_t)gy * pitch + x0 + 4 * tx;
+                const int gx = x0 + 4 * tx;
+                if (gx + 3 < nx && (pitch & 3) == 0) {
+                    *reinterpret_cast<float4*>(dst) = make_float4(o4[0] * inz, o4[1] * inz, o4[2] * inz, o4[3] * inz);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (gx + i < nx) dst[i] = o4[i] * inz;
+                }
+            }
+            __syncthreads();  // s_x and the input buffer of plane zi are reused
         }
-        // push into the z ring (slot P-1 = plane zi) and emit plane zi - Rz
 #pragma unroll
         for (int q = 0; q < P - 1; ++q)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) ring[q][i] = ring[q + 1][i];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) ring[P - 1][i] = v[i];
-        const int zo = zi - Rz;
-        if (zo >= z0 && zo < z1 && gy < ny) {
-            float o4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int jj = 0; jj < P; ++jj) {
-                const float wz = prm.wz[jj];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) o4[i] = fmaf(wz, ring[P - 1 - jj][i], o4[i]);
-            }
-            const float inz = inv_nz[zo];
-            float* dst = out + (int64_t)(zo - z0) * plane + (int64_t)gy * pitch + x0 + 4 * tx;
-            const int gx = x0 + 4 * tx;
-            if (gx + 3 < nx && (pitch & 3) == 0) {
-                *reinterpret_cast<float4*>(dst) = make_float4(o4[0] * inz, o4[1] * inz, o4[2] * inz, o4[3] * inz);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (gx + i < nx) dst[i] = o4[i] * inz;
-            }
-        }
-        __syncthreads();  // s_x and the input buffer of plane zi are reused
+            for (int i = 0; i < 4; ++i) ring[q][i] = ring[q + U][i];
     }
 }
 

@@ -62,14 +62,30 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# CUDA sources each instrumented kernel is built from (the others: every source)
+_KERNEL_SOURCES = {
+    "residual": ("multigrid.cu", "fpconv.cuh", "mg_fused.cuh", "emfuse_common.cuh"),
+    "wave": ("fused_impl.cuh", "fused_f32.cu", "fused_f64.cu", "mg_fused.cuh", "tma.cuh", "emfuse_common.cuh"),
+    "coarse_tail": ("fused_impl.cuh", "fused_f32.cu", "fused_f64.cu", "mg_fused.cuh", "emfuse_common.cuh"),
+    "smooth": ("smooth.cu", "tma.cuh", "emfuse_common.cuh"),
+}
+
+
 def kernel_source_hash(name: str) -> str:
-    """Hash of the CUDA sources, so stored ncu traffic is dropped once a kernel changes."""
-    h = hashlib.sha256()
+    """Hash of the CUDA sources of kernel `name`, so stored ncu traffic is dropped once that
+    kernel's code changes."""
     csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    files = None
+    for prefix, fs in _KERNEL_SOURCES.items():
+        if name.startswith(prefix):
+            files = fs
+    if files is None:
+        files = tuple(f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh")))
+    h = hashlib.sha256()
+    for f in sorted(files):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

@@ -101,3 +101,40 @@ def test_slices_met_at_initial_iterate_return_o(dev):
         assert torch.equal(f[1], I0[1])
         f0, _ = solve(s, I0, 1e-2, precision=prec, max_vcycles=0)
         assert torch.equal(f0, I0)
+
+
+@pytest.mark.parametrize("precision", [api.PREC_FP32, api.PREC_MIXED])
+def test_graph_replay_and_tile_rows_are_bit_identical(dev, precision):
+    """Replaying the V-cycle as a CUDA graph, and any rows-per-work-item on the finest level,
+    give exactly the directly launched result."""
+    s, o, ny, nx, offs = make_ragged_batch(9, seed=6, side_lo=40, side_hi=700)
+    s, o = s.to(dev), o.to(dev)
+    def run(**kw):
+        return api.emfuse_screened_poisson(s, o, 1e-3, api.default_opts(precision=precision, **kw), nx=nx, ny=ny,
+                                           offsets=offs, return_stats=True)
+    f0, st0 = run(no_graphs=1)
+    for kw in (dict(), dict(tile_rows=8), dict(tile_rows=32), dict(tile_rows=256), dict(no_graphs=1, tile_rows=64)):
+        f1, st1 = run(**kw)
+        assert torch.equal(f1, f0), kw
+        assert [a["vcycles"] for a in st1] == [a["vcycles"] for a in st0]
+    # a graph captured for one alpha is not replayed for another
+    g1 = api.emfuse_screened_poisson(s, o, 0.1, api.default_opts(precision=precision), nx=nx, ny=ny, offsets=offs)
+    g2 = api.emfuse_screened_poisson(s, o, 0.1, api.default_opts(precision=precision, no_graphs=1), nx=nx, ny=ny,
+                                     offsets=offs)
+    assert torch.equal(g1, g2)
+
+
+def test_autotune_picks_the_fastest_candidate(dev):
+    s, o, ny, nx, offs = make_ragged_batch(10, seed=2, side_lo=64, side_hi=900)
+    s, o = s.to(dev), o.to(dev)
+    f, st = api.emfuse_screened_poisson(s, o, 1e-3, api.default_opts(autotune=1), nx=nx, ny=ny, offsets=offs,
+                                        return_stats=True)
+    table = api.emfuse_autotune_result()
+    assert len(table) == 7
+    best = table[0]
+    assert best["ms"] == min(e["ms"] for e in table if e["ms"] >= 0)
+    ref = api.emfuse_screened_poisson(s, o, 1e-3, api.default_opts(nu_pre=best["nu_pre"], nu_post=best["nu_post"],
+                                                                    tile_rows=best["tile_rows"]),
+                                      nx=nx, ny=ny, offsets=offs)
+    assert torch.equal(f, ref)
+    assert all(a["converged"] for a in st)
