@@ -145,6 +145,8 @@ struct TopSlice {
 template <class TF>
 struct AlphaDeg {
     TF v[5];
+    float alpha_f;  // alpha rounded to float once on the host (a conversion per thread would
+                    // take the FP64 pipe)
 };
 
 constexpr int kTopTX = 64;
@@ -189,7 +191,7 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
         }
         __syncthreads();
     }
-    const float af = float(alpha);
+    const float af = ad.alpha_f;
     // squared norms: FP32 partial sums over a warp's 128 cells, FP64 from there on (per-block
     // sums, per-slice atomics); this keeps the FP64 pipe for the residual itself
     float rrf = 0.f, bbf = 0.f;
@@ -739,6 +741,7 @@ struct Solver {
         KernelScope ks(MODE == 0 ? "residual_first" : "residual_update", st, bytes, flops);
         AlphaDeg<TF> ad;
         for (int q = 0; q < 5; ++q) ad.v[q] = TF(rq->alpha) + TF(q);
+        ad.alpha_f = float(rq->alpha);
         if (rq->opts.tol < 1e-7)
             k_top<TF, TV, To, MODE, true><<<(unsigned)top_tiles, 256, 0, st>>>(
                 d_top, d_top_ts, (int)rq->nslices, d_active, rq->s, o, rq->rhs, d_old, d_new, rq->out,
