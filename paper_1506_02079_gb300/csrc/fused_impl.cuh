@@ -101,13 +101,13 @@ struct WaveOcc { static constexpr int value = sizeof(T) == 4 ? 4 : 2; };
 
 // ---------------------------------------------------------------- per-cell stencils
 // Interior cells (full cells with full neighbours) all share one stencil.  Cells on a slice
-// edge, a partial coarse cell or outside the level take per-cell stencils: cheap selects at
-// level 0 (degree 2..4, reciprocals tabulated once per kernel), the general finite-volume
-// formula out of line on coarse levels.
+// edge, a partial coarse cell or outside the level take per-cell stencils: selects at level 0
+// (alpha + degree and its reciprocal formed when needed, so that nothing of these rare paths
+// stays live in registers across the march), the general finite-volume formula out of line on
+// coarse levels.
 template <class T>
 struct StencilTab {
     Coef<T> ci;   // interior stencil
-    T d[5], id[5];  // level 0: alpha + deg and its reciprocal, deg = 0..4
 };
 
 template <class T>
@@ -115,33 +115,19 @@ __device__ __forceinline__ void make_stencil_tab(StencilTab<T>& tab, int k, T al
     AxisCoef<T> one;
     one.w = T(1); one.gm = T(1); one.gp = T(1);
     tab.ci = make_coef<T>(one, one, k, alpha, sk);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        tab.d[q] = alpha + T(q);  // = alpha + (((cw + ce) + cn) + cs) for 0/1 coefficients
-        tab.id[q] = rcp_t(tab.d[q]);
-    }
-}
-
-template <class T>
-__device__ __forceinline__ T pick5(const T (&v)[5], int i) {
-    return i <= 1 ? (i == 0 ? v[0] : v[1]) : (i == 2 ? v[2] : (i == 3 ? v[3] : v[4]));
 }
 
 // Level-0 stencil of cell (x, r) from selects; equal to make_coef at level 0.
 template <class T>
-__device__ __forceinline__ Coef<T> level0_coef(const StencilTab<T>& tab, int x, int r, int nx, int ny) {
+__device__ __forceinline__ Coef<T> level0_coef(int x, int r, int nx, int ny, T alpha) {
     Coef<T> c;
     const bool in = x >= 0 && x < nx && r >= 0 && r < ny;
     const int w = in && x > 0, e = in && x + 1 < nx, n = in && r > 0, s = in && r + 1 < ny;
     c.cw = T(w); c.ce = T(e); c.cn = T(n); c.cs = T(s);
-    const int deg = w + e + n + s;
-    if (in) {
-        c.D = pick5<T>(tab.d, deg);
-        c.iD = pick5<T>(tab.id, deg);
-    } else {  // outside the level: decoupled (the w = 1 cell of axis_coef) -> D = alpha
-        c.D = tab.d[0];
-        c.iD = tab.id[0];
-    }
+    // alpha + (((cw + ce) + cn) + cs) for 0/1 coefficients; outside the level the cell is
+    // decoupled (the w = 1 cell of axis_coef): D = alpha
+    c.D = alpha + T(w + e + n + s);
+    c.iD = rcp_t(c.D);
     return c;
 }
 
@@ -154,7 +140,7 @@ __device__ __noinline__ Coef<T> coarse_cell_coef(int x, int r, int nx, int ny, i
 template <class T>
 __device__ __forceinline__ Coef<T> edge_coef(const StencilTab<T>& tab, int x, int r, int nx, int ny, int n0x,
                                              int n0y, int k, T alpha, T sk) {
-    return k == 0 ? level0_coef<T>(tab, x, r, nx, ny) : coarse_cell_coef<T>(x, r, nx, ny, n0x, n0y, k, alpha, sk);
+    return k == 0 ? level0_coef<T>(x, r, nx, ny, alpha) : coarse_cell_coef<T>(x, r, nx, ny, n0x, n0y, k, alpha, sk);
 }
 
 // Stencil of cell i of the lane on an interior row, from the lane's shared-memory cache
@@ -216,15 +202,20 @@ __device__ __forceinline__ void residual_row(T (&res)[4], const T (&row)[4], con
     }
 }
 
-// Prolongation for lanes whose cells do not follow the interior 1/4-3/4 pattern.
+// Prolongation for lanes whose cells do not follow the interior 1/4-3/4 pattern; v0 / v1 hold
+// coarse columns cx0 - 1 .. cx0 + 2.  The interpolation along x is formed here, when needed,
+// so that nothing of this rare path stays live in registers across the march.
 template <class T>
-__device__ __forceinline__ void prolong_generic(T (&uu)[4], const T (&v0)[4], const T (&v1)[4], const int (&oI)[4],
-                                                const int (&oJ)[4], const T (&cwx)[4], T wy, int xlane, int nx) {
+__device__ __forceinline__ void prolong_generic(T (&uu)[4], const T (&v0)[4], const T (&v1)[4], int cx0, T wy,
+                                                int xlane, int nx, int n0x, int k, int ncx) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         if (xlane + i >= nx) continue;
-        uu[i] = uu[i] + bilinear<T>(pick4<T>(v0, oI[i]), pick4<T>(v0, oJ[i]), pick4<T>(v1, oI[i]),
-                                    pick4<T>(v1, oJ[i]), cwx[i], wy);
+        int I, J;
+        T wx;
+        interp_axis<T>(xlane + i, n0x, k, ncx, I, J, wx);
+        const int oI = I - cx0 + 1, oJ = J - cx0 + 1;
+        uu[i] = uu[i] + bilinear<T>(pick4<T>(v0, oI), pick4<T>(v0, oJ), pick4<T>(v1, oI), pick4<T>(v1, oJ), wx, wy);
     }
 }
 
@@ -321,11 +312,11 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     // prolongation geometry along x (UP): coarse columns cx0-1 .. cx0+2 around the lane
     const int cx0 = X0 / 2 + 2 * lane;
     const int cbox_x = X0 / 2 - 4;  // first staged coarse column (x * size stays 16-B aligned)
-    int oI[4], oJ[4];
-    T cwx[4];
     bool std_lane = true;  // interior pattern: J = I-1, I+1, I-1, I+1 with weight 1/4
     const bool has_coarse = UP && L.uco != nullptr;
     if (UP) {
+        int oI[4], oJ[4];
+        T cwx[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             int I = 0, J = 0;
@@ -444,7 +435,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                         row[2] = row[2] + bilinear<T>(v0[2], v0[1], v1[2], v1[1], q4, wy);
                         row[3] = row[3] + bilinear<T>(v0[2], v0[3], v1[2], v1[3], q4, wy);
                     } else {
-                        prolong_generic<T>(row, v0, v1, oI, oJ, cwx, wy, xlane, nx);
+                        prolong_generic<T>(row, v0, v1, cx0, wy, xlane, nx, L.n0x, k, L.ncx);
                     }
                 }
             }
