@@ -10,6 +10,9 @@ What it computes (every function cites the passage it follows):
 
 * ``smooth_stack``  -- phase 1, Sec. 3 "Anisotropic Smoothing": I1 = I0 * G_{sxy,sz},
   with the Gaussian truncated at three standard deviations (Sec. 3 "Implementation").
+* ``robust_smooth_stack`` -- phase 1 with robust averaging across slices (Sec. 3, the
+  outlier example): z-window samples beyond kappa = 2 weighted standard deviations of the
+  weighted mean are left out of the average.
 * ``solve_dct``     -- phase 2, Sec. 3 "Screened-Poisson Blending", Eq. (1):
   (alpha - Lap) I2_j = alpha I1_j - Lap I0_j, solved exactly by the frequency-space blend of
   Sec. 3 "Frequency-Space Interpretation" written for the discrete Neumann problem.
@@ -40,7 +43,8 @@ import numpy as np
 import scipy.fft as sfft
 
 __all__ = [
-    "gaussian_taps", "smooth_axis", "smooth_stack", "smooth_transpose", "dsmooth_dsigma_z",
+    "gaussian_taps", "smooth_axis", "smooth_stack", "robust_smooth_stack", "robust_margin",
+    "smooth_transpose", "dsmooth_dsigma_z",
     "laplacian", "screened_rhs", "apply_A", "neumann_eigenvalues", "solve_dct", "apply_Ainv",
     "relative_residual", "correct_stack", "backward_slice", "backward_stack",
 ]
@@ -105,6 +109,58 @@ def smooth_stack(I0: np.ndarray, sigma_xy: float, sigma_z: float,
     v = smooth_axis(v, sigma_xy, 1, radius_xy)
     v = smooth_axis(v, sigma_z, 0, radius_z)
     return v
+
+
+def robust_smooth_stack(I0: np.ndarray, sigma_xy: float, sigma_z: float, kappa: float = 2.0) -> np.ndarray:
+    """Phase 1 with robust averaging across slices (Sec. 3, the outlier example of Fig.
+    "f:outliers": only colour values within two standard deviations are averaged).
+
+    Reading: x and y are smoothed as in ``smooth_stack``; along z, the window of every voxel
+    (the in-stack taps |d| <= floor(3 sigma_z), weights w_d, values v_d) has weighted mean
+        mu = sum w_d v_d / sum w_d   and variance   var = sum w_d (v_d - mu)^2 / sum w_d;
+    the samples with (v_d - mu)^2 <= kappa^2 var are kept and averaged with their weights
+    renormalised.  kappa = inf gives ``smooth_stack``.
+    """
+    v = np.asarray(I0, dtype=np.float64)
+    v = smooth_axis(v, sigma_xy, 2)
+    v = smooth_axis(v, sigma_xy, 1)
+    w = gaussian_taps(sigma_z)
+    R = (len(w) - 1) // 2
+    nz = v.shape[0]
+    out = np.empty_like(v)
+    for z in range(nz):
+        ds = [d for d in range(-R, R + 1) if 0 <= z + d < nz]
+        ws = np.array([w[d + R] for d in ds])
+        vals = np.stack([v[z + d] for d in ds])               # [taps][y][x]
+        W = ws.sum()
+        mu = np.tensordot(ws, vals, axes=1) / W
+        var = np.tensordot(ws, (vals - mu) ** 2, axes=1) / W
+        keep = (vals - mu) ** 2 <= (kappa * kappa) * var      # [taps][y][x]
+        wk = ws[:, None, None] * keep
+        out[z] = (wk * vals).sum(axis=0) / wk.sum(axis=0)
+    return out
+
+
+def robust_margin(I0: np.ndarray, sigma_xy: float, sigma_z: float, kappa: float = 2.0) -> np.ndarray:
+    """For every voxel, min over its window of | (v_d - mu)^2 - kappa^2 var | / (kappa^2 var + 1):
+    how far the keep / drop decisions of ``robust_smooth_stack`` are from a tie (0 = a tie)."""
+    v = np.asarray(I0, dtype=np.float64)
+    v = smooth_axis(v, sigma_xy, 2)
+    v = smooth_axis(v, sigma_xy, 1)
+    w = gaussian_taps(sigma_z)
+    R = (len(w) - 1) // 2
+    nz = v.shape[0]
+    out = np.empty_like(v)
+    for z in range(nz):
+        ds = [d for d in range(-R, R + 1) if 0 <= z + d < nz]
+        ws = np.array([w[d + R] for d in ds])
+        vals = np.stack([v[z + d] for d in ds])
+        W = ws.sum()
+        mu = np.tensordot(ws, vals, axes=1) / W
+        var = np.tensordot(ws, (vals - mu) ** 2, axes=1) / W
+        thr = (kappa * kappa) * var
+        out[z] = (np.abs((vals - mu) ** 2 - thr) / (thr + 1.0)).min(axis=0)
+    return out
 
 
 def _axis_transpose(g: np.ndarray, sigma: float, axis: int, radius: int | None = None) -> np.ndarray:

@@ -297,3 +297,65 @@ def test_correct_stack_shapes_and_continuity():
     assert I2.shape == I0.shape
     jump = lambda v: float(np.mean((v[1:] - v[:-1]) ** 2))
     assert jump(I2) < 0.5 * jump(I0)
+
+
+# ----------------------------------------------------------------------------- robust averaging
+def test_robust_constant_stack_with_a_corrupt_slice_closed_form():
+    """A constant stack (100) with one slice zeroed (missing data): in every z-window that
+    contains it, the zero sample has weight fraction p <= 1/sum(w) < 0.2, so |0 - mu| =
+    100 (1 - p) exceeds 2 sigma = 200 sqrt(p (1 - p)) while the constant samples stay within
+    it; the robust average is exactly 100 everywhere, the zeroed slice included, whereas the
+    plain average is pulled down next to it."""
+    I0 = np.full((15, 4, 5), 100.0)
+    I0[7] = 0.0
+    out = O.robust_smooth_stack(I0, 0.0, 3.0)
+    np.testing.assert_allclose(out, 100.0, rtol=0, atol=1e-12)
+    plain = O.smooth_stack(I0, 0.0, 3.0)
+    assert plain[6].max() < 90.0
+
+
+def test_robust_reduces_to_plain_for_large_kappa():
+    I0 = np.random.default_rng(4).uniform(0, 255, size=(9, 7, 6))
+    np.testing.assert_allclose(O.robust_smooth_stack(I0, 1.0, 1.5, kappa=1e9), O.smooth_stack(I0, 1.0, 1.5),
+                               rtol=0, atol=1e-10)
+
+
+def test_robust_is_affine_equivariant_and_within_window_range():
+    """robust(a v + b) = a robust(v) + b (mean, deviation and decisions scale together), and
+    each output lies between the smallest and largest xy-smoothed value of its z-window."""
+    I0 = np.random.default_rng(6).uniform(0, 255, size=(10, 6, 5))
+    r = O.robust_smooth_stack(I0, 1.0, 2.0)
+    np.testing.assert_allclose(O.robust_smooth_stack(-3.0 * I0 + 7.0, 1.0, 2.0), -3.0 * r + 7.0,
+                               rtol=0, atol=1e-9)
+    xy = O.smooth_axis(O.smooth_axis(I0, 1.0, 2), 1.0, 1)
+    R = O.support_radius(2.0)
+    for z in range(10):
+        win = xy[max(0, z - R):min(10, z + R + 1)]
+        assert np.all(r[z] >= win.min(axis=0) - 1e-9) and np.all(r[z] <= win.max(axis=0) + 1e-9)
+
+
+def test_robust_keep_and_drop_on_hand_computed_windows():
+    """With sigma_z = 100 every plane of a short stack is in every window with almost equal
+    weights.  Six samples 10, 10, 10, 10, 10, 40: mean 15, variance 125, 2 sigma = 22.4 < 25,
+    so the 40 is dropped and the average is 10.  Three samples 10, 10, 40: mean 20, variance
+    200, 2 sigma = 28.3 > 20, so nothing is dropped and the average is the plain one."""
+    I0 = np.full((6, 1, 1), 10.0)
+    I0[5] = 40.0
+    np.testing.assert_allclose(O.robust_smooth_stack(I0, 0.0, 100.0), 10.0, rtol=0, atol=1e-9)
+    I3 = np.array([10.0, 10.0, 40.0]).reshape(3, 1, 1)
+    np.testing.assert_allclose(O.robust_smooth_stack(I3, 0.0, 100.0), O.smooth_stack(I3, 0.0, 100.0),
+                               rtol=0, atol=1e-12)
+
+
+def test_robust_uses_weighted_statistics_and_kappa_in_sigma_units():
+    """Window [10, 40, 10] at the middle plane with sigma_z = 1 (weights e^-1/2, 1, e^-1/2):
+    the 40 has weight fraction p = 1 / (1 + 2 e^-1/2) = 0.452, and its deviation is
+    sqrt((1 - p) / p) = 1.101 weighted standard deviations (with equal weights it would be
+    sqrt(2) = 1.414).  So kappa = 1.2 keeps it (the plain average) and kappa = 1.05 drops it
+    (the average of the two 10s); an unweighted or variance-scaled threshold fails one of the
+    two."""
+    I0 = np.array([10.0, 40.0, 10.0]).reshape(3, 1, 1)
+    keep = O.robust_smooth_stack(I0, 0.0, 1.0, kappa=1.2)
+    assert keep[1, 0, 0] == pytest.approx(O.smooth_stack(I0, 0.0, 1.0)[1, 0, 0], abs=1e-12)
+    drop = O.robust_smooth_stack(I0, 0.0, 1.0, kappa=1.05)
+    assert drop[1, 0, 0] == pytest.approx(10.0, abs=1e-12)
