@@ -279,7 +279,7 @@ def run_gpu(args):
     import numpy as np
     import torch
     from paper_1506_02079_gb300 import api
-    from paper_1506_02079_gb300.profiling import profile_steps, kernel_roofline, relaxation_roofline
+    from paper_1506_02079_gb300.profiling import profile_steps, kernel_roofline, relaxation_roofline, measured_hbm_peak
 
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
@@ -368,6 +368,23 @@ def run_gpu(args):
                                  "max_rel_residual": max(s["rel_residual"] for s in sa)}
         extras["per_alpha"] = per_alpha
         extras["batched_512"] = batched_extra(dev, args.alpha)
+        # the first "next" row: smoothing with robust averaging across slices, against the
+        # plain smoothing of the same stack (both read the stack once and write s once)
+        sm = {}
+        for label, fn in (("plain", lambda: api.emfuse_smooth_z(I0, 1.0, 3.0, out=out)),
+                          ("robust_kappa2", lambda: api.emfuse_smooth_z_robust(I0, 1.0, 3.0, 2.0, out=out))):
+            fn()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(5):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_s = e0.elapsed_time(e1) / 5
+            gbs = voxels * 8.0 / (ms_s * 1e-3) / 1e9
+            sm[label] = {"ms": ms_s, "value": voxels / (ms_s * 1e-3), "unit": "voxels/s", "gbs": gbs,
+                         "hbm_frac": gbs / measured_hbm_peak()[0]}
+        extras["smoothing"] = sm
         # parity on a sampled slice of the timed output vs the CPU FP64 oracle
         from oracle import emfuse_oracle as O
         api.emfuse_correct_stack(I0, 1.0, 3.0, args.alpha, opts, out=out)

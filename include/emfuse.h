@@ -80,7 +80,10 @@ typedef struct {
                             emfuse_autotune_result).  Default 0.                           */
     int no_graphs;       /* 1: launch every V-cycle kernel directly instead of replaying
                             the V-cycle as a captured CUDA graph.  Default 0.              */
-    int reserved[2];     /* must be zero                                                   */
+    float robust_kappa;  /* emfuse_correct_stack only: > 0 smooths with robust averaging
+                            across slices at this threshold (see emfuse_smooth_z_robust;
+                            the paper uses 2); 0 = plain averaging.  Default 0.            */
+    int reserved[1];     /* must be zero                                                   */
 } emfuse_solve_opts;
 
 /* Per-slice result of a solve. */
@@ -113,6 +116,19 @@ void emfuse_default_opts(emfuse_solve_opts* opts);
 int emfuse_smooth_z(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
                     int64_t pitch, int64_t z0, int64_t z1, float sigma_xy, float sigma_z,
                     void* stream);
+
+/*
+ * Phase 1 with robust averaging across slices (Sec. 3, the outlier example of the figure on
+ * missing data: only colour values within two standard deviations are averaged).  As
+ * emfuse_smooth_z, except along z: for every voxel the in-stack taps |d| <= floor(3 sigma_z)
+ * with weights w_d and xy-smoothed values v_d give the weighted mean mu and variance var;
+ * samples with (v_d - mu)^2 > kappa^2 var are left out and the rest averaged with their
+ * weights renormalised.  kappa >= 1 (the paper: 2).  Needs floor(3 sigma_xy) <= 8 and
+ * floor(3 sigma_z) <= 9 (else EMFUSE_EINVAL).  Asynchronous on `stream`.
+ */
+int emfuse_smooth_z_robust(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                           int64_t pitch, int64_t z0, int64_t z1, float sigma_xy, float sigma_z,
+                           float kappa, void* stream);
 
 /*
  * Allocation-free smoothing.  The paper has no counterpart: this is a deployment variant of

@@ -18,7 +18,8 @@ from . import build as _build
 
 __all__ = [
     "EmfuseError", "EmfuseUnavailable", "SolveOpts", "SliceStats", "lib", "library_path",
-    "default_opts", "emfuse_smooth_z", "emfuse_smooth_z_noalloc", "emfuse_screened_poisson",
+    "default_opts", "emfuse_smooth_z", "emfuse_smooth_z_robust", "emfuse_smooth_z_noalloc",
+    "emfuse_screened_poisson",
     "emfuse_autotune_result", "TuneEntry", "emfuse_correct_stack",
     "emfuse_backward", "emfuse_version", "emfuse_release_cache", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
     "PREC_FP64", "EXPORTED_SYMBOLS",
@@ -32,7 +33,7 @@ EXPORTED_SYMBOLS = ["emfuse_default_opts", "emfuse_smooth_z", "emfuse_screened_p
                     "emfuse_correct_stack", "emfuse_backward", "emfuse_last_error",
                     "emfuse_version", "emfuse_kernel_launches", "emfuse_profile_begin",
                     "emfuse_profile_end", "emfuse_release_cache", "emfuse_smooth_z_noalloc",
-                    "emfuse_selftest_fpconv", "emfuse_autotune_result"]
+                    "emfuse_selftest_fpconv", "emfuse_autotune_result", "emfuse_smooth_z_robust"]
 
 
 class EmfuseError(RuntimeError):
@@ -49,7 +50,7 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_vcycles", ctypes.c_int), ("nu_pre", ctypes.c_int),
                 ("nu_post", ctypes.c_int), ("precision", ctypes.c_int), ("fused", ctypes.c_int),
                 ("first_vcycles", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("no_graphs", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("no_graphs", ctypes.c_int), ("robust_kappa", ctypes.c_float), ("reserved", ctypes.c_int * 1)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -84,6 +85,7 @@ def lib() -> ctypes.CDLL:
             L.emfuse_default_opts.argtypes = [ctypes.POINTER(SolveOpts)]
             L.emfuse_default_opts.restype = None
             L.emfuse_smooth_z.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
+            L.emfuse_smooth_z_robust.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, fl, vp]
             L.emfuse_smooth_z_noalloc.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
             L.emfuse_selftest_fpconv.argtypes = [vp, vp]
             L.emfuse_autotune_result.argtypes = [vp, ci]
@@ -96,7 +98,7 @@ def lib() -> ctypes.CDLL:
             L.emfuse_backward.argtypes = [vp, vp, vp, vp, ci, i64, i64, i64, fl, fl, db, vp, vp, vp,
                                           vp, vp, ctypes.POINTER(SolveOpts), vp]
             for name in ("emfuse_smooth_z", "emfuse_screened_poisson", "emfuse_correct_stack",
-                         "emfuse_backward", "emfuse_smooth_z_noalloc"):
+                         "emfuse_backward", "emfuse_smooth_z_noalloc", "emfuse_smooth_z_robust"):
                 getattr(L, name).restype = ci
             L.emfuse_last_error.restype = ctypes.c_char_p
             L.emfuse_last_error.argtypes = []
@@ -171,6 +173,22 @@ def emfuse_smooth_z(stack: torch.Tensor, sigma_xy: float = 1.0, sigma_z: float =
     _require_cuda(out)
     _check(lib().emfuse_smooth_z(stack.data_ptr(), _dtype_code(stack), out.data_ptr(), nx, ny, nz,
                                  nx, z0, z1, float(sigma_xy), float(sigma_z), _stream_ptr(stack.device)))
+    return out
+
+
+def emfuse_smooth_z_robust(stack: torch.Tensor, sigma_xy: float = 1.0, sigma_z: float = 3.0, kappa: float = 2.0,
+                           out: torch.Tensor | None = None, z0: int = 0, z1: int | None = None) -> torch.Tensor:
+    """Phase 1 with robust averaging across slices (values beyond kappa weighted standard
+    deviations of each z-window's weighted mean are left out; Sec. 3, the outlier example)."""
+    _require_cuda(stack)
+    nz, ny, nx = stack.shape
+    z1 = nz if z1 is None else z1
+    if out is None:
+        out = torch.empty((z1 - z0, ny, nx), device=stack.device, dtype=torch.float32)
+    _require_cuda(out)
+    _check(lib().emfuse_smooth_z_robust(stack.data_ptr(), _dtype_code(stack), out.data_ptr(), nx, ny, nz,
+                                        nx, z0, z1, float(sigma_xy), float(sigma_z), float(kappa),
+                                        _stream_ptr(stack.device)))
     return out
 
 

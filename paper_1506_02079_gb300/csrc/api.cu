@@ -38,6 +38,8 @@ static int resolve_opts(const emfuse_solve_opts* in, emfuse_solve_opts* out) {
         return einval("opts.tile_rows must be 0 or a power of two in [8, 256]");
     if (out->autotune != 0 && out->autotune != 1) return einval("opts.autotune must be 0 or 1");
     if (out->no_graphs != 0 && out->no_graphs != 1) return einval("opts.no_graphs must be 0 or 1");
+    if (!(out->robust_kappa == 0.f || (out->robust_kappa >= 1.f && std::isfinite(out->robust_kappa))))
+        return einval("opts.robust_kappa must be 0 (plain averaging) or finite and >= 1");
     return EMFUSE_OK;
 }
 
@@ -190,7 +192,7 @@ static int correct_stack_host(const void* in, int dt, float* out, int64_t nx, in
             EMF_CUDA(cudaStreamWaitEvent(st, ev_in[q], 0));
             if (i >= 2) EMF_CUDA(cudaStreamWaitEvent(st, ev_out[q], 0));  // dout[q] drained
             EMF_TRY(smooth_stack(din[q].as<char>(), dt, ds.as<float>(), nx, ny, b - a, nx, z0 - a, z1 - a,
-                                 sigma_xy, sigma_z, st, 0));
+                                 sigma_xy, sigma_z, st, 0, o2.robust_kappa));
             const char* o_chunk = din[q].as<char>() + (size_t)((z0 - a) * plane) * esz;
             const int rc = solve_stack(ds.as<float>(), o_chunk, dt, dout[q].as<float>(), nx, ny, z1 - z0, alpha,
                                        o2, stats ? stats + z0 : nullptr, nullptr, st);
@@ -276,6 +278,22 @@ int emfuse_smooth_z(const void* in, int dt, float* out, int64_t nx, int64_t ny, 
                         (cudaStream_t)stream, 0);
 }
 
+int emfuse_smooth_z_robust(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                           int64_t pitch, int64_t z0, int64_t z1, float sigma_xy, float sigma_z,
+                           float kappa, void* stream) {
+    set_error("");
+    if (!in || !out) return einval("emfuse_smooth_z_robust: null pointer");
+    if (!dtype_ok(dt)) return einval("emfuse_smooth_z_robust: dtype must be EMFUSE_U8 or EMFUSE_F32");
+    if (nx < 1 || ny < 1 || nz < 1 || nx > kMaxSide || ny > kMaxSide || nz > kMaxSide)
+        return einval("emfuse_smooth_z_robust: sizes must be in [1, 2^29]");
+    if (pitch < nx) return einval("emfuse_smooth_z_robust: pitch must be >= nx");
+    if (z0 < 0 || z1 > nz || z0 >= z1) return einval("emfuse_smooth_z_robust: need 0 <= z0 < z1 <= nz");
+    if (!(kappa >= 1.f) || !std::isfinite(kappa)) return einval("emfuse_smooth_z_robust: kappa must be finite and >= 1");
+    EMF_TRY(check_sigma(sigma_xy, sigma_z));
+    return smooth_stack(in, dt, out, nx, ny, nz, pitch, z0, z1, sigma_xy, sigma_z, (cudaStream_t)stream, 0,
+                        kappa);
+}
+
 int emfuse_screened_poisson(const float* s, const float* o, float* f, int64_t nslices,
                             const int64_t* nx, const int64_t* ny, const int64_t* offsets,
                             double alpha, const emfuse_solve_opts* opts,
@@ -325,7 +343,8 @@ int emfuse_correct_stack(const void* in, int dt, int in_is_host, float* out, int
     if (!in_is_host) {
         DeviceBuffer sbuf;
         EMF_TRY(sbuf.alloc((size_t)(plane * nz) * sizeof(float), st));
-        EMF_TRY(smooth_stack(in, dt, sbuf.as<float>(), nx, ny, nz, nx, 0, nz, sigma_xy, sigma_z, st, 0));
+        EMF_TRY(smooth_stack(in, dt, sbuf.as<float>(), nx, ny, nz, nx, 0, nz, sigma_xy, sigma_z, st, 0,
+                             o2.robust_kappa));
         return solve_stack(sbuf.as<float>(), in, dt, out, nx, ny, nz, alpha, o2, stats, nullptr, st);
     }
     return correct_stack_host(in, dt, out, nx, ny, nz, sigma_xy, sigma_z, alpha, o2, stats, st);

@@ -17,10 +17,11 @@ int* device_error_flag();
 int support_radius(float sigma);
 std::vector<float> gaussian_taps(float sigma, int R);
 std::vector<float> inverse_norms(const std::vector<float>& w, int n);
-// force_path: 0 = automatic, 1 = three 1-D passes
+// force_path: 0 = automatic, 1 = three 1-D passes; kappa > 0: robust z-averaging (samples
+// beyond kappa weighted standard deviations of the window's weighted mean left out)
 int smooth_stack(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
                  int64_t pitch, int64_t z0, int64_t z1, float sigma_xy, float sigma_z,
-                 cudaStream_t st, int force_path);
+                 cudaStream_t st, int force_path, float kappa = 0.f);
 int smooth_transpose(const float* g, float* out, int64_t nx, int64_t ny, int64_t nz,
                      float sigma_xy, float sigma_z, cudaStream_t st);
 int smooth_dsigma_z(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,

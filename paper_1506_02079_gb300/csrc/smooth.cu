@@ -43,12 +43,43 @@ struct SmoothParams {
     float wxy[2 * kMaxRxy + 1];  // taps w(d), d = -Rxy..Rxy
     float wz[19];                // wz[j] = w(Rz - j), j = 0..2Rz (zero beyond)
     int Rxy, Rz;
+    float kappa2;                // robust averaging: squared threshold in standard deviations
 };
+
+// Robust z-average of one voxel (Sec. 3, the outlier example: only values within kappa
+// weighted standard deviations of the window's weighted mean are averaged).  v[j] are the
+// xy-smoothed window values, w[j] their tap weights (0 for taps outside the stack).
+template <int P>
+__device__ __forceinline__ float robust_window(const float (&v)[P], const float (&w)[P], float kappa2) {
+    float W = 0.f, m = 0.f;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        W += w[j];
+        m = fmaf(w[j], v[j], m);
+    }
+    const float mu = m / W;
+    float s2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const float dv = v[j] - mu;
+        s2 = fmaf(w[j] * dv, dv, s2);
+    }
+    const float thr = kappa2 * (s2 / W);
+    float sk = 0.f, wk = 0.f;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const float dv = v[j] - mu;
+        const float wj = dv * dv <= thr ? w[j] : 0.f;
+        wk += wj;
+        sk = fmaf(wj, v[j], sk);
+    }
+    return sk / wk;
+}
 
 template <class Tin>
 __device__ __forceinline__ float load_in(const Tin* p) { return float(*p); }
 
-template <class Tin, int P>
+template <class Tin, int P, bool ROB>
 __global__ void __launch_bounds__(kThreads, 2)
 smooth_fused_kernel(const Tin* __restrict__ in, float* __restrict__ out, int nx, int ny, int nz,
                     int64_t pitch, int z0, int z1, const float* __restrict__ inv_nx,
@@ -120,14 +151,28 @@ smooth_fused_kernel(const Tin* __restrict__ in, float* __restrict__ out, int nx,
             const int zo = zi - Rz;
             if (zo >= z0 && zo < z1) {
                 float o4[4] = {0.f, 0.f, 0.f, 0.f};
+                float inz = 1.f;
+                if constexpr (ROB) {
+                    float wv[P];
 #pragma unroll
-                for (int j = 0; j < P; ++j) {
-                    const float w = prm.wz[j];
-                    const int slot = (q - j + P * 4) % P;
+                    for (int j = 0; j < P; ++j) wv[j] = (zi - j >= 0 && zi - j < nz) ? prm.wz[j] : 0.f;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) o4[i] = fmaf(w, ring[slot][i], o4[i]);
+                    for (int i = 0; i < 4; ++i) {
+                        float vv[P];
+#pragma unroll
+                        for (int j = 0; j < P; ++j) vv[j] = ring[(q - j + P * 4) % P][i];
+                        o4[i] = robust_window<P>(vv, wv, prm.kappa2);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < P; ++j) {
+                        const float w = prm.wz[j];
+                        const int slot = (q - j + P * 4) % P;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) o4[i] = fmaf(w, ring[slot][i], o4[i]);
+                    }
+                    inz = inv_nz[zo];
                 }
-                const float inz = inv_nz[zo];
                 const int gy = y0 + ty;
                 if (gy < ny) {
                     float* dst = out + (int64_t)(zo - z0) * plane + (int64_t)gy * pitch;
@@ -168,7 +213,7 @@ __device__ __forceinline__ void load_word<uint8_t>(const uint8_t* p, float (&v)[
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
 }
 
-template <class Tin, int R>
+template <class Tin, int R, bool ROB>
 __global__ void __launch_bounds__(kThreads, 2)
 smooth_tma_kernel(const __grid_constant__ CUtensorMap map, float* __restrict__ out, int nx, int ny, int nz,
                   int64_t pitch, int z0, int z1, const float* __restrict__ inv_nx,
@@ -289,13 +334,27 @@ smooth_tma_kernel(const __grid_constant__ CUtensorMap map, float* __restrict__ o
             const int zo = zi - Rz;
             if (zo >= z0 && zo < z1 && gy < ny) {
                 float o4[4] = {0.f, 0.f, 0.f, 0.f};
+                float inz = 1.f;
+                if constexpr (ROB) {
+                    float wv[P];
 #pragma unroll
-                for (int jj = 0; jj < P; ++jj) {
-                    const float wz = prm.wz[jj];
+                    for (int jj = 0; jj < P; ++jj) wv[jj] = (zi - jj >= 0 && zi - jj < nz) ? prm.wz[jj] : 0.f;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) o4[i] = fmaf(wz, ring[u + P - 1 - jj][i], o4[i]);
+                    for (int i = 0; i < 4; ++i) {
+                        float vv[P];
+#pragma unroll
+                        for (int jj = 0; jj < P; ++jj) vv[jj] = ring[u + P - 1 - jj][i];
+                        o4[i] = robust_window<P>(vv, wv, prm.kappa2);
+                    }
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < P; ++jj) {
+                        const float wz = prm.wz[jj];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) o4[i] = fmaf(wz, ring[u + P - 1 - jj][i], o4[i]);
+                    }
+                    inz = inv_nz[zo];
                 }
-                const float inz = inv_nz[zo];
                 float* dst = out + (int64_t)(zo - z0) * plane + (int64_t)gy * pitch + x0 + 4 * tx;
                 const int gx = x0 + 4 * tx;
                 if (gx + 3 < nx && (pitch & 3) == 0) {
@@ -417,9 +476,14 @@ static int upload_norms(DeviceBuffer& buf, const std::vector<float>& ix, const s
 
 int smooth_stack(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
                  int64_t pitch, int64_t z0, int64_t z1, float sigma_xy, float sigma_z,
-                 cudaStream_t st, int force_path) {
+                 cudaStream_t st, int force_path, float kappa) {
     const int Rxy = support_radius(sigma_xy);
     const int Rz = support_radius(sigma_z);
+    const bool rob = kappa > 0.f;
+    if (rob && (Rxy > kMaxRxy || Rz > 9 || force_path == 1)) {
+        set_error("robust averaging needs floor(3 sigma_xy) <= 8 and floor(3 sigma_z) <= 9");
+        return EMFUSE_EINVAL;
+    }
     const auto wxy = gaussian_taps(sigma_xy, Rxy);
     const auto wz = gaussian_taps(sigma_z, Rz);
     std::vector<float> host;
@@ -439,6 +503,7 @@ int smooth_stack(const void* in, int dt, float* out, int64_t nx, int64_t ny, int
         prm.Rz = Rz;
         for (int d = 0; d < 2 * Rxy + 1; ++d) prm.wxy[d] = wxy[d];
         for (int j = 0; j < 2 * Rz + 1; ++j) prm.wz[j] = wz[2 * Rz - j];
+        prm.kappa2 = kappa * kappa;
         CUtensorMap map;
         const int hx = dt == EMFUSE_U8 ? 16 : 4;
         EMF_TRY(encode_tensor_map_3d(&map, in, (int)esz, nx, ny, nz, pitch, kTX + 2 * hx, kTY + 2 * Rxy));
@@ -450,15 +515,21 @@ int smooth_stack(const void* in, int dt, float* out, int64_t nx, int64_t ny, int
         dim3 grid((unsigned)ceil_div(nx, kTX), (unsigned)ceil_div(ny, kTY));
         const int64_t zin0 = std::max<int64_t>(0, z0 - Rz), zin1 = std::min<int64_t>(nz, z1 + Rz);
         {
-            KernelScope ks("smooth_tma", st, (double)nx * ny * ((zin1 - zin0) * (double)esz + (z1 - z0) * 4.0));
-#define EMF_SMOOTH_TMA(RR)                                                                         \
+            KernelScope ks(rob ? "smooth_tma_robust" : "smooth_tma", st,
+                           (double)nx * ny * ((zin1 - zin0) * (double)esz + (z1 - z0) * 4.0));
+#define EMF_SMOOTH_TMA1(RR, RB)                                                                    \
     do {                                                                                           \
         if (dt == EMFUSE_U8)                                                                       \
-            smooth_tma_kernel<uint8_t, RR><<<grid, kThreads, 0, st>>>(map, out, (int)nx, (int)ny, (int)nz, \
+            smooth_tma_kernel<uint8_t, RR, RB><<<grid, kThreads, 0, st>>>(map, out, (int)nx, (int)ny, (int)nz, \
                 pitch, (int)z0, (int)z1, inv_x, inv_y, inv_z, prm, err);              \
         else                                                                                       \
-            smooth_tma_kernel<float, RR><<<grid, kThreads, 0, st>>>(map, out, (int)nx, (int)ny, (int)nz, \
+            smooth_tma_kernel<float, RR, RB><<<grid, kThreads, 0, st>>>(map, out, (int)nx, (int)ny, (int)nz, \
                 pitch, (int)z0, (int)z1, inv_x, inv_y, inv_z, prm, err);              \
+    } while (0)
+#define EMF_SMOOTH_TMA(RR)                                                                         \
+    do {                                                                                           \
+        if (rob) EMF_SMOOTH_TMA1(RR, true);                                                        \
+        else EMF_SMOOTH_TMA1(RR, false);                                                           \
     } while (0)
             switch (Rxy) {
                 case 0: EMF_SMOOTH_TMA(0); break;
@@ -468,6 +539,7 @@ int smooth_stack(const void* in, int dt, float* out, int64_t nx, int64_t ny, int
                 default: EMF_SMOOTH_TMA(4); break;
             }
 #undef EMF_SMOOTH_TMA
+#undef EMF_SMOOTH_TMA1
             EMF_CHECK_LAUNCH();
         }
         // a timed-out wait is reported by the next call that synchronises (the solves)
@@ -480,26 +552,33 @@ int smooth_stack(const void* in, int dt, float* out, int64_t nx, int64_t ny, int
         prm.Rz = Rz;
         for (int d = 0; d < 2 * Rxy + 1; ++d) prm.wxy[d] = wxy[d];
         for (int j = 0; j < 2 * Rz + 1; ++j) prm.wz[j] = wz[2 * Rz - j];
+        prm.kappa2 = kappa * kappa;
         dim3 grid((unsigned)ceil_div(nx, kTX), (unsigned)ceil_div(ny, kTY));
         const int P = 2 * Rz + 1;
         const int64_t zin0 = std::max<int64_t>(0, z0 - Rz), zin1 = std::min<int64_t>(nz, z1 + Rz);
-        KernelScope ks("smooth_fused", st,
+        KernelScope ks(rob ? "smooth_fused_robust" : "smooth_fused", st,
                        (double)nx * ny * ((zin1 - zin0) * (dt == EMFUSE_U8 ? 1.0 : 4.0) + (z1 - z0) * 4.0));
-#define EMF_SMOOTH_LAUNCH(PP)                                                                  \
+#define EMF_SMOOTH_LAUNCH1(PP, RB)                                                             \
     do {                                                                                       \
         if (dt == EMFUSE_U8)                                                                   \
-            smooth_fused_kernel<uint8_t, PP><<<grid, kThreads, 0, st>>>(                       \
+            smooth_fused_kernel<uint8_t, PP, RB><<<grid, kThreads, 0, st>>>(                   \
                 (const uint8_t*)in, out, (int)nx, (int)ny, (int)nz, pitch, (int)z0, (int)z1,   \
                 inv_x, inv_y, inv_z, prm);                                                     \
         else                                                                                   \
-            smooth_fused_kernel<float, PP><<<grid, kThreads, 0, st>>>(                         \
+            smooth_fused_kernel<float, PP, RB><<<grid, kThreads, 0, st>>>(                     \
                 (const float*)in, out, (int)nx, (int)ny, (int)nz, pitch, (int)z0, (int)z1,     \
                 inv_x, inv_y, inv_z, prm);                                                     \
+    } while (0)
+#define EMF_SMOOTH_LAUNCH(PP)                                                                  \
+    do {                                                                                       \
+        if (rob) EMF_SMOOTH_LAUNCH1(PP, true);                                                 \
+        else EMF_SMOOTH_LAUNCH1(PP, false);                                                    \
     } while (0)
         if (P <= 1) EMF_SMOOTH_LAUNCH(1);
         else if (P <= 7) EMF_SMOOTH_LAUNCH(7);
         else EMF_SMOOTH_LAUNCH(19);
 #undef EMF_SMOOTH_LAUNCH
+#undef EMF_SMOOTH_LAUNCH1
         EMF_CHECK_LAUNCH();
         return EMFUSE_OK;
     }
@@ -699,11 +778,11 @@ extern "C" int emfuse_smooth_z_noalloc(const void* in, int dt, float* out, int64
 #define EMF_NOALLOC_LAUNCH(PP)                                                               \
     do {                                                                                     \
         if (dt == EMFUSE_U8)                                                                 \
-            smooth_fused_kernel<uint8_t, PP><<<grid, kThreads, 0, st>>>(                     \
+            smooth_fused_kernel<uint8_t, PP, false><<<grid, kThreads, 0, st>>>(              \
                 (const uint8_t*)in, out, (int)nx, (int)ny, (int)nz, pitch, (int)z0, (int)z1, \
                 inv_x, inv_y, inv_z, prm);                                                   \
         else                                                                                 \
-            smooth_fused_kernel<float, PP><<<grid, kThreads, 0, st>>>(                       \
+            smooth_fused_kernel<float, PP, false><<<grid, kThreads, 0, st>>>(                \
                 (const float*)in, out, (int)nx, (int)ny, (int)nz, pitch, (int)z0, (int)z1,   \
                 inv_x, inv_y, inv_z, prm);                                                   \
     } while (0)

@@ -202,3 +202,71 @@ def test_sharded_slabs_equal_whole_stack(dev, dtype):
         s = sharding.slab_bounds(20, 3, r, 3.0)
         parts.append(sharding.correct_slab(I0[s.a:s.b].contiguous(), s, 1.0, 3.0, 0.01))
     assert torch.equal(torch.cat(parts), full)
+
+
+# ----------------------------------------------------------------------------- robust averaging
+def corrupted_stack(nz, ny, nx, seed, dtype=torch.float32):
+    """A synthetic stack with missing data: a rectangle of one slice set to 0 (the situation of
+    the paper's outlier example)."""
+    I0 = make_stack(nz, ny, nx, seed=seed, out_dtype=dtype)
+    I0[nz // 2, ny // 4:3 * ny // 4, nx // 5:4 * nx // 5] = 0
+    return I0
+
+
+def robust_compare(got, I0, sxy, sz, kappa):
+    """Element-wise against the oracle wherever no keep / drop decision of the window is within
+    a relative 1e-3 of a tie (FP32 and FP64 may decide ties differently; either is valid)."""
+    x = I0.double().numpy()
+    ref = O.robust_smooth_stack(x, sxy, sz, kappa)
+    margin = O.robust_margin(x, sxy, sz, kappa)
+    clear = margin > 1e-3
+    assert clear.mean() > 0.99
+    d = np.abs(np.asarray(got, np.float64) - ref)[clear]
+    assert d.max() <= SMOOTH_TOL
+
+
+@pytest.mark.parametrize("shape,dtype", [((17, 64, 96), torch.float32), ((12, 40, 33), torch.uint8),
+                                         ((9, 33, 70), torch.float32)])
+@pytest.mark.parametrize("sig", [(1.0, 3.0), (0.5, 1.5)])
+def test_robust_smoothing_matches_oracle(dev, shape, dtype, sig):
+    I0 = corrupted_stack(*shape, seed=31, dtype=dtype)
+    got = api.emfuse_smooth_z_robust(I0.to(dev), *sig, kappa=2.0).cpu().numpy()
+    robust_compare(got, I0, *sig, 2.0)
+
+
+def test_robust_smoothing_removes_the_missing_slice_and_slabs_are_exact(dev):
+    """Next to the zeroed rectangle the plain average is pulled down; the robust one is not
+    (the paper's outlier example); and slabs with floor(3 sigma_z) halo planes give exactly the
+    stack's slices, as for the plain smoothing."""
+    I0 = corrupted_stack(30, 64, 80, seed=32).to(dev)   # slice 15 has the missing rectangle
+    rob = api.emfuse_smooth_z_robust(I0, 1.0, 3.0, kappa=2.0)
+    plain = api.emfuse_smooth_z(I0, 1.0, 3.0)
+    clean = make_stack(30, 64, 80, seed=32).to(dev)
+    rob_clean = api.emfuse_smooth_z_robust(clean, 1.0, 3.0, kappa=2.0)
+    plain_clean = api.emfuse_smooth_z(clean, 1.0, 3.0)
+    # what the missing rectangle changes in and next to its slice: the plain average is pulled
+    # toward the zeros; the robust one leaves them out (it then misses that slice's true values,
+    # which may shift it either way, but not toward 0)
+    region = (slice(14, 17), slice(24, 40), slice(24, 56))
+    pull_rob = float((rob[region] - rob_clean[region]).mean())
+    pull_plain = float((plain[region] - plain_clean[region]).mean())
+    assert pull_plain < -5.0 and pull_rob > 0.1 * pull_plain, (pull_rob, pull_plain)
+    part = api.emfuse_smooth_z_robust(I0[5:25].contiguous(), 1.0, 3.0, kappa=2.0, z0=9, z1=11)
+    assert torch.equal(part, rob[14:16])
+    big = api.emfuse_smooth_z_robust(I0, 1.0, 3.0, kappa=1e6)
+    assert float((big - plain).abs().max()) <= SMOOTH_TOL
+
+
+def test_correct_stack_with_robust_averaging(dev):
+    """correct_stack with robust averaging is the robust smoothing (checked against the oracle
+    above, near-ties aside) followed by the solve: bit for bit the two calls, and within the solve
+    bar of the oracle's solve of the same s."""
+    I0 = corrupted_stack(10, 48, 64, seed=33).to(dev)
+    got = api.emfuse_correct_stack(I0, 1.0, 3.0, 0.01, api.default_opts(robust_kappa=2.0))
+    s = api.emfuse_smooth_z_robust(I0, 1.0, 3.0, kappa=2.0)
+    assert torch.equal(got, api.emfuse_screened_poisson(s, I0, 0.01))
+    s64, x = s.double().cpu().numpy(), I0.double().cpu().numpy()
+    ref = np.stack([O.solve_dct(s64[j], x[j], 0.01) for j in range(10)])
+    assert maxdiff(got.cpu().numpy(), ref) <= SOLVE_TOL
+    with pytest.raises(api.EmfuseError):
+        api.emfuse_correct_stack(I0, 1.0, 3.0, 0.01, api.default_opts(robust_kappa=0.5))
