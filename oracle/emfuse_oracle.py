@@ -17,6 +17,8 @@ What it computes (every function cites the passage it follows):
   (alpha - Lap) I2_j = alpha I1_j - Lap I0_j, solved exactly by the frequency-space blend of
   Sec. 3 "Frequency-Space Interpretation" written for the discrete Neumann problem.
 * ``correct_stack`` -- both phases.
+* ``fuse_color``    -- the colour / monochrome fusion example of Sec. 3: one solve per colour
+  channel with the grey image as the gradient constraint.
 * ``backward_*``    -- the adjoint of both phases (gradients w.r.t. s, o, alpha, I0, sigma_z).
 
 Readings of points the paper leaves open:
@@ -45,7 +47,7 @@ import scipy.fft as sfft
 __all__ = [
     "gaussian_taps", "smooth_axis", "smooth_stack", "robust_smooth_stack", "robust_margin",
     "smooth_transpose", "dsmooth_dsigma_z",
-    "laplacian", "screened_rhs", "apply_A", "neumann_eigenvalues", "solve_dct", "apply_Ainv",
+    "laplacian", "screened_rhs", "apply_A", "neumann_eigenvalues", "solve_dct", "fuse_color", "apply_Ainv",
     "relative_residual", "correct_stack", "backward_slice", "backward_stack",
 ]
 
@@ -279,6 +281,15 @@ def solve_dct(s: np.ndarray, o: np.ndarray, alpha: float) -> np.ndarray:
     o_hat = sfft.dctn(o, type=2, norm="ortho", workers=-1)
     f_hat = (alpha * s_hat + lam * o_hat) / (alpha + lam)
     return sfft.idctn(f_hat, type=2, norm="ortho", workers=-1)
+
+
+def fuse_color(s_rgb: np.ndarray, o_grey: np.ndarray, alpha: float) -> np.ndarray:
+    """Fusion of a low-frequency colour image with a high-frequency monochrome one (Sec. 3,
+    the colour example): the colour channels give the value constraints, the grey image, copied
+    into every channel, the gradient constraints; one solve of Eq. (1) per channel.
+    s_rgb: [3][ny][nx], o_grey: [ny][nx]."""
+    s_rgb = np.asarray(s_rgb, dtype=np.float64)
+    return np.stack([solve_dct(s_rgb[c], o_grey, alpha) for c in range(s_rgb.shape[0])])
 
 
 def apply_Ainv(rhs: np.ndarray, alpha: float) -> np.ndarray:

@@ -359,3 +359,35 @@ def test_robust_uses_weighted_statistics_and_kappa_in_sigma_units():
     assert keep[1, 0, 0] == pytest.approx(O.smooth_stack(I0, 0.0, 1.0)[1, 0, 0], abs=1e-12)
     drop = O.robust_smooth_stack(I0, 0.0, 1.0, kappa=1.05)
     assert drop[1, 0, 0] == pytest.approx(10.0, abs=1e-12)
+
+
+# ----------------------------------------------------------------------------- colour fusion
+def test_fuse_color_closed_forms():
+    """Colour / monochrome fusion (Sec. 3): (1) a grey colour image (three equal channels)
+    gives three copies of the monochrome solve; (2) each channel keeps the mean of its colour
+    channel (the DCT mode 0 has gain 1); (3) the difference of two channels is
+    alpha A^-1 (s_c - s_d), so it does not depend on the monochrome image at all, and it is
+    the low-pass of the colour difference (checked against the dense inverse)."""
+    rng = np.random.default_rng(12)
+    ny, nx, alpha = 6, 7, 0.2
+    s = rng.uniform(0, 255, size=(3, ny, nx))
+    o = rng.uniform(0, 255, size=(ny, nx))
+    f = O.fuse_color(s, o, alpha)
+    grey = O.fuse_color(np.stack([s[0]] * 3), o, alpha)
+    for c in range(3):
+        np.testing.assert_allclose(grey[c], O.solve_dct(s[0], o, alpha), rtol=0, atol=1e-9)
+        assert f[c].mean() == pytest.approx(s[c].mean(), rel=1e-12)
+    f2 = O.fuse_color(s, rng.uniform(0, 255, size=(ny, nx)), alpha)
+    np.testing.assert_allclose(f[0] - f[1], f2[0] - f2[1], rtol=0, atol=1e-9)
+    # dense (alpha I + L) on the ny x nx grid, built edge by edge
+    n = ny * nx
+    A = alpha * np.eye(n)
+    for y in range(ny):
+        for x in range(nx):
+            p = y * nx + x
+            for qy, qx in ((y, x + 1), (y + 1, x)):
+                if qy < ny and qx < nx:
+                    q = qy * nx + qx
+                    A[p, p] += 1; A[q, q] += 1; A[p, q] -= 1; A[q, p] -= 1
+    diff = alpha * np.linalg.solve(A, (s[0] - s[2]).ravel()).reshape(ny, nx)
+    np.testing.assert_allclose(f[0] - f[2], diff, rtol=0, atol=1e-8)
