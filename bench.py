@@ -385,6 +385,27 @@ def run_gpu(args):
             sm[label] = {"ms": ms_s, "value": voxels / (ms_s * 1e-3), "unit": "voxels/s", "gbs": gbs,
                          "hbm_frac": gbs / measured_hbm_peak()[0]}
         extras["smoothing"] = sm
+        # colour / monochrome fusion (Sec. 3 colour example): 4 images of 4096 x 4096, RGB value
+        # constraints (colour casts of the synthetic base), grey gradient constraints
+        from paper_1506_02079_gb300.synthetic import make_stack as _mk
+        base = _mk(4, 4096, 4096, 5, device=dev)
+        casts = torch.tensor([[1.1, 5.0], [0.9, -3.0], [1.0, 12.0]], device=dev)
+        s_rgb = (base[:, None] * casts[None, :, 0, None, None] + casts[None, :, 1, None, None]).clamp_(0, 255)
+        s_rgb = s_rgb.contiguous()
+        api.emfuse_fuse_color(s_rgb, base, args.alpha)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            _, stc = api.emfuse_fuse_color(s_rgb, base, args.alpha, return_stats=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_c = e0.elapsed_time(e1) / 3
+        extras["color_fusion"] = {"images": 4, "ny": 4096, "nx": 4096, "channels": 3, "ms": ms_c,
+                                  "value": s_rgb.numel() / (ms_c * 1e-3), "unit": "pixels/s",
+                                  "vcycles": max(a["vcycles"] for a in stc),
+                                  "max_rel_residual": max(a["rel_residual"] for a in stc)}
+        del base, s_rgb
+        torch.cuda.empty_cache()
         # parity on a sampled slice of the timed output vs the CPU FP64 oracle
         from oracle import emfuse_oracle as O
         api.emfuse_correct_stack(I0, 1.0, 3.0, args.alpha, opts, out=out)

@@ -188,6 +188,21 @@ typedef struct {
 int emfuse_autotune_result(emfuse_tune_entry* out, int max_entries);
 
 /*
+ * Fusion of low-frequency colour images with high-frequency monochrome ones (Sec. 3, the
+ * colour example): for every image i and colour channel c, Eq. (1) with the colour channel as
+ * the value constraint and the grey image as the gradient constraint,
+ *     (alpha I + L) f_{i,c} = alpha s_{i,c} + L o_i,
+ * solved as one batch of 3 * nimages slices.
+ *   s_rgb, f_rgb  device float32, planar: image i channel c is the ny x nx plane 3 i + c.
+ *   o_grey        device float32, one ny x nx plane per image.
+ *   stats         NULL or a HOST array of 3 * nimages entries (plane order).
+ * Allocates a temporary copy of o_grey per channel (3 * nimages planes) on `stream`.
+ */
+int emfuse_fuse_color(const float* s_rgb, const float* o_grey, float* f_rgb, int64_t nimages, int64_t nx,
+                      int64_t ny, double alpha, const emfuse_solve_opts* opts, emfuse_slice_stats* stats,
+                      void* stream);
+
+/*
  * Both phases on a stack: s = smooth(I0), then f_j = solve(s_j, o_j = I0_j) for every j.
  *
  *   in        I0, nz x ny x nx dense, dtype `dt`.

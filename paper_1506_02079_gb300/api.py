@@ -20,7 +20,7 @@ __all__ = [
     "EmfuseError", "EmfuseUnavailable", "SolveOpts", "SliceStats", "lib", "library_path",
     "default_opts", "emfuse_smooth_z", "emfuse_smooth_z_robust", "emfuse_smooth_z_noalloc",
     "emfuse_screened_poisson",
-    "emfuse_autotune_result", "TuneEntry", "emfuse_correct_stack",
+    "emfuse_autotune_result", "TuneEntry", "emfuse_fuse_color", "emfuse_correct_stack",
     "emfuse_backward", "emfuse_version", "emfuse_release_cache", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
     "PREC_FP64", "EXPORTED_SYMBOLS",
 ]
@@ -33,7 +33,8 @@ EXPORTED_SYMBOLS = ["emfuse_default_opts", "emfuse_smooth_z", "emfuse_screened_p
                     "emfuse_correct_stack", "emfuse_backward", "emfuse_last_error",
                     "emfuse_version", "emfuse_kernel_launches", "emfuse_profile_begin",
                     "emfuse_profile_end", "emfuse_release_cache", "emfuse_smooth_z_noalloc",
-                    "emfuse_selftest_fpconv", "emfuse_autotune_result", "emfuse_smooth_z_robust"]
+                    "emfuse_selftest_fpconv", "emfuse_autotune_result", "emfuse_smooth_z_robust",
+                    "emfuse_fuse_color"]
 
 
 class EmfuseError(RuntimeError):
@@ -86,6 +87,7 @@ def lib() -> ctypes.CDLL:
             L.emfuse_default_opts.restype = None
             L.emfuse_smooth_z.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
             L.emfuse_smooth_z_robust.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, fl, vp]
+            L.emfuse_fuse_color.argtypes = [vp, vp, vp, i64, i64, i64, db, ctypes.POINTER(SolveOpts), vp, vp]
             L.emfuse_smooth_z_noalloc.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
             L.emfuse_selftest_fpconv.argtypes = [vp, vp]
             L.emfuse_autotune_result.argtypes = [vp, ci]
@@ -98,7 +100,8 @@ def lib() -> ctypes.CDLL:
             L.emfuse_backward.argtypes = [vp, vp, vp, vp, ci, i64, i64, i64, fl, fl, db, vp, vp, vp,
                                           vp, vp, ctypes.POINTER(SolveOpts), vp]
             for name in ("emfuse_smooth_z", "emfuse_screened_poisson", "emfuse_correct_stack",
-                         "emfuse_backward", "emfuse_smooth_z_noalloc", "emfuse_smooth_z_robust"):
+                         "emfuse_backward", "emfuse_smooth_z_noalloc", "emfuse_smooth_z_robust",
+                         "emfuse_fuse_color"):
                 getattr(L, name).restype = ci
             L.emfuse_last_error.restype = ctypes.c_char_p
             L.emfuse_last_error.argtypes = []
@@ -273,6 +276,29 @@ def emfuse_screened_poisson(s, o, alpha: float, opts: SolveOpts | None = None, *
         f = [f[int(a):int(a) + h * w].view(h, w) for a, (h, w) in zip(offs, shapes)]
     elif isinstance(s, torch.Tensor) and s.dim() == 2 and nx is None:
         f = f[0]
+    return (f, _stats_list(stats)) if return_stats else f
+
+
+def emfuse_fuse_color(s_rgb: torch.Tensor, o_grey: torch.Tensor, alpha: float, opts: SolveOpts | None = None,
+                      return_stats: bool = False, allow_noconv: bool = False):
+    """Colour / monochrome fusion (Sec. 3): ``s_rgb`` [n][3][ny][nx] or [3][ny][nx] colour
+    images (value constraints), ``o_grey`` [n][ny][nx] or [ny][nx] monochrome images (gradient
+    constraints of every channel); CUDA float32.  Returns f with the shape of ``s_rgb``."""
+    _require_cuda(s_rgb, o_grey)
+    single = s_rgb.dim() == 3
+    s4 = s_rgb[None] if single else s_rgb
+    o3 = o_grey[None] if single else o_grey
+    n, c, ny, nx = s4.shape
+    if c != 3 or tuple(o3.shape) != (n, ny, nx):
+        raise ValueError("expected s_rgb [n][3][ny][nx] and o_grey [n][ny][nx]")
+    if s4.dtype != torch.float32 or o3.dtype != torch.float32:
+        raise TypeError("s_rgb and o_grey must be float32")
+    f = torch.empty_like(s4)
+    stats = (SliceStats * (3 * n))()
+    _check(lib().emfuse_fuse_color(s4.data_ptr(), o3.data_ptr(), f.data_ptr(), n, nx, ny, float(alpha),
+                                   ctypes.byref(opts) if opts is not None else None, ctypes.addressof(stats),
+                                   _stream_ptr(s4.device)), allow_noconv)
+    f = f[0] if single else f
     return (f, _stats_list(stats)) if return_stats else f
 
 

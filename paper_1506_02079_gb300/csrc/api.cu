@@ -325,6 +325,43 @@ int emfuse_screened_poisson(const float* s, const float* o, float* f, int64_t ns
     return solve_batch(req, (cudaStream_t)stream);
 }
 
+int emfuse_fuse_color(const float* s_rgb, const float* o_grey, float* f_rgb, int64_t nimages, int64_t nx,
+                      int64_t ny, double alpha, const emfuse_solve_opts* opts, emfuse_slice_stats* stats,
+                      void* stream) {
+    set_error("");
+    if (!s_rgb || !o_grey || !f_rgb) return einval("emfuse_fuse_color: null pointer");
+    if (nimages < 1 || nx < 1 || ny < 1 || nx > kMaxSide || ny > kMaxSide)
+        return einval("emfuse_fuse_color: need nimages >= 1 and sizes in [1, 2^29]");
+    if (f_rgb == s_rgb) return einval("emfuse_fuse_color: f_rgb must not alias s_rgb");
+    EMF_TRY(check_alpha(alpha));
+    emfuse_solve_opts o2;
+    EMF_TRY(resolve_opts(opts, &o2));
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int64_t plane = nx * ny, n = 3 * nimages;
+    // the grey image is the gradient constraint of every channel: one copy per channel
+    DeviceBuffer o3;
+    EMF_TRY(o3.alloc((size_t)(n * plane) * sizeof(float), st));
+    for (int64_t i = 0; i < nimages; ++i)
+        for (int c = 0; c < 3; ++c)
+            EMF_CUDA(cudaMemcpyAsync(o3.as<float>() + (3 * i + c) * plane, o_grey + i * plane,
+                                     (size_t)plane * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    std::vector<int64_t> vx(n, nx), vy(n, ny), off(n);
+    for (int64_t j = 0; j < n; ++j) off[j] = j * plane;
+    SolveRequest req;
+    req.s = s_rgb;
+    req.o = o3.as<float>();
+    req.o_dtype = EMFUSE_F32;
+    req.out = f_rgb;
+    req.nslices = n;
+    req.nx = vx.data();
+    req.ny = vy.data();
+    req.offsets = off.data();
+    req.alpha = alpha;
+    req.opts = o2;
+    req.stats = stats;
+    return solve_batch(req, st);
+}
+
 int emfuse_correct_stack(const void* in, int dt, int in_is_host, float* out, int64_t nx,
                          int64_t ny, int64_t nz, float sigma_xy, float sigma_z, double alpha,
                          const emfuse_solve_opts* opts, emfuse_slice_stats* stats,

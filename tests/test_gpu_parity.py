@@ -270,3 +270,24 @@ def test_correct_stack_with_robust_averaging(dev):
     assert maxdiff(got.cpu().numpy(), ref) <= SOLVE_TOL
     with pytest.raises(api.EmfuseError):
         api.emfuse_correct_stack(I0, 1.0, 3.0, 0.01, api.default_opts(robust_kappa=0.5))
+
+
+# ----------------------------------------------------------------------------- colour fusion
+def test_fuse_color_matches_oracle_and_per_channel_solves(dev):
+    """Colour / monochrome fusion: against the oracle per channel, and bit for bit the same as
+    solving each channel with the grey image as its own call (batching does not change results)."""
+    rng = np.random.default_rng(21)
+    n, ny, nx = 2, 96, 130
+    base = make_stack(n, ny, nx, seed=22).numpy()
+    s = np.stack([np.stack([np.clip(base[i] * g + b, 0, 255) for g, b in ((1.1, 5), (0.9, -3), (1.0, 12))])
+                  for i in range(n)]).astype(np.float32)                     # colour casts per channel
+    o = (base + rng.normal(0, 6, size=base.shape)).astype(np.float32)         # detailed monochrome
+    sd, od = torch.from_numpy(s).to(dev), torch.from_numpy(o).to(dev)
+    f, st = api.emfuse_fuse_color(sd, od, 0.01, return_stats=True)
+    assert f.shape == sd.shape and all(a["converged"] for a in st)
+    for i in range(n):
+        ref = O.fuse_color(s[i], o[i], 0.01)
+        assert maxdiff(f[i].cpu().numpy(), ref) <= SOLVE_TOL
+        for c in range(3):
+            one = api.emfuse_screened_poisson(sd[i, c].contiguous(), od[i].contiguous(), 0.01)
+            assert torch.equal(f[i, c], one)
