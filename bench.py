@@ -385,6 +385,29 @@ def run_gpu(args):
             sm[label] = {"ms": ms_s, "value": voxels / (ms_s * 1e-3), "unit": "voxels/s", "gbs": gbs,
                          "hbm_frac": gbs / measured_hbm_peak()[0]}
         extras["smoothing"] = sm
+        # the second next row: the direct FFT solve of the same 64 solves (mirror extension,
+        # cuFFT) against the multigrid solve alone, and their largest difference
+        s_c2 = api.emfuse_smooth_z(I0, 1.0, 3.0)
+        sol = {}
+        for label, fn in (("multigrid_mixed", lambda: api.emfuse_screened_poisson(s_c2, I0, args.alpha, opts)),
+                          ("fft_fp32", lambda: api.emfuse_screened_poisson_dct(s_c2, I0, args.alpha, api.PREC_FP32)),
+                          ("fft_fp64", lambda: api.emfuse_screened_poisson_dct(s_c2, I0, args.alpha, api.PREC_FP64))):
+            res = fn()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(2):
+                res = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sol[label] = {"ms": e0.elapsed_time(e1) / 2, "value": voxels / (e0.elapsed_time(e1) / 2 * 1e-3),
+                          "unit": "voxels/s"}
+            sol[label + "_out"] = res
+        sol["max_abs_diff_multigrid_vs_fft_fp64"] = float((sol.pop("multigrid_mixed_out") - sol["fft_fp64_out"]).abs().max())
+        sol["max_abs_diff_fft_fp32_vs_fft_fp64"] = float((sol.pop("fft_fp32_out") - sol.pop("fft_fp64_out")).abs().max())
+        extras["solve_multigrid_vs_fft"] = sol
+        del s_c2
+        api.emfuse_release_cache()
+        torch.cuda.empty_cache()
         # colour / monochrome fusion (Sec. 3 colour example): 4 images of 4096 x 4096, RGB value
         # constraints (colour casts of the synthetic base), grey gradient constraints
         from paper_1506_02079_gb300.synthetic import make_stack as _mk

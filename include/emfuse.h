@@ -188,6 +188,23 @@ typedef struct {
 int emfuse_autotune_result(emfuse_tune_entry* out, int max_entries);
 
 /*
+ * Direct solve of Eq. (1) by fast Fourier transforms: the frequency-space form of Sec. 3
+ * ("Frequency-Space Interpretation"; the FFT solver that Sec. 3 "Alternate Solutions" weighs
+ * against multigrid), as an exact second solver to compare the multigrid against.  For every
+ * slice, f = o + d with d = alpha A^{-1} (s - o) computed on the mirror extension of the slice
+ * to 2ny x 2nx (whose periodic Laplacian is the Neumann one of the slice) by one batched
+ * real-to-complex FFT, a per-frequency scaling by alpha / (alpha + lambda), and one inverse FFT
+ * (cuFFT).
+ *   s, o, f     device float32, nslices dense slices of ny x nx (uniform batch).
+ *   precision   EMFUSE_PREC_FP32 or EMFUSE_PREC_FP64 (transforms and scaling in that type).
+ * Temporaries: the extended slices and their spectra (about 4 and 4 times the slices, in the
+ * chosen type), from the library's pool; cuFFT plans are cached per size, batch and precision
+ * until emfuse_release_cache().  Asynchronous on `stream`.
+ */
+int emfuse_screened_poisson_dct(const float* s, const float* o, float* f, int64_t nslices, int64_t nx,
+                                int64_t ny, double alpha, int precision, void* stream);
+
+/*
  * Fusion of low-frequency colour images with high-frequency monochrome ones (Sec. 3, the
  * colour example): for every image i and colour channel c, Eq. (1) with the colour channel as
  * the value constraint and the grey image as the gradient constraint,

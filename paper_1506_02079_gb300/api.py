@@ -20,7 +20,7 @@ __all__ = [
     "EmfuseError", "EmfuseUnavailable", "SolveOpts", "SliceStats", "lib", "library_path",
     "default_opts", "emfuse_smooth_z", "emfuse_smooth_z_robust", "emfuse_smooth_z_noalloc",
     "emfuse_screened_poisson",
-    "emfuse_autotune_result", "TuneEntry", "emfuse_fuse_color", "emfuse_correct_stack",
+    "emfuse_autotune_result", "TuneEntry", "emfuse_fuse_color", "emfuse_screened_poisson_dct", "emfuse_correct_stack",
     "emfuse_backward", "emfuse_version", "emfuse_release_cache", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
     "PREC_FP64", "EXPORTED_SYMBOLS",
 ]
@@ -34,7 +34,7 @@ EXPORTED_SYMBOLS = ["emfuse_default_opts", "emfuse_smooth_z", "emfuse_screened_p
                     "emfuse_version", "emfuse_kernel_launches", "emfuse_profile_begin",
                     "emfuse_profile_end", "emfuse_release_cache", "emfuse_smooth_z_noalloc",
                     "emfuse_selftest_fpconv", "emfuse_autotune_result", "emfuse_smooth_z_robust",
-                    "emfuse_fuse_color"]
+                    "emfuse_fuse_color", "emfuse_screened_poisson_dct"]
 
 
 class EmfuseError(RuntimeError):
@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
             L.emfuse_smooth_z.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
             L.emfuse_smooth_z_robust.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, fl, vp]
             L.emfuse_fuse_color.argtypes = [vp, vp, vp, i64, i64, i64, db, ctypes.POINTER(SolveOpts), vp, vp]
+            L.emfuse_screened_poisson_dct.argtypes = [vp, vp, vp, i64, i64, i64, db, ci, vp]
             L.emfuse_smooth_z_noalloc.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
             L.emfuse_selftest_fpconv.argtypes = [vp, vp]
             L.emfuse_autotune_result.argtypes = [vp, ci]
@@ -101,7 +102,7 @@ def lib() -> ctypes.CDLL:
                                           vp, vp, ctypes.POINTER(SolveOpts), vp]
             for name in ("emfuse_smooth_z", "emfuse_screened_poisson", "emfuse_correct_stack",
                          "emfuse_backward", "emfuse_smooth_z_noalloc", "emfuse_smooth_z_robust",
-                         "emfuse_fuse_color"):
+                         "emfuse_fuse_color", "emfuse_screened_poisson_dct"):
                 getattr(L, name).restype = ci
             L.emfuse_last_error.restype = ctypes.c_char_p
             L.emfuse_last_error.argtypes = []
@@ -277,6 +278,22 @@ def emfuse_screened_poisson(s, o, alpha: float, opts: SolveOpts | None = None, *
     elif isinstance(s, torch.Tensor) and s.dim() == 2 and nx is None:
         f = f[0]
     return (f, _stats_list(stats)) if return_stats else f
+
+
+def emfuse_screened_poisson_dct(s: torch.Tensor, o: torch.Tensor, alpha: float, precision: int = PREC_FP64,
+                                out: torch.Tensor | None = None) -> torch.Tensor:
+    """Direct solve of Eq. (1) by fast transforms (cuFFT on the mirror-extended slices) for a
+    uniform batch: ``s``, ``o`` CUDA float32 [z][y][x] or [y][x]; precision PREC_FP32 / PREC_FP64."""
+    _require_cuda(s, o)
+    s3 = s[None] if s.dim() == 2 else s
+    o3 = o[None] if o.dim() == 2 else o
+    if s3.shape != o3.shape or s3.dtype != torch.float32 or o3.dtype != torch.float32:
+        raise ValueError("s and o must be float32 with the same shape")
+    n, ny, nx = s3.shape
+    f = torch.empty_like(s3) if out is None else out.view(n, ny, nx)
+    _check(lib().emfuse_screened_poisson_dct(s3.data_ptr(), o3.data_ptr(), f.data_ptr(), n, nx, ny, float(alpha),
+                                             int(precision), _stream_ptr(s3.device)))
+    return f[0] if s.dim() == 2 else f
 
 
 def emfuse_fuse_color(s_rgb: torch.Tensor, o_grey: torch.Tensor, alpha: float, opts: SolveOpts | None = None,

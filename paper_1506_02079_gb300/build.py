@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(PKG, "libemfuse.so")
-SOURCES = ["api.cu", "smooth.cu", "multigrid.cu", "fused_f32.cu", "fused_f64.cu", "runtime.cu"]
+SOURCES = ["api.cu", "smooth.cu", "multigrid.cu", "fused_f32.cu", "fused_f64.cu", "runtime.cu", "dct_solve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -60,7 +60,7 @@ def build(verbose: bool = False, force: bool = False, extra: list[str] | None = 
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra, verbose), srcs))
     tmp = LIB_PATH + ".tmp"
-    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
+    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lcufft"]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)

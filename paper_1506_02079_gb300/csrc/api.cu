@@ -258,6 +258,7 @@ int emfuse_autotune_result(emfuse_tune_entry* out, int max_entries) {
 void emfuse_release_cache(void) {
     cudaDeviceSynchronize();
     release_plans();
+    release_fft_plans();
     trim_library_pools();
 }
 
@@ -323,6 +324,19 @@ int emfuse_screened_poisson(const float* s, const float* o, float* f, int64_t ns
     req.opts = o2;
     req.stats = stats;
     return solve_batch(req, (cudaStream_t)stream);
+}
+
+int emfuse_screened_poisson_dct(const float* s, const float* o, float* f, int64_t nslices, int64_t nx,
+                                int64_t ny, double alpha, int precision, void* stream) {
+    set_error("");
+    if (!s || !o || !f) return einval("emfuse_screened_poisson_dct: null pointer");
+    if (nslices < 1 || nx < 1 || ny < 1 || nx > kMaxSide || ny > kMaxSide)
+        return einval("emfuse_screened_poisson_dct: need nslices >= 1 and sizes in [1, 2^29]");
+    if (f == s || f == o) return einval("emfuse_screened_poisson_dct: f must not alias s or o");
+    if (precision != EMFUSE_PREC_FP32 && precision != EMFUSE_PREC_FP64)
+        return einval("emfuse_screened_poisson_dct: precision must be EMFUSE_PREC_FP32 or EMFUSE_PREC_FP64");
+    EMF_TRY(check_alpha(alpha));
+    return solve_dct_batch(s, o, f, nslices, nx, ny, alpha, precision, (cudaStream_t)stream);
 }
 
 int emfuse_fuse_color(const float* s_rgb, const float* o_grey, float* f_rgb, int64_t nimages, int64_t nx,

@@ -47,6 +47,12 @@ int solve_batch(const SolveRequest& req, cudaStream_t st);
 const std::vector<emfuse_tune_entry>& last_autotune();
 void release_plans();
 
+// ---- direct solve by fast transforms (dct_solve.cu): uniform batch of n slices of ny x nx,
+// precision EMFUSE_PREC_FP32 or EMFUSE_PREC_FP64; FFT plans cached until release_fft_plans()
+int solve_dct_batch(const float* s, const float* o, float* f, int64_t n, int64_t nx, int64_t ny, double alpha,
+                    int precision, cudaStream_t st);
+void release_fft_plans();
+
 // elementwise helpers used by the adjoint (multigrid.cu)
 int apply_laplacian_stack(const float* in, float* out, int64_t nx, int64_t ny, int64_t nz,
                           float scale, cudaStream_t st);

@@ -291,3 +291,23 @@ def test_fuse_color_matches_oracle_and_per_channel_solves(dev):
         for c in range(3):
             one = api.emfuse_screened_poisson(sd[i, c].contiguous(), od[i].contiguous(), 0.01)
             assert torch.equal(f[i, c], one)
+
+
+# ----------------------------------------------------------------------------- direct FFT solve
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 2, 3), (1, 17, 1), (3, 64, 48), (2, 127, 200)])
+@pytest.mark.parametrize("alpha", [1e-3, 0.1])
+def test_fft_solve_matches_oracle(dev, shape, alpha):
+    """The mirror-extension FFT solve is exact up to rounding: FP64 within 1e-4 (the FP32
+    output's own rounding is below 8e-6 at 255), FP32 within the solve bar; and the multigrid
+    at tol 1e-10 agrees with it."""
+    rng = np.random.default_rng(shape[1] * 7 + shape[2])
+    s = rng.uniform(0, 255, size=shape).astype(np.float32)
+    o = np.clip(0.9 * s + rng.normal(0, 10, size=shape), 0, 255).astype(np.float32)
+    sd, od = torch.from_numpy(s).to(dev), torch.from_numpy(o).to(dev)
+    ref = np.stack([O.solve_dct(s[j], o[j], alpha) for j in range(shape[0])])
+    f64 = api.emfuse_screened_poisson_dct(sd, od, alpha, api.PREC_FP64).cpu().numpy()
+    assert maxdiff(f64, ref) <= 1e-4
+    f32 = api.emfuse_screened_poisson_dct(sd, od, alpha, api.PREC_FP32).cpu().numpy()
+    assert maxdiff(f32, ref) <= SOLVE_TOL
+    mg = api.emfuse_screened_poisson(sd, od, alpha, api.default_opts(tol=1e-10)).cpu().numpy()
+    assert maxdiff(mg, f64) <= SOLVE_TOL
