@@ -114,9 +114,10 @@ static int correct_stack_host(const void* in, int dt, float* out, int64_t nx, in
                   std::to_string(ny) + " x " + std::to_string(nx) + " plus halo planes");
         return EMFUSE_ENOMEM;
     }
-    // at least four chunks when the stack allows it, so that copies overlap compute; equal
-    // chunk sizes (but the last) keep the solver's cached plan valid from chunk to chunk
-    cmax = std::min<int64_t>({cmax, 64, std::max<int64_t>(1, (nz + 3) / 4)});
+    // at least two chunks when the stack allows it, so that copies overlap compute (every extra
+    // chunk costs a solve's fixed, latency-bound coarse-level time, so no more than needed);
+    // equal chunk sizes (but the last) keep the solver's cached plan valid from chunk to chunk
+    cmax = std::min<int64_t>({cmax, 64, std::max<int64_t>(1, (nz + 1) / 2)});
     const int64_t nchunks = (nz + cmax - 1) / cmax;
     const int64_t C = (nz + nchunks - 1) / nchunks;
     const int64_t slab_cap = std::min<int64_t>(nz, C + 2 * R);
