@@ -337,8 +337,23 @@ def run_gpu(args):
         for _ in range(ne):
             api.emfuse_correct_stack(I0_h, 1.0, 3.0, args.alpha, opts, out=out_h)
         e2e_s = (time.perf_counter() - t0) / ne
+        # the host link as this run saw it: one whole-stack copy each way on these buffers
+        dev_tmp = torch.empty_like(I0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        dev_tmp.copy_(I0_h, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        h2d_gbs = I0_h.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        e0.record(stream)
+        out_h.copy_(dev_tmp, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        d2h_gbs = out_h.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        del dev_tmp
         e2e = {"value": voxels / e2e_s, "unit": "voxels/s", "h2d_bytes_per_step": I0_h.numel() * 4,
-               "d2h_bytes_per_step": out_h.numel() * 4, "ms_per_step": 1e3 * e2e_s}
+               "d2h_bytes_per_step": out_h.numel() * 4, "ms_per_step": 1e3 * e2e_s,
+               "link_h2d_gbs": h2d_gbs, "link_d2h_gbs": d2h_gbs}
         # plain FP64 GPU solve at the same tolerance
         o64 = api.default_opts(tol=1e-6, precision=api.PREC_FP64)
         api.emfuse_correct_stack(I0, 1.0, 3.0, args.alpha, o64, out=out)

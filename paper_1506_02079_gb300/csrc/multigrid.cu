@@ -490,7 +490,7 @@ struct Solver {
             // chunk); shorter ones only while the level would otherwise leave SMs idle
             // (down to 8 rows on small levels, where a march's latency, not its work, is the cost)
             L.ch = 128;
-            while (L.ch > 8 && want / L.ch < (int64_t)kNumSMs * 16 * 2) L.ch /= 2;
+            while (L.ch > 8 && want / L.ch < (int64_t)kNumSMs * 16) L.ch /= 2;  // about one item per resident warp
             if (k == 0 && rq->opts.tile_rows > 0) L.ch = rq->opts.tile_rows;
             for (const auto& S : L.wsl) {
                 L.item_start.push_back(L.item_start.back() + (int64_t)S.fstrips * ceil_div(S.ny, L.ch));
