@@ -83,7 +83,10 @@ typedef struct {
     float robust_kappa;  /* emfuse_correct_stack only: > 0 smooths with robust averaging
                             across slices at this threshold (see emfuse_smooth_z_robust;
                             the paper uses 2); 0 = plain averaging.  Default 0.            */
-    int reserved[1];     /* must be zero                                                   */
+    int host_pipeline;   /* emfuse_correct_stack with host buffers: 0 = choose (the whole
+                            input and its smoothed copy on the device when they fit, else
+                            slabs with halo planes), 1 = slabs, 2 = whole input (EMFUSE_ENOMEM
+                            if it does not fit).  Default 0.                               */
 } emfuse_solve_opts;
 
 /* Per-slice result of a solve. */
@@ -226,9 +229,12 @@ int emfuse_fuse_color(const float* s_rgb, const float* o_grey, float* f_rgb, int
  *   out       I2, float32, same shape.
  *   in_is_host  0: `in` and `out` are device pointers.
  *               1: `in` and `out` are HOST pointers (page-locked memory is strongly
- *                  recommended); the stack is streamed through the device in z-chunks with
- *                  floor(3 sigma_z) halo planes, copies overlapped with compute on side
- *                  streams, so stacks larger than device memory are supported.
+ *                  recommended); copies overlap compute on side streams.  When the input and
+ *                  its smoothed copy fit on the device, the input is copied whole, smoothed in
+ *                  two z-chunks and solved in chunks whose results are copied back while the
+ *                  next solves; otherwise the stack streams through in z-slabs with
+ *                  floor(3 sigma_z) halo planes, so stacks larger than device memory are
+ *                  supported (opts->host_pipeline chooses explicitly).
  *   stats     NULL or a HOST array of nz entries.
  */
 int emfuse_correct_stack(const void* in, int dt, int in_is_host, float* out, int64_t nx,

@@ -51,7 +51,7 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_vcycles", ctypes.c_int), ("nu_pre", ctypes.c_int),
                 ("nu_post", ctypes.c_int), ("precision", ctypes.c_int), ("fused", ctypes.c_int),
                 ("first_vcycles", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("no_graphs", ctypes.c_int), ("robust_kappa", ctypes.c_float), ("reserved", ctypes.c_int * 1)]
+                ("no_graphs", ctypes.c_int), ("robust_kappa", ctypes.c_float), ("host_pipeline", ctypes.c_int)]
 
 
 class TuneEntry(ctypes.Structure):

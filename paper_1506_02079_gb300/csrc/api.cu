@@ -38,6 +38,7 @@ static int resolve_opts(const emfuse_solve_opts* in, emfuse_solve_opts* out) {
         return einval("opts.tile_rows must be 0 or a power of two in [8, 256]");
     if (out->autotune != 0 && out->autotune != 1) return einval("opts.autotune must be 0 or 1");
     if (out->no_graphs != 0 && out->no_graphs != 1) return einval("opts.no_graphs must be 0 or 1");
+    if (out->host_pipeline < 0 || out->host_pipeline > 2) return einval("opts.host_pipeline must be 0, 1 or 2");
     if (!(out->robust_kappa == 0.f || (out->robust_kappa >= 1.f && std::isfinite(out->robust_kappa))))
         return einval("opts.robust_kappa must be 0 (plain averaging) or finite and >= 1");
     return EMFUSE_OK;
@@ -86,6 +87,105 @@ static int solve_stack(const float* s, const void* o, int dt, float* out, int64_
 }
 
 
+// Host-resident stack whose input and smoothed copy fit on the device together with the
+// solver's chunk workspace.  The smoothing then runs in large z-chunks (two, or one) reading
+// the resident input, so the x/y blur of the floor(3 sigma_z) halo planes is redone only at the
+// one chunk boundary, while the solves run in chunks of C slices sized by memory:
+//   copy-in  (side stream): the input in two pieces, each with an event;
+//   compute  (the caller's stream): smoothing of a z-chunk once the input it reads has arrived,
+//            then the solves of the slices it covers, into output buffer i mod 2;
+//   copy-out (side stream): output buffer i mod 2 to the host.
+static int correct_stack_resident(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                                  float sigma_xy, float sigma_z, double alpha, const emfuse_solve_opts& o2,
+                                  emfuse_slice_stats* stats, cudaStream_t st, int64_t C) {
+    const int64_t R = support_radius(sigma_z);
+    const int64_t plane = nx * ny;
+    const size_t esz = dtype_size(dt);
+    const int64_t ns = nz >= 2 ? 2 : 1;       // smoothing chunks (and input pieces)
+    const int64_t Cs = (nz + ns - 1) / ns;
+    const int64_t nchunks = (nz + C - 1) / C;  // solve chunks
+    DeviceBuffer din, ds, dout[2];
+    EMF_TRY(din.alloc((size_t)(nz * plane) * esz, st));
+    EMF_TRY(ds.alloc((size_t)(nz * plane) * sizeof(float), st));
+    for (int q = 0; q < 2; ++q) EMF_TRY(dout[q].alloc((size_t)(C * plane) * sizeof(float), st));
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_alloc = nullptr, ev_piece[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
+                ev_out[2] = {nullptr, nullptr};
+    int rc_all = EMFUSE_OK;
+    auto cleanup = [&]() {
+        for (int q = 0; q < 2; ++q) {
+            if (ev_piece[q]) cudaEventDestroy(ev_piece[q]);
+            if (ev_comp[q]) cudaEventDestroy(ev_comp[q]);
+            if (ev_out[q]) cudaEventDestroy(ev_out[q]);
+        }
+        if (ev_alloc) cudaEventDestroy(ev_alloc);
+        if (s_in) cudaStreamDestroy(s_in);
+        if (s_out) cudaStreamDestroy(s_out);
+    };
+    auto body = [&]() -> int {
+        EMF_CUDA(cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking));
+        EMF_CUDA(cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking));
+        EMF_CUDA(cudaEventCreateWithFlags(&ev_alloc, cudaEventDisableTiming));
+        for (int q = 0; q < 2; ++q) {
+            EMF_CUDA(cudaEventCreateWithFlags(&ev_piece[q], cudaEventDisableTiming));
+            EMF_CUDA(cudaEventCreateWithFlags(&ev_comp[q], cudaEventDisableTiming));
+            EMF_CUDA(cudaEventCreateWithFlags(&ev_out[q], cudaEventDisableTiming));
+        }
+        EMF_CUDA(cudaEventRecord(ev_alloc, st));
+        EMF_CUDA(cudaStreamWaitEvent(s_in, ev_alloc, 0));
+        EMF_CUDA(cudaStreamWaitEvent(s_out, ev_alloc, 0));
+        for (int64_t k = 0; k < ns; ++k) {
+            const int64_t a = k * Cs, b = std::min(nz, a + Cs);
+            EMF_CUDA(cudaMemcpyAsync(din.as<char>() + (size_t)(a * plane) * esz, (const char*)in + (size_t)(a * plane) * esz,
+                                     (size_t)((b - a) * plane) * esz, cudaMemcpyHostToDevice, s_in));
+            EMF_CUDA(cudaEventRecord(ev_piece[k], s_in));
+        }
+        int64_t smoothed = 0;  // output planes [0, smoothed) are queued for smoothing
+        for (int64_t i = 0; i < nchunks; ++i) {
+            const int q = int(i & 1);
+            const int64_t z0 = i * C, z1 = std::min(nz, z0 + C);
+            while (smoothed < z1) {
+                const int64_t k = smoothed / Cs;
+                const int64_t a = k * Cs, b = std::min(nz, a + Cs);
+                const int64_t need = std::min(nz, b + R);  // input planes [0, need) are read
+                EMF_CUDA(cudaStreamWaitEvent(st, ev_piece[(need - 1) / Cs], 0));
+                EMF_TRY(smooth_stack(din.as<char>(), dt, ds.as<float>() + a * plane, nx, ny, nz, nx, a, b, sigma_xy,
+                                     sigma_z, st, 0, o2.robust_kappa));
+                smoothed = b;
+            }
+            if (i >= 2) EMF_CUDA(cudaStreamWaitEvent(st, ev_out[q], 0));  // dout[q] drained
+            const int rc = solve_stack(ds.as<float>() + z0 * plane, din.as<char>() + (size_t)(z0 * plane) * esz, dt,
+                                       dout[q].as<float>(), nx, ny, z1 - z0, alpha, o2, stats ? stats + z0 : nullptr,
+                                       nullptr, st);
+            if (rc != EMFUSE_OK && rc != EMFUSE_ENOCONV) return rc;
+            if (rc == EMFUSE_ENOCONV) rc_all = rc;
+            EMF_CUDA(cudaEventRecord(ev_comp[q], st));
+            EMF_CUDA(cudaStreamWaitEvent(s_out, ev_comp[q], 0));
+            EMF_CUDA(cudaMemcpyAsync(out + z0 * plane, dout[q].as<float>(), (size_t)((z1 - z0) * plane) * sizeof(float),
+                                     cudaMemcpyDeviceToHost, s_out));
+            EMF_CUDA(cudaEventRecord(ev_out[q], s_out));
+        }
+        for (int q = 0; q < 2; ++q) EMF_CUDA(cudaStreamWaitEvent(st, ev_out[q], 0));
+        EMF_CUDA(cudaStreamWaitEvent(st, ev_piece[ns - 1], 0));
+        return EMFUSE_OK;
+    };
+    const int rc = body();
+    if (rc != EMFUSE_OK) {
+        if (s_in) cudaStreamSynchronize(s_in);
+        if (s_out) cudaStreamSynchronize(s_out);
+        cudaStreamSynchronize(st);
+        cleanup();
+        return rc;
+    }
+    const cudaError_t e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) {
+        set_error(std::string("emfuse_correct_stack: ") + cudaGetErrorString(e));
+        return EMFUSE_ECUDA;
+    }
+    return rc_all;
+}
+
 // Host-resident stack, streamed through the device in z-chunks of C output slices.  Chunk i
 // needs input planes [a_i, b_i) = [z0 - R, z1 + R) clipped to the stack (R = floor(3 sigma_z)),
 // so that smoothing the slab alone gives exactly the stack's slices.  Three streams overlap:
@@ -104,6 +204,9 @@ static int correct_stack_host(const void* in, int dt, float* out, int64_t nx, in
     const size_t esz = dtype_size(dt);
     size_t free_b = 0, total_b = 0;
     EMF_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    // memory this library already holds counts as available: idle pages of its pool, and the
+    // buffers of this stream's cached solver plan, which the chunk solves reuse
+    free_b += library_pool_idle_bytes() + cached_plan_bytes(st, o2.precision);
     // device bytes per output slice of a chunk: two slabs of input, s, two output buffers, and
     // the solver's pyramids (about 16 B/px) and FP64 iterates (16 B/px)
     const double per_slice = (double)plane * (2.0 * esz + 4.0 + 8.0 + 32.0);
@@ -120,6 +223,15 @@ static int correct_stack_host(const void* in, int dt, float* out, int64_t nx, in
     cmax = std::min<int64_t>({cmax, 64, std::max<int64_t>(1, (nz + 1) / 2)});
     const int64_t nchunks = (nz + cmax - 1) / cmax;
     const int64_t C = (nz + nchunks - 1) / nchunks;
+    // the whole input and its smoothed copy on the device as well: smooth in large chunks
+    const double resident = (double)(nz * plane) * (esz + 4.0) + (double)(C * plane) * (8.0 + 32.0);
+    const bool fits = resident <= 0.7 * (double)free_b;
+    if (o2.host_pipeline == 2 && !fits) {
+        set_error("emfuse_correct_stack: the whole input and its smoothed copy do not fit on the device");
+        return EMFUSE_ENOMEM;
+    }
+    if (o2.host_pipeline == 2 || (o2.host_pipeline == 0 && fits))
+        return correct_stack_resident(in, dt, out, nx, ny, nz, sigma_xy, sigma_z, alpha, o2, stats, st, C);
     const int64_t slab_cap = std::min<int64_t>(nz, C + 2 * R);
 
     DeviceBuffer din[2], dout[2], ds;

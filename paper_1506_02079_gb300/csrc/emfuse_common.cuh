@@ -78,6 +78,8 @@ void add_launches(int64_t n);
 // pool cannot be created (the device's default pool is used then).
 cudaMemPool_t library_pool();
 void trim_library_pools();
+// bytes the pool of the current device holds without any allocation using them
+size_t library_pool_idle_bytes();
 
 // Stream-ordered allocation from the library's pool; freed stream-ordered at scope exit.
 class DeviceBuffer {

@@ -46,6 +46,9 @@ int solve_batch(const SolveRequest& req, cudaStream_t st);
 // candidates timed by the last autotuning solve on this host thread, the chosen one first
 const std::vector<emfuse_tune_entry>& last_autotune();
 void release_plans();
+// bytes of the pyramids and FP64 iterates held by the cached plan of (current device, stream,
+// precision): a later solve on that stream reuses them
+size_t cached_plan_bytes(cudaStream_t st, int precision);
 
 // ---- direct solve by fast transforms (dct_solve.cu): uniform batch of n slices of ny x nx,
 // precision EMFUSE_PREC_FP32 or EMFUSE_PREC_FP64; FFT plans cached until release_fft_plans()

@@ -858,6 +858,7 @@ struct PlanEntry {
     int prec;
     std::shared_ptr<void> solver;
     std::shared_ptr<std::mutex> mu;
+    size_t (*bytes)(const void*);  // large buffers held by the solver
 };
 std::mutex g_plans_mu;
 // heap-allocated and never destroyed: no CUDA call from a static destructor at process exit
@@ -882,7 +883,10 @@ int run_precision(const SolveRequest& req, cudaStream_t st) {
             if (g_plans.size() >= kMaxPlans) g_plans.erase(g_plans.begin());
             solver = std::make_shared<Solver<TF, TV>>(st);
             mu = std::make_shared<std::mutex>();
-            g_plans.push_back(PlanEntry{dev, st, prec, solver, mu});
+            g_plans.push_back(PlanEntry{dev, st, prec, solver, mu, [](const void* p) -> size_t {
+                const auto* s = static_cast<const Solver<TF, TV>*>(p);
+                return s->ws_levels.bytes() + s->ws_f.bytes();
+            }});
         }
     }
     std::lock_guard<std::mutex> lk(*mu);
@@ -1061,6 +1065,16 @@ int solve_batch(const SolveRequest& req, cudaStream_t st) {
 }
 
 const std::vector<emfuse_tune_entry>& last_autotune() { return t_last_tune; }
+
+size_t cached_plan_bytes(cudaStream_t st, int precision) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    size_t b = 0;
+    for (auto& e : g_plans)
+        if (e.dev == dev && e.st == st && e.prec == precision && e.bytes) b += e.bytes(e.solver.get());
+    return b;
+}
 
 void release_plans() {
     std::lock_guard<std::mutex> lk(g_plans_mu);

@@ -155,6 +155,18 @@ cudaMemPool_t library_pool() {
     return g_pools[dev];
 }
 
+size_t library_pool_idle_bytes() {
+    cudaMemPool_t p = library_pool();
+    if (!p) return 0;
+    uint64_t reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(p, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+        cudaMemPoolGetAttribute(p, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return reserved > used ? (size_t)(reserved - used) : 0;
+}
+
 void trim_library_pools() {
     std::lock_guard<std::mutex> lk(g_pool_mu);
     for (int d = 0; d < 64; ++d)

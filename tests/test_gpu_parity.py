@@ -178,14 +178,17 @@ def test_backward_matches_oracle(dev):
     assert s_np.shape == (nz, ny, nx)
 
 
-@pytest.mark.parametrize("nz,dtype", [(7, torch.uint8), (13, torch.float32), (2, torch.float32), (40, torch.uint8)])
-def test_streamed_host_path_equals_device_path(dev, nz, dtype):
-    """The host-resident path (z-chunks with floor(3 sigma_z) halo planes, copies on side
-    streams) must give exactly the device-resident result: every chunk's slab holds all taps
-    of its output planes, and the batched solve does not depend on how slices are grouped."""
+@pytest.mark.parametrize("pipeline", [1, 2])
+@pytest.mark.parametrize("nz,dtype", [(7, torch.uint8), (13, torch.float32), (2, torch.float32), (40, torch.uint8),
+                                      (1, torch.float32)])
+def test_streamed_host_path_equals_device_path(dev, nz, dtype, pipeline):
+    """Both host pipelines (1: z-slabs with floor(3 sigma_z) halo planes; 2: whole input on the
+    device, smoothed in two z-chunks) must give exactly the device-resident result: every
+    smoothing reads all taps of its output planes, and the batched solve does not depend on how
+    slices are grouped."""
     I0 = make_stack(nz, 72, 100, seed=17, out_dtype=dtype)
     ref = api.emfuse_correct_stack(I0.to(dev), 1.0, 3.0, 0.01)
-    got = api.emfuse_correct_stack(I0.pin_memory(), 1.0, 3.0, 0.01)
+    got = api.emfuse_correct_stack(I0.pin_memory(), 1.0, 3.0, 0.01, api.default_opts(host_pipeline=pipeline))
     assert got.device.type == "cpu"
     assert torch.equal(got, ref.cpu())
 
