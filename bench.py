@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--nz", type=int, default=NZ, help="slices (smaller stacks for profiling only)")
     p.add_argument("--paper-scale", type=int, default=0, metavar="NZ",
                    help="instead: stream NZ paper-scale slices (21504 x 26624 uint8) from pinned host memory")
+    p.add_argument("--host-pipeline", type=int, default=0, choices=[0, 1, 2],
+                   help="host-buffer schedule of --paper-scale: 0 chosen by memory, 1 slabs, 2 whole input resident")
     return p.parse_args()
 
 
@@ -234,6 +236,7 @@ def run_paper_scale(args):
     out = torch.empty((nz, PAPER_NY, PAPER_NX), dtype=torch.float32, pin_memory=True)
     t_gen = time.perf_counter() - t0
     opts = api.default_opts(tol=1e-6)
+    opts.host_pipeline = args.host_pipeline
     step = lambda: api.emfuse_correct_stack(I0, 1.0, 3.0, args.alpha, opts, out=out, return_stats=True)
     for _ in range(max(1, args.warmup)):
         step()
@@ -247,6 +250,20 @@ def run_paper_scale(args):
         secs = (time.perf_counter() - t0) / args.steps
     launches = api.lib().emfuse_kernel_launches() - launches0
     prof = profile_steps(step, 1)
+    # the host link on these buffers: one whole copy each way
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dtmp = torch.empty((nz, PAPER_NY, PAPER_NX), dtype=torch.float32, device=dev)
+    din = dtmp.view(torch.uint8).view(-1)[: I0.numel()].view(I0.shape)
+    link_h2d, link_d2h = [], []
+    for _ in range(3):
+        e0.record(); din.copy_(I0, non_blocking=True); e1.record()
+        torch.cuda.synchronize()
+        link_h2d.append(round(I0.numel() / (e0.elapsed_time(e1) * 1e-3) / 1e9, 1))
+        e0.record(); out.copy_(dtmp, non_blocking=True); e1.record()
+        torch.cuda.synchronize()
+        link_d2h.append(round(out.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9, 1))
+    del dtmp, din
+    torch.cuda.empty_cache()
     # a property that holds at any size: the DCT mode 0 of Eq. (1) has gain 1, so every
     # corrected slice keeps the mean of its smoothed slice (checked on the middle slice)
     j = nz // 2
@@ -264,9 +281,11 @@ def run_paper_scale(args):
             "data": "synthetic (mirror-tiled generator slices)",
             "config": {"workload": f"{nz} slices x {PAPER_NY} x {PAPER_NX} uint8 from pinned host, sigma_xy=1, "
                                    "sigma_z=3, FP32 multigrid + FP64 defect correction to rel. residual 1e-6",
+                       "host_pipeline": ["auto", "slabs", "resident"][args.host_pipeline],
                        "alpha": args.alpha, "nz": nz, "ny": PAPER_NY, "nx": PAPER_NX, "seed": PAPER_SEED},
             "e2e": {"value": vox / secs, "unit": "voxels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "link_gbs": (h2d + d2h) / secs / 1e9, "kernel_ms_per_step": kernel_ms,
+            "link_gbs": (h2d + d2h) / secs / 1e9, "link_h2d_gbs_whole_copy": link_h2d, "link_d2h_gbs_whole_copy": link_d2h,
+            "kernel_ms_per_step": kernel_ms,
             "gpu_launches": int(launches // max(args.steps, 1)) * args.steps,
             "vcycles": max(s["vcycles"] for s in stats), "max_rel_residual": max(s["rel_residual"] for s in stats),
             "clocks": clk.summary(), "input_generation_s": t_gen,

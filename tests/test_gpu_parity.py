@@ -314,3 +314,37 @@ def test_fft_solve_matches_oracle(dev, shape, alpha):
     assert maxdiff(f32, ref) <= SOLVE_TOL
     mg = api.emfuse_screened_poisson(sd, od, alpha, api.default_opts(tol=1e-10)).cpu().numpy()
     assert maxdiff(mg, f64) <= SOLVE_TOL
+
+
+# ----------------------------------------------------------------------------- stored exact solutions
+def _eq1_exact_cases():
+    import os
+    from fractions import Fraction
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "eq1_exact_small.txt")
+    cases, cur = [], None
+    for line in open(path):
+        tok = line.split()
+        if not tok or tok[0].startswith("#"):
+            continue
+        if tok[0] == "case":
+            cur = {"name": tok[1], "ny": int(tok[2]), "nx": int(tok[3]), "alpha": Fraction(tok[4])}
+            cases.append(cur)
+        else:
+            cur[tok[0]] = np.array([float(Fraction(v)) for v in tok[1:]])
+    return cases
+
+
+@pytest.mark.parametrize("case", _eq1_exact_cases(), ids=lambda c: c["name"])
+def test_solves_match_stored_exact_solutions(dev, case):
+    """Multigrid (mixed precision, tol 1e-10) and FFT (FP64) solves against the exact rational
+    solutions of tests/golden/eq1_exact_small.txt (alpha a power of two or an integer, inputs
+    integers: the GPU sees exactly the stored problem).  Bar: 1e-6 * 255, the FP32 output's
+    rounding plus the residual tolerance amplified by kappa(A) <= 3.3e4."""
+    ny, nx, a = case["ny"], case["nx"], float(case["alpha"])
+    s = torch.from_numpy(case["s"].reshape(ny, nx)).float().to(dev)
+    o = torch.from_numpy(case["o"].reshape(ny, nx)).float().to(dev)
+    exact = case["f"].reshape(ny, nx)
+    mg = api.emfuse_screened_poisson(s, o, a, api.default_opts(tol=1e-10)).cpu().numpy()
+    assert maxdiff(mg, exact) <= 1e-6 * 255.0
+    fft = api.emfuse_screened_poisson_dct(s[None], o[None], a, api.PREC_FP64)[0].cpu().numpy()
+    assert maxdiff(fft, exact) <= 1e-6 * 255.0

@@ -1,7 +1,8 @@
 """Pins of the CPU FP64 oracle against things other than itself.
 
 The paper prints no worked numeric example, so each oracle function is pinned by
-brute force on tiny inputs, by explicit matrices built from first principles, by closed
+brute force on tiny inputs (among them the exact rational solutions of Eq. (1) stored in
+tests/golden/eq1_exact_small.txt), by explicit matrices built from first principles, by closed
 forms and limits stated in Sec. 3, and by finite differences.  Each pin is chosen so that a
 plausible slip (a dropped term, a wrong sign, swapped W/H, a missing renormalisation)
 fails at least one test.
@@ -391,3 +392,56 @@ def test_fuse_color_closed_forms():
                     A[p, p] += 1; A[q, q] += 1; A[p, q] -= 1; A[q, p] -= 1
     diff = alpha * np.linalg.solve(A, (s[0] - s[2]).ravel()).reshape(ny, nx)
     np.testing.assert_allclose(f[0] - f[2], diff, rtol=0, atol=1e-8)
+
+
+# ----------------------------------------------------------------------------- stored exact solutions
+def load_eq1_exact():
+    """Cases of tests/golden/eq1_exact_small.txt: (name, alpha, s, o, f) with f exact Fractions."""
+    import os
+    from fractions import Fraction
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "eq1_exact_small.txt")
+    cases, cur = [], None
+    for line in open(path):
+        tok = line.split()
+        if not tok or tok[0].startswith("#"):
+            continue
+        if tok[0] == "case":
+            cur = {"name": tok[1], "ny": int(tok[2]), "nx": int(tok[3]), "alpha": Fraction(tok[4])}
+            cases.append(cur)
+        else:
+            cur[tok[0]] = [Fraction(v) for v in tok[1:]]
+    return cases
+
+
+EQ1_CASES = load_eq1_exact()
+
+
+@pytest.mark.parametrize("case", EQ1_CASES, ids=lambda c: c["name"])
+def test_stored_exact_solution_satisfies_eq1_exactly(case):
+    """The stored f solves Eq. (1) with zero residual in rational arithmetic (rows assembled
+    here from the 4-neighbour definition), and keeps the sum of s exactly (summing the rows of
+    Eq. (1) cancels every Laplacian term)."""
+    ny, nx, a = case["ny"], case["nx"], case["alpha"]
+    s, o, f = case["s"], case["o"], case["f"]
+    assert len(s) == len(o) == len(f) == ny * nx
+    for y in range(ny):
+        for x in range(nx):
+            p = y * nx + x
+            lhs, rhs = a * f[p], a * s[p]
+            for yq, xq in ((y - 1, x), (y + 1, x), (y, x - 1), (y, x + 1)):
+                if 0 <= yq < ny and 0 <= xq < nx:
+                    q = yq * nx + xq
+                    lhs += f[p] - f[q]
+                    rhs += o[p] - o[q]
+            assert lhs == rhs
+    assert sum(f) == sum(s)
+
+
+@pytest.mark.parametrize("case", EQ1_CASES, ids=lambda c: c["name"])
+def test_solve_dct_matches_stored_exact_solution(case):
+    """The DCT solve reaches the exact rational solution up to FP64 rounding amplified by at most
+    kappa(A) = 1 + 8 / alpha (<= 3.3e4 here): within 1e-8 on values of up to 255."""
+    ny, nx, a = case["ny"], case["nx"], float(case["alpha"])
+    grid = lambda v: np.array([float(t) for t in v]).reshape(ny, nx)
+    f = O.solve_dct(grid(case["s"]), grid(case["o"]), a)
+    assert np.max(np.abs(f - grid(case["f"]))) <= 1e-8
