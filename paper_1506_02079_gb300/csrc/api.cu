@@ -91,7 +91,8 @@ static int solve_stack(const float* s, const void* o, int dt, float* out, int64_
 // solver's chunk workspace.  The smoothing then runs in large z-chunks (two, or one) reading
 // the resident input, so the x/y blur of the floor(3 sigma_z) halo planes is redone only at the
 // one chunk boundary, while the solves run in chunks of C slices sized by memory:
-//   copy-in  (side stream): the input in two pieces, each with an event;
+//   copy-in  (side stream): the input in pieces, piece k ending at the last plane smoothing
+//            chunk k reads, each with an event (the first chunk starts before the rest arrives);
 //   compute  (the caller's stream): smoothing of a z-chunk once the input it reads has arrived,
 //            then the solves of the slices it covers, into output buffer i mod 2;
 //   copy-out (side stream): output buffer i mod 2 to the host.
@@ -134,10 +135,13 @@ static int correct_stack_resident(const void* in, int dt, float* out, int64_t nx
         EMF_CUDA(cudaEventRecord(ev_alloc, st));
         EMF_CUDA(cudaStreamWaitEvent(s_in, ev_alloc, 0));
         EMF_CUDA(cudaStreamWaitEvent(s_out, ev_alloc, 0));
-        for (int64_t k = 0; k < ns; ++k) {
-            const int64_t a = k * Cs, b = std::min(nz, a + Cs);
-            EMF_CUDA(cudaMemcpyAsync(din.as<char>() + (size_t)(a * plane) * esz, (const char*)in + (size_t)(a * plane) * esz,
-                                     (size_t)((b - a) * plane) * esz, cudaMemcpyHostToDevice, s_in));
+        for (int64_t k = 0, have = 0; k < ns; ++k) {
+            const int64_t need = std::min(nz, std::min(nz, (k + 1) * Cs) + R);  // planes [0, need) read
+            if (need > have)
+                EMF_CUDA(cudaMemcpyAsync(din.as<char>() + (size_t)(have * plane) * esz,
+                                         (const char*)in + (size_t)(have * plane) * esz,
+                                         (size_t)((need - have) * plane) * esz, cudaMemcpyHostToDevice, s_in));
+            have = std::max(have, need);
             EMF_CUDA(cudaEventRecord(ev_piece[k], s_in));
         }
         int64_t smoothed = 0;  // output planes [0, smoothed) are queued for smoothing
@@ -147,8 +151,7 @@ static int correct_stack_resident(const void* in, int dt, float* out, int64_t nx
             while (smoothed < z1) {
                 const int64_t k = smoothed / Cs;
                 const int64_t a = k * Cs, b = std::min(nz, a + Cs);
-                const int64_t need = std::min(nz, b + R);  // input planes [0, need) are read
-                EMF_CUDA(cudaStreamWaitEvent(st, ev_piece[(need - 1) / Cs], 0));
+                EMF_CUDA(cudaStreamWaitEvent(st, ev_piece[k], 0));  // input planes [0, b + R) arrived
                 EMF_TRY(smooth_stack(din.as<char>(), dt, ds.as<float>() + a * plane, nx, ny, nz, nx, a, b, sigma_xy,
                                      sigma_z, st, 0, o2.robust_kappa));
                 smoothed = b;
