@@ -19,6 +19,9 @@ What it computes (every function cites the passage it follows):
 * ``correct_stack`` -- both phases.
 * ``fuse_color``    -- the colour / monochrome fusion example of Sec. 3: one solve per colour
   channel with the grey image as the gradient constraint.
+* ``gradient_domain_smooth`` -- phase 1 as the 3-D gradient-domain problem of the earlier
+  method (Sec. 3 "Alternate Solutions": target gradients with the z-components zeroed),
+  solved exactly by the 3-D DCT.
 * ``backward_*``    -- the adjoint of both phases (gradients w.r.t. s, o, alpha, I0, sigma_z).
 
 Readings of points the paper leaves open:
@@ -48,6 +51,7 @@ __all__ = [
     "gaussian_taps", "smooth_axis", "smooth_stack", "robust_smooth_stack", "robust_margin",
     "smooth_transpose", "dsmooth_dsigma_z",
     "laplacian", "screened_rhs", "apply_A", "neumann_eigenvalues", "solve_dct", "fuse_color", "apply_Ainv",
+    "gradient_domain_smooth",
     "relative_residual", "correct_stack", "backward_slice", "backward_stack",
 ]
 
@@ -290,6 +294,30 @@ def fuse_color(s_rgb: np.ndarray, o_grey: np.ndarray, alpha: float) -> np.ndarra
     s_rgb: [3][ny][nx], o_grey: [ny][nx]."""
     s_rgb = np.asarray(s_rgb, dtype=np.float64)
     return np.stack([solve_dct(s_rgb[c], o_grey, alpha) for c in range(s_rgb.shape[0])])
+
+
+def gradient_domain_smooth(I0: np.ndarray, alpha: float) -> np.ndarray:
+    """Phase 1 as the 3-D gradient-domain problem of the earlier method (Sec. 3 "Alternate
+    Solutions": the target gradient field is the input's gradient with its z-components set to
+    zero).  With the same screening as Eq. (1), the smoothed stack minimises
+
+        alpha sum_p (f_p - I0_p)^2 + sum_{x, y edges pq} ((f_p - f_q) - (I0_p - I0_q))^2
+                                   + sum_{z edges pq} (f_p - f_q)^2
+
+    over the 6-neighbour graph of the stack (Neumann boundaries), i.e.
+    (alpha I + L_xy + L_z) f = alpha I0 + L_xy I0.  The 3-D Neumann graph Laplacian is diagonal
+    in the orthonormal 3-D DCT-II basis with eigenvalues lam_z + lam_y + lam_x, so
+    f_hat = (alpha + lam_xy) / (alpha + lam_xy + lam_z) * I0_hat: a z-frequency is damped
+    the more, the lower its in-plane frequency (the anisotropic diffusion of that method).
+    I0: [z][y][x]."""
+    if not alpha > 0:
+        raise ValueError("alpha must be > 0")
+    I0 = np.asarray(I0, dtype=np.float64)
+    nz, ny, nx = I0.shape
+    lam_z = neumann_eigenvalues(nz)[:, None, None]
+    lam_xy = _lambda_grid(ny, nx)[None, :, :]
+    h = sfft.dctn(I0, type=2, norm="ortho", workers=-1)
+    return sfft.idctn(h * (alpha + lam_xy) / (alpha + lam_xy + lam_z), type=2, norm="ortho", workers=-1)
 
 
 def apply_Ainv(rhs: np.ndarray, alpha: float) -> np.ndarray:

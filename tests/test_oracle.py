@@ -445,3 +445,65 @@ def test_solve_dct_matches_stored_exact_solution(case):
     grid = lambda v: np.array([float(t) for t in v]).reshape(ny, nx)
     f = O.solve_dct(grid(case["s"]), grid(case["o"]), a)
     assert np.max(np.abs(f - grid(case["f"]))) <= 1e-8
+
+
+# ----------------------------------------------------------------------------- 3-D gradient-domain smoothing
+def gd_energy_minimiser(I0, alpha):
+    """Brute force for the gradient-domain smoothing: the energy alpha sum (f - I0)^2 +
+    sum over x/y edges ((f_p - f_q) - (I0_p - I0_q))^2 + sum over z edges (f_p - f_q)^2 as a
+    dense least-squares problem (no normal equations, no transform)."""
+    nz, ny, nx = I0.shape
+    n = I0.size
+    idx = lambda z, y, x: (z * ny + y) * nx + x
+    rows, rhs = [], []
+    sa = math.sqrt(alpha)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                r = np.zeros(n); r[idx(z, y, x)] = sa
+                rows.append(r); rhs.append(sa * I0[z, y, x])
+                for dz, dy, dx in ((0, 0, 1), (0, 1, 0), (1, 0, 0)):
+                    z2, y2, x2 = z + dz, y + dy, x + dx
+                    if z2 < nz and y2 < ny and x2 < nx:
+                        r = np.zeros(n); r[idx(z, y, x)] = 1.0; r[idx(z2, y2, x2)] = -1.0
+                        rows.append(r)
+                        rhs.append(0.0 if dz else I0[z, y, x] - I0[z2, y2, x2])
+    f, *_ = np.linalg.lstsq(np.array(rows), np.array(rhs), rcond=None)
+    return f.reshape(nz, ny, nx)
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (4, 1, 6), (5, 3, 1), (1, 3, 4), (2, 2, 2)])
+@pytest.mark.parametrize("alpha", [1e-3, 0.3, 4.0])
+def test_gradient_domain_smooth_equals_energy_minimiser(shape, alpha):
+    I0 = RNG.uniform(0, 255, size=shape)
+    assert np.allclose(O.gradient_domain_smooth(I0, alpha), gd_energy_minimiser(I0, alpha), atol=1e-7, rtol=0)
+
+
+def test_gradient_domain_smooth_removes_slice_offsets_by_a_1d_screened_solve():
+    """I0 = B(x, y) + c_z: the in-plane part carries no z-gradient and stays; the offsets
+    solve the 1-D z problem (alpha I + L_z) g = alpha c, written here as a dense tridiagonal
+    matrix (closed form, independent of the DCT)."""
+    nz, ny, nx, alpha = 7, 5, 6, 0.05
+    B = RNG.uniform(0, 200, size=(ny, nx))
+    c = RNG.uniform(-30, 30, size=nz)
+    I0 = B[None] + c[:, None, None]
+    Lz = np.zeros((nz, nz))
+    for z in range(nz - 1):
+        Lz[z, z] += 1; Lz[z + 1, z + 1] += 1; Lz[z, z + 1] -= 1; Lz[z + 1, z] -= 1
+    g = np.linalg.solve(alpha * np.eye(nz) + Lz, alpha * c)
+    assert np.allclose(O.gradient_domain_smooth(I0, alpha), B[None] + g[:, None, None], atol=1e-9, rtol=0)
+
+
+def test_gradient_domain_smooth_invariants():
+    I0 = RNG.uniform(0, 255, size=(6, 9, 8))
+    f = O.gradient_domain_smooth(I0, 0.01)
+    # summing the normal equations cancels every Laplacian term: the total is kept
+    assert abs(f.sum() - I0.sum()) <= 1e-8 * abs(I0.sum())
+    # a stack constant in z is a fixed point (no z-gradient to remove); one slice is unchanged
+    flat = np.repeat(I0[:1], 6, axis=0)
+    assert np.allclose(O.gradient_domain_smooth(flat, 0.01), flat, atol=1e-9, rtol=0)
+    assert np.allclose(O.gradient_domain_smooth(I0[:1], 0.01), I0[:1], atol=1e-9, rtol=0)
+    # alpha -> infinity: the value constraint wins
+    assert np.allclose(O.gradient_domain_smooth(I0, 1e12), I0, atol=1e-6, rtol=0)
+    # inter-slice differences shrink
+    assert np.abs(np.diff(f, axis=0)).mean() < np.abs(np.diff(I0, axis=0)).mean()
