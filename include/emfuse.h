@@ -208,6 +208,27 @@ int emfuse_screened_poisson_dct(const float* s, const float* o, float* f, int64_
                                 int64_t ny, double alpha, int precision, void* stream);
 
 /*
+ * Phase 1 as the 3-D gradient-domain problem of the earlier method (Sec. 3 "Alternate
+ * Solutions": the target gradient field is the input's gradient with its z-components set to
+ * zero), with the screening of Eq. (1):
+ *     out = argmin_f  alpha |f - in|^2 + |grad_xy f - grad_xy in|^2 + |d_z f|^2
+ * on the 6-neighbour graph of the stack with Neumann boundaries, i.e.
+ * (alpha I + L_xy + L_z) out = alpha in + L_xy in.  Solved exactly: out = in + d, with d from
+ * one 3-D real-to-complex FFT of the stack's mirror extension to 2nz x 2ny x 2nx, a scaling
+ * by -lambda_z / (alpha + lambda), and the inverse FFT (cuFFT).
+ *   in          device, nz x ny x nx dense [z][y][x], uint8 (dt = EMFUSE_U8) or float32.
+ *   out         device float32, same shape; must not alias in.
+ *   alpha       > 0 (finite).
+ *   precision   EMFUSE_PREC_FP32 or EMFUSE_PREC_FP64 (transforms and scaling in that type).
+ * Temporaries: the extended stack and its half spectrum (8 and about 8 times the stack's
+ * cells, in the chosen type) plus cuFFT's work area, from the library's pool; EMFUSE_ENOMEM
+ * when they do not fit.  The cuFFT plan is cached per shape and precision until
+ * emfuse_release_cache().  Asynchronous on `stream`.
+ */
+int emfuse_smooth_gradient_domain(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                                  double alpha, int precision, void* stream);
+
+/*
  * Fusion of low-frequency colour images with high-frequency monochrome ones (Sec. 3, the
  * colour example): for every image i and colour channel c, Eq. (1) with the colour channel as
  * the value constraint and the grey image as the gradient constraint,

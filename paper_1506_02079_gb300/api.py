@@ -20,7 +20,8 @@ __all__ = [
     "EmfuseError", "EmfuseUnavailable", "SolveOpts", "SliceStats", "lib", "library_path",
     "default_opts", "emfuse_smooth_z", "emfuse_smooth_z_robust", "emfuse_smooth_z_noalloc",
     "emfuse_screened_poisson",
-    "emfuse_autotune_result", "TuneEntry", "emfuse_fuse_color", "emfuse_screened_poisson_dct", "emfuse_correct_stack",
+    "emfuse_autotune_result", "TuneEntry", "emfuse_fuse_color", "emfuse_screened_poisson_dct",
+    "emfuse_smooth_gradient_domain", "emfuse_correct_stack",
     "emfuse_backward", "emfuse_version", "emfuse_release_cache", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
     "PREC_FP64", "EXPORTED_SYMBOLS",
 ]
@@ -34,7 +35,7 @@ EXPORTED_SYMBOLS = ["emfuse_default_opts", "emfuse_smooth_z", "emfuse_screened_p
                     "emfuse_version", "emfuse_kernel_launches", "emfuse_profile_begin",
                     "emfuse_profile_end", "emfuse_release_cache", "emfuse_smooth_z_noalloc",
                     "emfuse_selftest_fpconv", "emfuse_autotune_result", "emfuse_smooth_z_robust",
-                    "emfuse_fuse_color", "emfuse_screened_poisson_dct"]
+                    "emfuse_fuse_color", "emfuse_screened_poisson_dct", "emfuse_smooth_gradient_domain"]
 
 
 class EmfuseError(RuntimeError):
@@ -89,6 +90,7 @@ def lib() -> ctypes.CDLL:
             L.emfuse_smooth_z_robust.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, fl, vp]
             L.emfuse_fuse_color.argtypes = [vp, vp, vp, i64, i64, i64, db, ctypes.POINTER(SolveOpts), vp, vp]
             L.emfuse_screened_poisson_dct.argtypes = [vp, vp, vp, i64, i64, i64, db, ci, vp]
+            L.emfuse_smooth_gradient_domain.argtypes = [vp, ci, vp, i64, i64, i64, db, ci, vp]
             L.emfuse_smooth_z_noalloc.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
             L.emfuse_selftest_fpconv.argtypes = [vp, vp]
             L.emfuse_autotune_result.argtypes = [vp, ci]
@@ -102,7 +104,7 @@ def lib() -> ctypes.CDLL:
                                           vp, vp, ctypes.POINTER(SolveOpts), vp]
             for name in ("emfuse_smooth_z", "emfuse_screened_poisson", "emfuse_correct_stack",
                          "emfuse_backward", "emfuse_smooth_z_noalloc", "emfuse_smooth_z_robust",
-                         "emfuse_fuse_color", "emfuse_screened_poisson_dct"):
+                         "emfuse_fuse_color", "emfuse_screened_poisson_dct", "emfuse_smooth_gradient_domain"):
                 getattr(L, name).restype = ci
             L.emfuse_last_error.restype = ctypes.c_char_p
             L.emfuse_last_error.argtypes = []
@@ -294,6 +296,24 @@ def emfuse_screened_poisson_dct(s: torch.Tensor, o: torch.Tensor, alpha: float, 
     _check(lib().emfuse_screened_poisson_dct(s3.data_ptr(), o3.data_ptr(), f.data_ptr(), n, nx, ny, float(alpha),
                                              int(precision), _stream_ptr(s3.device)))
     return f[0] if s.dim() == 2 else f
+
+
+def emfuse_smooth_gradient_domain(stack: torch.Tensor, alpha: float, precision: int = PREC_FP32,
+                                  out: torch.Tensor | None = None) -> torch.Tensor:
+    """Phase 1 as the 3-D gradient-domain problem of the earlier method (Sec. 3 "Alternate
+    Solutions": target gradients with their z-components zeroed, screened by alpha), solved
+    exactly by one 3-D FFT of the mirror-extended stack.  ``stack`` CUDA uint8 or float32
+    [z][y][x]; precision PREC_FP32 / PREC_FP64.  Returns float32 of the same shape."""
+    _require_cuda(stack)
+    if stack.dim() != 3 or not stack.is_contiguous():
+        raise ValueError("stack must be a contiguous [z][y][x] tensor")
+    nz, ny, nx = stack.shape
+    if out is None:
+        out = torch.empty((nz, ny, nx), device=stack.device, dtype=torch.float32)
+    _require_cuda(out)
+    _check(lib().emfuse_smooth_gradient_domain(stack.data_ptr(), _dtype_code(stack), out.data_ptr(), nx, ny, nz,
+                                               float(alpha), int(precision), _stream_ptr(stack.device)))
+    return out
 
 
 def emfuse_fuse_color(s_rgb: torch.Tensor, o_grey: torch.Tensor, alpha: float, opts: SolveOpts | None = None,

@@ -455,6 +455,22 @@ int emfuse_screened_poisson_dct(const float* s, const float* o, float* f, int64_
     return solve_dct_batch(s, o, f, nslices, nx, ny, alpha, precision, (cudaStream_t)stream);
 }
 
+int emfuse_smooth_gradient_domain(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                                  double alpha, int precision, void* stream) {
+    set_error("");
+    if (!in || !out) return einval("emfuse_smooth_gradient_domain: null pointer");
+    if (dt != EMFUSE_U8 && dt != EMFUSE_F32) return einval("emfuse_smooth_gradient_domain: dt must be EMFUSE_U8 or EMFUSE_F32");
+    if (nx < 1 || ny < 1 || nz < 1 || nx > kMaxSide || ny > kMaxSide || nz > kMaxSide)
+        return einval("emfuse_smooth_gradient_domain: need sizes in [1, 2^29]");
+    if ((double)nx * (double)ny * (double)nz > 1099511627776.0)
+        return einval("emfuse_smooth_gradient_domain: more than 2^40 cells");
+    if ((const void*)out == in) return einval("emfuse_smooth_gradient_domain: out must not alias in");
+    if (precision != EMFUSE_PREC_FP32 && precision != EMFUSE_PREC_FP64)
+        return einval("emfuse_smooth_gradient_domain: precision must be EMFUSE_PREC_FP32 or EMFUSE_PREC_FP64");
+    EMF_TRY(check_alpha(alpha));
+    return smooth_gradient_domain(in, dt, out, nx, ny, nz, alpha, precision, (cudaStream_t)stream);
+}
+
 int emfuse_fuse_color(const float* s_rgb, const float* o_grey, float* f_rgb, int64_t nimages, int64_t nx,
                       int64_t ny, double alpha, const emfuse_solve_opts* opts, emfuse_slice_stats* stats,
                       void* stream) {

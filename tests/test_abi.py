@@ -67,3 +67,11 @@ def test_host_side_calls_without_gpu(libpath):
     bad = api.default_opts(nu_pre=0, nu_post=0)
     assert L.emfuse_screened_poisson(fake, ctypes.c_void_p(32), ctypes.c_void_p(48), 1, one, one,
                                      off, 1e-3, ctypes.byref(bad), None, None) == 1
+    # 3-D gradient-domain smoothing: aliasing, precision, alpha and size checks
+    assert L.emfuse_smooth_gradient_domain(fake, 1, fake, 4, 4, 4, 1e-3, api.PREC_FP32, None) == 1
+    assert b"alias" in L.emfuse_last_error()
+    assert L.emfuse_smooth_gradient_domain(fake, 1, ctypes.c_void_p(32), 4, 4, 4, 1e-3, api.PREC_MIXED, None) == 1
+    assert L.emfuse_smooth_gradient_domain(fake, 1, ctypes.c_void_p(32), 4, 4, 4, 0.0, api.PREC_FP32, None) == 1
+    assert L.emfuse_smooth_gradient_domain(fake, 1, ctypes.c_void_p(32), 1 << 20, 1 << 20, 4, 1e-3,
+                                           api.PREC_FP32, None) == 1
+    assert L.emfuse_smooth_gradient_domain(fake, 3, ctypes.c_void_p(32), 4, 4, 4, 1e-3, api.PREC_FP32, None) == 1
