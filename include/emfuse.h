@@ -213,17 +213,20 @@ int emfuse_screened_poisson_dct(const float* s, const float* o, float* f, int64_
  * zero), with the screening of Eq. (1):
  *     out = argmin_f  alpha |f - in|^2 + |grad_xy f - grad_xy in|^2 + |d_z f|^2
  * on the 6-neighbour graph of the stack with Neumann boundaries, i.e.
- * (alpha I + L_xy + L_z) out = alpha in + L_xy in.  Solved exactly: out = in + d, with d from
- * one 3-D real-to-complex FFT of the stack's mirror extension to 2nz x 2ny x 2nx, a scaling
- * by -lambda_z / (alpha + lambda), and the inverse FFT (cuFFT).
+ * (alpha I + L_xy + L_z) out = alpha in + L_xy in.  Solved exactly: out = in + d.  The
+ * orthonormal DCT-II along z (a dense nz x nz matrix applied to every pixel column, cuBLAS
+ * GEMM) diagonalises L_z, which splits the problem into nz slice problems
+ * (alpha + lambda_z[k]) d_k + L_xy d_k = -lambda_z[k] I_k; those are solved at once by the
+ * batched mirror-extension FFT of emfuse_screened_poisson_dct, and the inverse z transform
+ * (GEMM) gives d.
  *   in          device, nz x ny x nx dense [z][y][x], uint8 (dt = EMFUSE_U8) or float32.
  *   out         device float32, same shape; must not alias in.
  *   alpha       > 0 (finite).
  *   precision   EMFUSE_PREC_FP32 or EMFUSE_PREC_FP64 (transforms and scaling in that type).
- * Temporaries: the extended stack and its half spectrum (8 and about 8 times the stack's
- * cells, in the chosen type) plus cuFFT's work area, from the library's pool; EMFUSE_ENOMEM
- * when they do not fit.  The cuFFT plan is cached per shape and precision until
- * emfuse_release_cache().  Asynchronous on `stream`.
+ * Temporaries: two copies of the stack, its mirror extension and half spectrum (about 10
+ * times the stack's cells in the chosen type) plus cuFFT's work area, from the library's pool;
+ * EMFUSE_ENOMEM when they do not fit.  The cuFFT plan (per shape and precision) and the
+ * cuBLAS handle are cached until emfuse_release_cache().  Asynchronous on `stream`.
  */
 int emfuse_smooth_gradient_domain(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
                                   double alpha, int precision, void* stream);

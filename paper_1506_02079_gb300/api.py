@@ -302,7 +302,8 @@ def emfuse_smooth_gradient_domain(stack: torch.Tensor, alpha: float, precision: 
                                   out: torch.Tensor | None = None) -> torch.Tensor:
     """Phase 1 as the 3-D gradient-domain problem of the earlier method (Sec. 3 "Alternate
     Solutions": target gradients with their z-components zeroed, screened by alpha), solved
-    exactly by one 3-D FFT of the mirror-extended stack.  ``stack`` CUDA uint8 or float32
+    exactly: a DCT along z (GEMM) splits it into slice problems solved by the batched
+    mirror-extension FFT.  ``stack`` CUDA uint8 or float32
     [z][y][x]; precision PREC_FP32 / PREC_FP64.  Returns float32 of the same shape."""
     _require_cuda(stack)
     if stack.dim() != 3 or not stack.is_contiguous():

@@ -55,11 +55,12 @@ size_t cached_plan_bytes(cudaStream_t st, int precision);
 int solve_dct_batch(const float* s, const float* o, float* f, int64_t n, int64_t nx, int64_t ny, double alpha,
                     int precision, cudaStream_t st);
 // 3-D gradient-domain smoothing (dct_solve.cu): out = argmin alpha |f - in|^2 +
-// |grad_xy f - grad_xy in|^2 + |d_z f|^2 over an nz x ny x nx stack, exact by one 3-D FFT of
-// the mirror-extended stack; in uint8 (dt EMFUSE_U8) or float, transforms in `precision`
+// |grad_xy f - grad_xy in|^2 + |d_z f|^2 over an nz x ny x nx stack, exact: a DCT along z
+// (GEMM) splits it into nz slice problems solved by the mirror-extension FFT; in uint8
+// (dt EMFUSE_U8) or float, transforms in `precision`
 int smooth_gradient_domain(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz, double alpha,
                            int precision, cudaStream_t st);
-void release_fft_plans();
+void release_fft_plans();  // and the cuBLAS handles
 
 // elementwise helpers used by the adjoint (multigrid.cu)
 int apply_laplacian_stack(const float* in, float* out, int64_t nx, int64_t ny, int64_t nz,
