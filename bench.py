@@ -348,6 +348,15 @@ def run_gpu(args):
         extras["kernels"] = prof
         roof = kernel_roofline(prof)
         extras["roofline_relaxation"] = relaxation_roofline(prof)
+        # whole-step effective HBM fraction: voxels/s times the bytes per voxel the method must
+        # move (input 4 + output 4 + first residual 12 + 16 per V-cycle + 40 per FP64 correction
+        # pass; counts from this step's launches) over the measured HBM peak
+        per = {p["name"]: p["launches"] for p in prof}  # launches per step
+        n_v, n_outer = per.get("wave_up_l0", 0.0), per.get("residual_update", 0.0)
+        b_alg = 4.0 + 4.0 + 12.0 + 16.0 * n_v + 40.0 * n_outer
+        eff_gbs = voxels * world / (ms * 1e-3) * b_alg / 1e9
+        extras["effective_hbm"] = {"bytes_per_voxel": b_alg, "vcycles": n_v, "fp64_passes": n_outer,
+                                   "gbs": eff_gbs, "frac": eff_gbs / measured_hbm_peak()[0]}
         # end to end through the public API with host buffers
         I0_h = I0.cpu().pin_memory()
         out_h = torch.empty_like(I0_h).pin_memory()
