@@ -258,14 +258,26 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
         rrf += __shfl_xor_sync(0xffffffffu, rrf, m);
         if (MODE == 0) bbf += __shfl_xor_sync(0xffffffffu, bbf, m);
     }
-    __shared__ double red[2][8];
-    if ((tid & 31) == 0) { red[0][tid >> 5] = double(rrf); red[1][tid >> 5] = double(bbf); }
+    // the 8 warp partials: converted on the integer pipe and added in FP64 by a shuffle tree in
+    // the first warp (lanes l and l + 8, l + 16, l + 24 hold the same partial), 3 FP64 adds per
+    // norm: on this part one warp-wide FP64 instruction holds the pipe for 16 cycles, so a serial
+    // per-block loop would cost a sizeable share of the whole pass
+    __shared__ float red[2][8];
+    if ((tid & 31) == 0) { red[0][tid >> 5] = rrf; red[1][tid >> 5] = bbf; }
     __syncthreads();
-    if (tid == 0) {
-        double r2 = 0.0, b2 = 0.0;
-        for (int w = 0; w < 8; ++w) { r2 += red[0][w]; b2 += red[1][w]; }
-        atomicAdd(&norms[2 * j], r2);
-        if (MODE == 0) atomicAdd(&norms[2 * j + 1], b2);
+    if (tid < 32) {
+        const int l = tid & 7;
+        double r2 = cvt<double>(red[0][l]);
+        double b2 = MODE == 0 ? cvt<double>(red[1][l]) : 0.0;
+#pragma unroll
+        for (int m = 4; m > 0; m >>= 1) {
+            r2 += __shfl_xor_sync(0xffffffffu, r2, m);
+            if (MODE == 0) b2 += __shfl_xor_sync(0xffffffffu, b2, m);
+        }
+        if (tid == 0) {
+            atomicAdd(&norms[2 * j], r2);
+            if (MODE == 0) atomicAdd(&norms[2 * j + 1], b2);
+        }
     }
 }
 
