@@ -335,6 +335,17 @@ void emfuse_release_cache(void);
  */
 int emfuse_selftest_fpconv(int64_t* f2d_mismatches, int64_t* d2f_mismatches);
 
+/*
+ * Self-test of the bounded device waits (no counterpart in the paper: failure handling).  The
+ * library's kernels never wait without a bound: a wait on a shared-memory barrier that does not
+ * complete within its poll limit sets a per-device error word and the kernel returns, and the
+ * host call reports EMFUSE_ETIMEOUT with the context still usable.  This call launches one warp
+ * that waits, with at most `limit` polls (1 .. 2^20), on a barrier that nothing completes, on
+ * `stream`, synchronously; it returns EMFUSE_ETIMEOUT (the expected outcome) and clears the
+ * error word, or EMFUSE_EINVAL for a limit out of range.
+ */
+int emfuse_selftest_wait_timeout(int limit, void* stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* emfuse_last_error(void);
 

@@ -35,7 +35,8 @@ EXPORTED_SYMBOLS = ["emfuse_default_opts", "emfuse_smooth_z", "emfuse_screened_p
                     "emfuse_version", "emfuse_kernel_launches", "emfuse_profile_begin",
                     "emfuse_profile_end", "emfuse_release_cache", "emfuse_smooth_z_noalloc",
                     "emfuse_selftest_fpconv", "emfuse_autotune_result", "emfuse_smooth_z_robust",
-                    "emfuse_fuse_color", "emfuse_screened_poisson_dct", "emfuse_smooth_gradient_domain"]
+                    "emfuse_fuse_color", "emfuse_screened_poisson_dct", "emfuse_smooth_gradient_domain",
+                    "emfuse_selftest_wait_timeout"]
 
 
 class EmfuseError(RuntimeError):
@@ -91,6 +92,8 @@ def lib() -> ctypes.CDLL:
             L.emfuse_fuse_color.argtypes = [vp, vp, vp, i64, i64, i64, db, ctypes.POINTER(SolveOpts), vp, vp]
             L.emfuse_screened_poisson_dct.argtypes = [vp, vp, vp, i64, i64, i64, db, ci, vp]
             L.emfuse_smooth_gradient_domain.argtypes = [vp, ci, vp, i64, i64, i64, db, ci, vp]
+            L.emfuse_selftest_wait_timeout.argtypes = [ci, vp]
+            L.emfuse_selftest_wait_timeout.restype = ci
             L.emfuse_smooth_z_noalloc.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
             L.emfuse_selftest_fpconv.argtypes = [vp, vp]
             L.emfuse_autotune_result.argtypes = [vp, ci]

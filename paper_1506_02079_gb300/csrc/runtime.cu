@@ -190,6 +190,32 @@ int* device_error_flag() {
     return flags[dev];
 }
 
+// ---------------------------------------------------------------- bounded-wait self-test
+namespace {
+
+// The bounded wait of tma.cuh (mbar_wait_warp) with a poll limit given at run time.
+__device__ __forceinline__ bool wait_warp_polls(uint32_t bar, uint32_t parity, int limit) {
+    for (int it = 0; it < limit; ++it)
+        if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+    return false;
+}
+
+// One warp waits, with at most `limit` polls, for phase 0 of an mbarrier that nothing arrives
+// on: the wait runs out, and the kernel records that in the device error word and returns,
+// as every bounded wait of the library does when a copy never lands.
+__global__ void k_wait_timeout(int* err, int limit) {
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    if (!wait_warp_polls(b, 0, limit) && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------- conversion self-test
 namespace {
 
@@ -288,6 +314,32 @@ int emfuse_profile_end(emfuse_kernel_profile* out, int max_entries) {
         out[i].fp64_flops = v[i].second.flops;
     }
     return (int)v.size();
+}
+
+int emfuse_selftest_wait_timeout(int limit, void* stream) {
+    set_error("");
+    if (limit < 1 || limit > kWaitLimit) {
+        set_error("emfuse_selftest_wait_timeout: limit must be in [1, 2^20]");
+        return EMFUSE_EINVAL;
+    }
+    const cudaStream_t st = (cudaStream_t)stream;
+    int* err = device_error_flag();
+    if (!err) {
+        set_error("emfuse_selftest_wait_timeout: could not allocate the device error word");
+        return EMFUSE_ENOMEM;
+    }
+    k_wait_timeout<<<1, 32, 0, st>>>(err, limit);
+    EMF_CHECK_LAUNCH();
+    int flag = 0;
+    EMF_CUDA(cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EMF_CUDA(cudaStreamSynchronize(st));
+    if (flag) {
+        EMF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+        EMF_CUDA(cudaStreamSynchronize(st));
+        set_error("emfuse_selftest_wait_timeout: the bounded wait ran out (expected)");
+        return EMFUSE_ETIMEOUT;
+    }
+    return EMFUSE_OK;
 }
 
 int emfuse_selftest_fpconv(int64_t* f2d_mismatches, int64_t* d2f_mismatches) {

@@ -75,3 +75,6 @@ def test_host_side_calls_without_gpu(libpath):
     assert L.emfuse_smooth_gradient_domain(fake, 1, ctypes.c_void_p(32), 1 << 20, 1 << 20, 4, 1e-3,
                                            api.PREC_FP32, None) == 1
     assert L.emfuse_smooth_gradient_domain(fake, 3, ctypes.c_void_p(32), 4, 4, 4, 1e-3, api.PREC_FP32, None) == 1
+    # the bounded-wait self-test validates its limit before any CUDA call
+    assert L.emfuse_selftest_wait_timeout(0, None) == 1
+    assert L.emfuse_selftest_wait_timeout((1 << 20) + 1, None) == 1

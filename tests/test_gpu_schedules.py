@@ -138,3 +138,17 @@ def test_autotune_picks_the_fastest_candidate(dev):
                                       nx=nx, ny=ny, offsets=offs)
     assert torch.equal(f, ref)
     assert all(a["converged"] for a in st)
+
+
+def test_bounded_wait_runs_out_and_context_stays_usable(dev):
+    """A device wait on a barrier that nothing completes gives up after its poll limit: the
+    call reports EMFUSE_ETIMEOUT (5) and clears the device error word, and the context then
+    runs a solve and the self-test again as before (no fault, no hang: the wait is bounded)."""
+    L = api.lib()
+    st = torch.cuda.current_stream(dev).cuda_stream
+    assert L.emfuse_selftest_wait_timeout(1000, st) == 5
+    assert b"ran out" in L.emfuse_last_error()
+    I0 = make_stack(2, 64, 48, seed=21).to(dev)
+    f, stats = api.emfuse_screened_poisson(I0, I0.flip(0).contiguous(), 0.01, return_stats=True)
+    assert all(s["converged"] for s in stats) and bool(torch.isfinite(f).all())
+    assert L.emfuse_selftest_wait_timeout(1, st) == 5
