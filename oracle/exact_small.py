@@ -17,12 +17,74 @@ slice).  Setting dE/df_p = 0 gives, row by row,
 i.e. Eq. (1) with the graph Laplacian, assembled here edge by edge and solved by Gaussian
 elimination over ``fractions.Fraction``, so the result carries no rounding at all.  It is
 independent of the DCT solve in ``emfuse_oracle`` (no transform, no eigenvalues).
+
+``exact_gradient_domain`` does the same for the 3-D gradient-domain smoothing of the earlier
+method (Sec. 3 "Alternate Solutions": target gradients with their z-components zeroed),
+minimising alpha sum (f - I0)^2 + sum over x/y edges ((f_p - f_q) - (I0_p - I0_q))^2 +
+sum over z edges (f_p - f_q)^2 on the 6-neighbour graph of a tiny stack.
 """
 from __future__ import annotations
 
 from fractions import Fraction
 
-__all__ = ["exact_solve"]
+__all__ = ["exact_solve", "exact_gradient_domain"]
+
+
+def _solve_spd(A, b):
+    """Gaussian elimination over Fractions (A symmetric positive definite: pivots > 0)."""
+    n = len(b)
+    for k in range(n):
+        piv = A[k][k]
+        if piv == 0:
+            raise ArithmeticError("zero pivot")
+        for i in range(k + 1, n):
+            if A[i][k] != 0:
+                m = A[i][k] / piv
+                row_i, row_k = A[i], A[k]
+                for j in range(k, n):
+                    if row_k[j] != 0:
+                        row_i[j] -= m * row_k[j]
+                b[i] -= m * b[k]
+    f = [Fraction(0)] * n
+    for k in range(n - 1, -1, -1):
+        acc = b[k]
+        for j in range(k + 1, n):
+            acc -= A[k][j] * f[j]
+        f[k] = acc / A[k][k]
+    return f
+
+
+def exact_gradient_domain(I0, alpha):
+    """Exact smoothed stack for a tiny stack ``I0`` (nz x ny x nx nested lists of ints or
+    Fractions) and a positive Fraction ``alpha``; returns nested lists of Fractions."""
+    alpha = Fraction(alpha)
+    if alpha <= 0:
+        raise ValueError("alpha must be > 0")
+    nz, ny, nx = len(I0), len(I0[0]), len(I0[0][0])
+    n = nz * ny * nx
+    idx = lambda z, y, x: (z * ny + y) * nx + x
+    A = [[Fraction(0)] * n for _ in range(n)]
+    b = [Fraction(0)] * n
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                p = idx(z, y, x)
+                A[p][p] += alpha
+                b[p] += alpha * Fraction(I0[z][y][x])
+                for dz, dy, dx in ((0, 0, 1), (0, 1, 0), (1, 0, 0)):
+                    z2, y2, x2 = z + dz, y + dy, x + dx
+                    if z2 < nz and y2 < ny and x2 < nx:
+                        q = idx(z2, y2, x2)
+                        # target difference: the input's along x and y, zero along z
+                        g = Fraction(0) if dz else Fraction(I0[z][y][x]) - Fraction(I0[z2][y2][x2])
+                        A[p][p] += 1
+                        A[q][q] += 1
+                        A[p][q] -= 1
+                        A[q][p] -= 1
+                        b[p] += g
+                        b[q] -= g
+    f = _solve_spd(A, b)
+    return [[[f[idx(z, y, x)] for x in range(nx)] for y in range(ny)] for z in range(nz)]
 
 
 def exact_solve(s, o, alpha):
@@ -54,23 +116,5 @@ def exact_solve(s, o, alpha):
                     A[q][p] -= 1
                     b[p] += g
                     b[q] -= g
-    # Gaussian elimination (the matrix is symmetric positive definite, so every pivot is > 0)
-    for k in range(n):
-        piv = A[k][k]
-        if piv == 0:
-            raise ArithmeticError("zero pivot")
-        for i in range(k + 1, n):
-            if A[i][k] != 0:
-                m = A[i][k] / piv
-                row_i, row_k = A[i], A[k]
-                for j in range(k, n):
-                    if row_k[j] != 0:
-                        row_i[j] -= m * row_k[j]
-                b[i] -= m * b[k]
-    f = [Fraction(0)] * n
-    for k in range(n - 1, -1, -1):
-        acc = b[k]
-        for j in range(k + 1, n):
-            acc -= A[k][j] * f[j]
-        f[k] = acc / A[k][k]
+    f = _solve_spd(A, b)
     return [[f[y * nx + x] for x in range(nx)] for y in range(ny)]
