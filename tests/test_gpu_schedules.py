@@ -6,7 +6,6 @@
   and prolongation): outputs and statistics must be bit-identical.
 * Results do not depend on how the slices are batched (ragged batch vs one call per slice).
 """
-import numpy as np
 import pytest
 import torch
 
