@@ -18,9 +18,11 @@
  *   - Discretisation: Lap is the 5-point graph Laplacian with Neumann (no-flux) boundaries
  *     and unit pixel spacing; Gaussian taps are exp(-d^2 / 2 sigma^2) for integer
  *     |d| <= floor(3 sigma), renormalised over the taps that fall inside the stack.
- *   - Ownership: the caller owns every buffer passed in.  The library allocates its own
- *     device workspace (multigrid pyramids, FP64 iterates) stream-ordered on `stream` and
- *     releases it before returning.
+ *   - Ownership: the caller owns every buffer passed in.  The library owns its device
+ *     workspace: per-call temporaries come stream-ordered from its own memory pool and go back
+ *     to the pool by the end of the call; solver plans (multigrid pyramids, FP64 iterates,
+ *     tensor maps, captured graphs) are kept between calls for reuse, see
+ *     emfuse_release_cache().
  *   - Pointers are device pointers unless stated otherwise.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *   - Errors: every call returns an emfuse_status; it never aborts.  On error a message is
@@ -60,11 +62,20 @@ typedef enum {
 typedef struct {
     double tol;          /* stop when every slice has ||b - A f||_2 / ||b||_2 <= tol,
                             b = alpha s + L o, A = alpha I + L (residual measure of the
-                            solver table in Sec. 4).  Default 1e-6.                       */
+                            solver table in Sec. 4).  Default 1e-6.  The error it bounds is
+                            ||f - f*|| <= cond(A) tol ||f*||, cond(A) = 1 + 8 / alpha
+                            (8001 at alpha = 0.001): on smooth EM-like slices tol 1e-6
+                            keeps max |f - f*| well inside 1e-4 of the 8-bit range, on rough
+                            (noise-like) slices at small alpha it may not, and a smaller
+                            tol (1e-8 .. 1e-10, mixed or FP64 precision) is needed.     */
     int max_vcycles;     /* maximum outer iterations (one V-cycle each).  Default 40.      */
     int nu_pre;          /* red-black Gauss-Seidel sweeps before restriction.  Default 2.  */
     int nu_post;         /* sweeps after prolongation.  Default 2.                         */
-    int precision;       /* emfuse_precision.  Default EMFUSE_PREC_MIXED.                  */
+    int precision;       /* emfuse_precision.  Default EMFUSE_PREC_MIXED.  EMFUSE_PREC_FP32
+                            keeps the iterate in FP32: it meets 1e-4 of the 8-bit range at
+                            alpha >= 0.01, but at alpha = 0.001 its rounding reaches the
+                            smooth error modes amplified by ~1/alpha (about 4e-4 of the
+                            range), and it cannot reach tol below ~1e-6.                   */
     int fused;           /* 1: fused wavefront kernels on large levels; 0: one kernel per
                             half-sweep (reference schedule).  Default 1.                   */
     int first_vcycles;   /* V-cycles in the first outer iteration (the second continues from
@@ -87,6 +98,12 @@ typedef struct {
                             input and its smoothed copy on the device when they fit, else
                             slabs with halo planes), 1 = slabs, 2 = whole input (EMFUSE_ENOMEM
                             if it does not fit).  Default 0.                               */
+    int verify_residual; /* 1: after the solve, recompute every slice's relative residual
+                            with a separate plain FP64 kernel (b = alpha s + L o formed
+                            directly, every operation and sum in FP64) on the solver's final
+                            iterate and report it in stats.rel_residual_check: a check of
+                            the reported rel_residual, whose kernel rounds A d to FP32 and
+                            sums squares in FP32 per warp.  One extra pass.  Default 0.   */
 } emfuse_solve_opts;
 
 /* Per-slice result of a solve. */
@@ -95,6 +112,8 @@ typedef struct {
     int converged;        /* 1 if rel_residual <= tol                                      */
     double rel_residual;  /* final ||b - A f||_2 / ||b||_2, computed on the GPU              */
     double b_norm;        /* ||b||_2                                                        */
+    double rel_residual_check;  /* opts.verify_residual = 1: the same measure recomputed in
+                                   plain FP64 on the final iterate; else -1                  */
 } emfuse_slice_stats;
 
 /* Fill `opts` with the defaults listed above. */
@@ -142,7 +161,9 @@ int emfuse_smooth_z_robust(const void* in, int dt, float* out, int64_t nx, int64
  * Same arguments, layout and result as emfuse_smooth_z (within float rounding: it always runs
  * the plain-load fused kernel).  Its only scratch, the per-axis normaliser tables, lives in a
  * static device array of 3 * 32768 floats (384 KiB) that every GPU loading this library holds
- * until the process exits; it calls no cudaMalloc, cudaFree or other allocating routine.
+ * until the process exits; a small kernel fills the tables on `stream` from the Gaussian taps,
+ * so the call reads no host buffer.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.
  *
  *   Limits: nx + ny + nz <= 98304, floor(3 sigma_xy) <= 8, floor(3 sigma_z) <= 9; beyond
  *           them it returns EMFUSE_EINVAL with a message naming the limit.
@@ -345,6 +366,22 @@ int emfuse_selftest_fpconv(int64_t* f2d_mismatches, int64_t* d2f_mismatches);
  * error word, or EMFUSE_EINVAL for a limit out of range.
  */
 int emfuse_selftest_wait_timeout(int limit, void* stream);
+
+/*
+ * Architecture check (no counterpart in the paper): writes the binary version of the library's
+ * device code as loaded on the current device (major * 10 + minor, 103 for sm_103a) to the
+ * HOST int `binary_version`.  EMFUSE_ECUDA if the code cannot run on this device.
+ */
+int emfuse_kernel_binary_version(int* binary_version);
+
+/*
+ * FP64 roofline probe (no counterpart in the paper: measurement).  Times, with CUDA events on
+ * `stream`, a kernel of independent FP64 fused multiply-add chains filling every SM (8 chains
+ * per thread, 8 CTAs of 256 threads per SM), best of three launches after a warm-up, and
+ * writes the achieved FP64 rate in TFLOP/s (an FMA counts 2 flops) to the HOST double
+ * `tflops`.  Synchronous; allocates nothing; takes a few milliseconds.
+ */
+int emfuse_probe_fp64_fma_rate(double* tflops, void* stream);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* emfuse_last_error(void);

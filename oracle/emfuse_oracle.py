@@ -12,7 +12,8 @@ What it computes (every function cites the passage it follows):
   with the Gaussian truncated at three standard deviations (Sec. 3 "Implementation").
 * ``robust_smooth_stack`` -- phase 1 with robust averaging across slices (Sec. 3, the
   outlier example): z-window samples beyond kappa = 2 weighted standard deviations of the
-  weighted mean are left out of the average.
+  weighted mean are left out of the average.  ``robust_margin`` is how far a window's
+  decisions are from a tie; ``robust_outcomes`` lists every valid average where one is near.
 * ``solve_dct``     -- phase 2, Sec. 3 "Screened-Poisson Blending", Eq. (1):
   (alpha - Lap) I2_j = alpha I1_j - Lap I0_j, solved exactly by the frequency-space blend of
   Sec. 3 "Frequency-Space Interpretation" written for the discrete Neumann problem.
@@ -48,7 +49,7 @@ import numpy as np
 import scipy.fft as sfft
 
 __all__ = [
-    "gaussian_taps", "smooth_axis", "smooth_stack", "robust_smooth_stack", "robust_margin",
+    "gaussian_taps", "smooth_axis", "smooth_stack", "robust_smooth_stack", "robust_margin", "robust_outcomes",
     "smooth_transpose", "dsmooth_dsigma_z",
     "laplacian", "screened_rhs", "apply_A", "neumann_eigenvalues", "solve_dct", "fuse_color", "apply_Ainv",
     "gradient_domain_smooth",
@@ -167,6 +168,51 @@ def robust_margin(I0: np.ndarray, sigma_xy: float, sigma_z: float, kappa: float 
         thr = (kappa * kappa) * var
         out[z] = (np.abs((vals - mu) ** 2 - thr) / (thr + 1.0)).min(axis=0)
     return out
+
+
+def robust_outcomes(I0: np.ndarray, sigma_xy: float, sigma_z: float, kappa: float = 2.0,
+                    tie: float = 1e-3, max_ties: int = 8):
+    """Every valid result of ``robust_smooth_stack`` where a keep / drop decision is near a tie.
+
+    A sample of a window whose margin | (v_d - mu)^2 - kappa^2 var | / (kappa^2 var + 1) is at
+    most ``tie`` may be kept or dropped by an evaluation in other precision: both decisions
+    are valid readings of the rule (Sec. 3, the outlier example).  Returns (ref, alts): ref is
+    ``robust_smooth_stack``; alts maps the flat index of every voxel with such samples to the
+    array of weighted averages over all keep / drop choices of its near-tie samples (the other
+    samples as decided), ref's value among them.
+    """
+    v = np.asarray(I0, dtype=np.float64)
+    v = smooth_axis(v, sigma_xy, 2)
+    v = smooth_axis(v, sigma_xy, 1)
+    w = gaussian_taps(sigma_z)
+    R = (len(w) - 1) // 2
+    nz, ny, nx = v.shape
+    ref = robust_smooth_stack(I0, sigma_xy, sigma_z, kappa)
+    alts = {}
+    for z in range(nz):
+        ds = [d for d in range(-R, R + 1) if 0 <= z + d < nz]
+        ws = np.array([w[d + R] for d in ds])
+        vals = np.stack([v[z + d] for d in ds])
+        W = ws.sum()
+        mu = np.tensordot(ws, vals, axes=1) / W
+        var = np.tensordot(ws, (vals - mu) ** 2, axes=1) / W
+        thr = (kappa * kappa) * var
+        keep = (vals - mu) ** 2 <= thr
+        near = np.abs((vals - mu) ** 2 - thr) / (thr + 1.0) <= tie       # [taps][y][x]
+        for y, x in zip(*np.nonzero(near.any(axis=0))):
+            ties = np.nonzero(near[:, y, x])[0]
+            if len(ties) > max_ties:
+                raise ValueError(f"{len(ties)} near-tie samples in one window")
+            outs = []
+            for bits in range(1 << len(ties)):
+                k = keep[:, y, x].copy()
+                for b, t in enumerate(ties):
+                    k[t] = bool((bits >> b) & 1)
+                wk = ws * k
+                if wk.sum() > 0:
+                    outs.append(float((wk * vals[:, y, x]).sum() / wk.sum()))
+            alts[(z * ny + y) * nx + x] = np.array(outs)
+    return ref, alts
 
 
 def _axis_transpose(g: np.ndarray, sigma: float, axis: int, radius: int | None = None) -> np.ndarray:

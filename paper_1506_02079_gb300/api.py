@@ -22,7 +22,8 @@ __all__ = [
     "emfuse_screened_poisson",
     "emfuse_autotune_result", "TuneEntry", "emfuse_fuse_color", "emfuse_screened_poisson_dct",
     "emfuse_smooth_gradient_domain", "emfuse_correct_stack",
-    "emfuse_backward", "emfuse_version", "emfuse_release_cache", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
+    "emfuse_backward", "emfuse_version", "emfuse_release_cache", "emfuse_kernel_binary_version",
+    "emfuse_probe_fp64_fma_rate", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
     "PREC_FP64", "EXPORTED_SYMBOLS",
 ]
 
@@ -36,7 +37,8 @@ EXPORTED_SYMBOLS = ["emfuse_default_opts", "emfuse_smooth_z", "emfuse_screened_p
                     "emfuse_profile_end", "emfuse_release_cache", "emfuse_smooth_z_noalloc",
                     "emfuse_selftest_fpconv", "emfuse_autotune_result", "emfuse_smooth_z_robust",
                     "emfuse_fuse_color", "emfuse_screened_poisson_dct", "emfuse_smooth_gradient_domain",
-                    "emfuse_selftest_wait_timeout"]
+                    "emfuse_selftest_wait_timeout", "emfuse_kernel_binary_version",
+                    "emfuse_probe_fp64_fma_rate"]
 
 
 class EmfuseError(RuntimeError):
@@ -53,7 +55,8 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_vcycles", ctypes.c_int), ("nu_pre", ctypes.c_int),
                 ("nu_post", ctypes.c_int), ("precision", ctypes.c_int), ("fused", ctypes.c_int),
                 ("first_vcycles", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("no_graphs", ctypes.c_int), ("robust_kappa", ctypes.c_float), ("host_pipeline", ctypes.c_int)]
+                ("no_graphs", ctypes.c_int), ("robust_kappa", ctypes.c_float), ("host_pipeline", ctypes.c_int),
+                ("verify_residual", ctypes.c_int)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -63,7 +66,8 @@ class TuneEntry(ctypes.Structure):
 
 class SliceStats(ctypes.Structure):
     _fields_ = [("vcycles", ctypes.c_int), ("converged", ctypes.c_int),
-                ("rel_residual", ctypes.c_double), ("b_norm", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double), ("b_norm", ctypes.c_double),
+                ("rel_residual_check", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -96,6 +100,10 @@ def lib() -> ctypes.CDLL:
             L.emfuse_selftest_wait_timeout.restype = ci
             L.emfuse_smooth_z_noalloc.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
             L.emfuse_selftest_fpconv.argtypes = [vp, vp]
+            L.emfuse_kernel_binary_version.argtypes = [vp]
+            L.emfuse_kernel_binary_version.restype = ci
+            L.emfuse_probe_fp64_fma_rate.argtypes = [vp, vp]
+            L.emfuse_probe_fp64_fma_rate.restype = ci
             L.emfuse_autotune_result.argtypes = [vp, ci]
             L.emfuse_autotune_result.restype = ci
             L.emfuse_selftest_fpconv.restype = ci
@@ -123,6 +131,21 @@ def lib() -> ctypes.CDLL:
 
 def emfuse_version() -> str:
     return lib().emfuse_version().decode()
+
+
+def emfuse_kernel_binary_version() -> int:
+    """Binary version (major * 10 + minor) of the library's device code on the current device."""
+    v = ctypes.c_int(0)
+    _check(lib().emfuse_kernel_binary_version(ctypes.byref(v)))
+    return v.value
+
+
+def emfuse_probe_fp64_fma_rate(device: torch.device | None = None) -> float:
+    """Measured FP64 FMA throughput of the current device in TFLOP/s (CUDA events)."""
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    v = ctypes.c_double(0.0)
+    _check(lib().emfuse_probe_fp64_fma_rate(ctypes.byref(v), ctypes.c_void_p(_stream_ptr(dev))))
+    return v.value
 
 
 def emfuse_release_cache() -> None:
@@ -168,7 +191,7 @@ def _require_cuda(*ts):
 
 def _stats_list(arr) -> list[dict]:
     return [{"vcycles": s.vcycles, "converged": bool(s.converged), "rel_residual": s.rel_residual,
-             "b_norm": s.b_norm} for s in arr]
+             "b_norm": s.b_norm, "rel_residual_check": s.rel_residual_check} for s in arr]
 
 
 def emfuse_smooth_z(stack: torch.Tensor, sigma_xy: float = 1.0, sigma_z: float = 3.0,

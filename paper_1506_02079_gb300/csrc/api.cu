@@ -39,6 +39,7 @@ static int resolve_opts(const emfuse_solve_opts* in, emfuse_solve_opts* out) {
     if (out->autotune != 0 && out->autotune != 1) return einval("opts.autotune must be 0 or 1");
     if (out->no_graphs != 0 && out->no_graphs != 1) return einval("opts.no_graphs must be 0 or 1");
     if (out->host_pipeline < 0 || out->host_pipeline > 2) return einval("opts.host_pipeline must be 0, 1 or 2");
+    if (out->verify_residual != 0 && out->verify_residual != 1) return einval("opts.verify_residual must be 0 or 1");
     if (!(out->robust_kappa == 0.f || (out->robust_kappa >= 1.f && std::isfinite(out->robust_kappa))))
         return einval("opts.robust_kappa must be 0 (plain averaging) or finite and >= 1");
     return EMFUSE_OK;

@@ -281,12 +281,95 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
     }
 }
 
+// Independent check of the reported residual (opts.verify_residual): ||b - A f||^2 and ||b||^2
+// per slice for the final iterate f = o + d, with every operation in FP64 (hardware
+// conversions), b = alpha s + L o formed directly (not the correction form of k_top) and the
+// squares summed in FP64 (per-block shuffle tree, one FP64 atomic per block and slice).
+// which[j] picks the iterate buffer of slice j: 0 = none (d = 0, never iterated), 1 or 2 = the
+// first or second FP64 buffer.  Neighbours are read from global memory (a one-off pass).
+template <class TF, class To>
+__global__ void __launch_bounds__(256)
+k_verify(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, int nslices,
+         const int* __restrict__ which, const float* __restrict__ s, const To* __restrict__ o,
+         const float* __restrict__ rhs, const TF* __restrict__ d0, const TF* __restrict__ d1, double alpha,
+         double* __restrict__ sums) {
+    const int64_t t = blockIdx.x;
+    const int j = find_item(tile_start, nslices, t);
+    const TopSlice G = top[j];
+    const int lt = int(t - tile_start[j]);
+    const int tx0 = (lt % G.tiles_x) * kTopTX;
+    const int ty0 = (lt / G.tiles_x) * kTopTY;
+    const int tid = threadIdx.x;
+    const TF* d = which[j] == 1 ? d0 : (which[j] == 2 ? d1 : nullptr);
+    auto fval = [&](int64_t q) -> double {  // f = o + d (rhs mode: f = d)
+        const double dv = d ? (double)d[q] : 0.0;
+        return rhs ? dv : (double)o[q] + dv;
+    };
+    double rr = 0.0, bb = 0.0;
+    const int y = ty0 + tid / 16;
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+        const int x = tx0 + (tid % 16) + 16 * i;
+        if (x >= G.nx || y >= G.ny) continue;
+        const int64_t p = G.off + (int64_t)y * G.nx + x;
+        const bool hw = x > 0, he = x + 1 < G.nx, hn = y > 0, hs = y + 1 < G.ny;
+        double b, Lf = 0.0;
+        const double fc = fval(p);
+        if (hw) Lf += fc - fval(p - 1);
+        if (he) Lf += fc - fval(p + 1);
+        if (hn) Lf += fc - fval(p - G.nx);
+        if (hs) Lf += fc - fval(p + G.nx);
+        if (rhs) {
+            b = (double)rhs[p];
+        } else {
+            const double oc = (double)o[p];
+            double Lo = 0.0;
+            if (hw) Lo += oc - (double)o[p - 1];
+            if (he) Lo += oc - (double)o[p + 1];
+            if (hn) Lo += oc - (double)o[p - G.nx];
+            if (hs) Lo += oc - (double)o[p + G.nx];
+            b = alpha * (double)s[p] + Lo;
+        }
+        const double r = b - (alpha * fc + Lf);
+        rr += r * r;
+        bb += b * b;
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+        rr += __shfl_xor_sync(0xffffffffu, rr, m);
+        bb += __shfl_xor_sync(0xffffffffu, bb, m);
+    }
+    __shared__ double red[2][8];
+    if ((tid & 31) == 0) { red[0][tid >> 5] = rr; red[1][tid >> 5] = bb; }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0, c = 0.0;
+        for (int w = 0; w < 8; ++w) { a += red[0][w]; c += red[1][w]; }
+        atomicAdd(&sums[2 * j], a);
+        atomicAdd(&sums[2 * j + 1], c);
+    }
+}
+
 // out = o (or 0 in the adjoint mode) on one slice that was never iterated (it met the
 // tolerance at the initial iterate f = o).
 template <class To>
 __global__ void k_fill_initial(const To* __restrict__ o, float* __restrict__ out, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = o ? float(o[i]) : 0.f;
+}
+
+// A workspace larger than the device's whole memory can never be allocated: such a request
+// fails here with EMFUSE_ENOMEM, before any allocation and before any kernel reads the caller's
+// buffers.  (Smaller requests that exceed the free memory fail in the allocator, also ENOMEM.)
+inline int check_device_capacity(double bytes, const char* what) {
+    size_t free_b = 0, total_b = 0;
+    EMF_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    if (bytes > (double)total_b) {
+        set_error(std::string(what) + ": the solver workspace needs " + std::to_string(bytes / 1e9) +
+                  " GB, more than the device's " + std::to_string((double)total_b / 1e9) + " GB");
+        return EMFUSE_ENOMEM;
+    }
+    return EMFUSE_OK;
 }
 
 inline unsigned grid_for(int64_t n, int threads) {
@@ -438,6 +521,11 @@ struct Solver {
                 // u, b, and on wavefront levels the output iterate uo
                 total += (wave(j, k) ? 3 : 2) * round_up(lx, align) * ly;
             }
+        }
+        {
+            double fine = 0.0;  // the two FP64 iterates of run(): 2 x the finest levels
+            for (int64_t j = 0; j < n; ++j) fine += (double)rq->nx[j] * (double)rq->ny[j];
+            EMF_TRY(check_device_capacity((double)total * sizeof(TV) + 2.0 * fine * sizeof(TF), "solve"));
         }
         if (ws_levels.bytes() < (size_t)total * sizeof(TV))
             EMF_TRY(ws_levels.alloc_persistent((size_t)total * sizeof(TV)));
@@ -766,6 +854,31 @@ struct Solver {
         return EMFUSE_OK;
     }
 
+    // The plain FP64 recomputation of every slice's final relative residual (k_verify).
+    // last_pass[j]: the outer pass that last wrote slice j's iterate (0: never iterated).
+    template <class To>
+    int verify(const To* o, const std::vector<int>& last_pass, std::vector<double>& rel_out) {
+        const int64_t n = rq->nslices;
+        std::vector<int> which(n);
+        for (int64_t j = 0; j < n; ++j) which[j] = last_pass[j] == 0 ? 0 : 1 + (last_pass[j] & 1);
+        std::vector<double> sums(2 * n, 0.0);
+        EMF_CUDA(cudaMemcpyAsync(d_active, which.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+        EMF_CUDA(cudaMemsetAsync(d_norms, 0, 2 * n * sizeof(double), st));
+        {
+            KernelScope ks("residual_verify", st, top_cells * (12.0 + sizeof(TF) + sizeof(To)));
+            k_verify<TF, To><<<(unsigned)top_tiles, 256, 0, st>>>(d_top, d_top_ts, (int)n, d_active, rq->s, o,
+                                                                    rq->rhs, dbuf[0], dbuf[1], rq->alpha, d_norms);
+            EMF_CHECK_LAUNCH();
+        }
+        EMF_CUDA(cudaMemcpyAsync(sums.data(), d_norms, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        EMF_CUDA(cudaStreamSynchronize(st));
+        for (int64_t j = 0; j < n; ++j) {
+            const double bn = std::sqrt(sums[2 * j + 1]), rn = std::sqrt(sums[2 * j]);
+            rel_out[j] = bn > 0 ? rn / bn : rn;
+        }
+        return EMFUSE_OK;
+    }
+
     template <class To>
     int run(const To* o) {
         EMF_TRY(build());
@@ -777,7 +890,7 @@ struct Solver {
             EMF_TRY(ws_f.alloc_persistent((size_t)(2 * half) * sizeof(TF)));
         dbuf[0] = ws_f.as<TF>();
         dbuf[1] = ws_f.as<TF>() + half;
-        std::vector<int> active(n, 1), vcycles(n, 0);
+        std::vector<int> active(n, 1), vcycles(n, 0), last_pass(n, 0);
         std::vector<double> norms(2 * n), rel(n, 0.0), bnorm(n, 0.0);
         std::vector<char> done(n, 0);
         EMF_CUDA(cudaMemcpyAsync(d_active, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -806,6 +919,7 @@ struct Solver {
             all_done = true;
             for (int64_t j = 0; j < n; ++j) {
                 if (done[j]) continue;
+                last_pass[j] = it;  // this pass wrote the slice's iterate (it >= 1) and output
                 if (it == 0) bnorm[j] = std::sqrt(norms[2 * j + 1]);
                 const double rr = norms[2 * j];
                 rel[j] = bnorm[j] > 0 ? std::sqrt(rr) / bnorm[j] : std::sqrt(rr);
@@ -838,6 +952,8 @@ struct Solver {
                                                                      rq->out + rq->offsets[j], cells);
             EMF_CHECK_LAUNCH();
         }
+        std::vector<double> check(n, -1.0);
+        if (rq->opts.verify_residual) EMF_TRY(verify<To>(o, last_pass, check));
         bool nonfinite = false;
         if (rq->stats) {
             for (int64_t j = 0; j < n; ++j) {
@@ -845,6 +961,7 @@ struct Solver {
                 rq->stats[j].rel_residual = rel[j];
                 rq->stats[j].b_norm = bnorm[j];
                 rq->stats[j].converged = rel[j] <= rq->opts.tol ? 1 : 0;
+                rq->stats[j].rel_residual_check = check[j];
             }
         }
         for (int64_t j = 0; j < n; ++j) nonfinite |= !std::isfinite(rel[j]);
@@ -1036,6 +1153,7 @@ int solve_batch(const SolveRequest& req, cudaStream_t st) {
     auto trial = [&](int np, int nq, int rows) -> int {
         SolveRequest c = r;
         c.stats = nullptr;
+        c.opts.verify_residual = 0;
         c.opts.nu_pre = np;
         c.opts.nu_post = nq;
         c.opts.tile_rows = rows;

@@ -262,6 +262,30 @@ __global__ void k_selftest_fpconv(unsigned long long* bad) {
 
 }  // namespace
 
+// ---------------------------------------------------------------- FP64 rate probe
+namespace {
+
+constexpr int kRateChains = 8;  // independent DFMA chains per thread (covers the pipe latency)
+
+// Every thread runs kRateChains independent chains x <- x * a + b for `iters` steps (a, b keep
+// x bounded); the sums are written only if they match an impossible sentinel, so that the
+// chains stay live without a store per thread.
+__global__ void __launch_bounds__(256) k_fp64_rate(double* sink, int iters, double a, double b) {
+    double x[kRateChains];
+#pragma unroll
+    for (int i = 0; i < kRateChains; ++i) x[i] = 1e-3 * threadIdx.x + i;
+#pragma unroll 1
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int i = 0; i < kRateChains; ++i) x[i] = __fma_rn(x[i], a, b);
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < kRateChains; ++i) s += x[i];
+    if (sink && s == -1.25e300) sink[0] = s;
+}
+
+}  // namespace
+
 }  // namespace emfuse
 
 using namespace emfuse;
@@ -339,6 +363,61 @@ int emfuse_selftest_wait_timeout(int limit, void* stream) {
         set_error("emfuse_selftest_wait_timeout: the bounded wait ran out (expected)");
         return EMFUSE_ETIMEOUT;
     }
+    return EMFUSE_OK;
+}
+
+int emfuse_kernel_binary_version(int* binary_version) {
+    set_error("");
+    if (!binary_version) {
+        set_error("emfuse_kernel_binary_version: null pointer");
+        return EMFUSE_EINVAL;
+    }
+    cudaFuncAttributes attr;
+    EMF_CUDA(cudaFuncGetAttributes(&attr, k_wait_timeout));
+    *binary_version = attr.binaryVersion;
+    return EMFUSE_OK;
+}
+
+int emfuse_probe_fp64_fma_rate(double* tflops, void* stream) {
+    set_error("");
+    if (!tflops) {
+        set_error("emfuse_probe_fp64_fma_rate: null pointer");
+        return EMFUSE_EINVAL;
+    }
+    const cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    EMF_CUDA(cudaGetDevice(&dev));
+    EMF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    cudaEvent_t a = nullptr, b = nullptr;
+    EMF_CUDA(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        set_error("emfuse_probe_fp64_fma_rate: cudaEventCreate failed");
+        return EMFUSE_ECUDA;
+    }
+    float best = 0.f;
+    cudaError_t e = cudaSuccess;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first launch is a warm-up
+        cudaEventRecord(a, st);
+        {
+            KernelScope ks("fp64_rate_probe", st, 0.0, 2.0 * kRateChains * (double)iters * blocks * threads);
+            k_fp64_rate<<<blocks, threads, 0, st>>>(nullptr, iters, 0.9999999, 1e-7);
+        }
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) best = ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess || !(best > 0.f)) {
+        set_error(std::string("emfuse_probe_fp64_fma_rate: ") + cudaGetErrorString(e));
+        return EMFUSE_ECUDA;
+    }
+    *tflops = 2.0 * kRateChains * (double)iters * blocks * threads / (best * 1e-3) / 1e12;
     return EMFUSE_OK;
 }
 

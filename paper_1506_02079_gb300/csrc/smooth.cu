@@ -686,6 +686,25 @@ static __device__ __align__(256) float g_noalloc_norms[kNoAllocMaxNorms];
 
 namespace {
 
+// Fills the table [inv_x | inv_y | inv_z] of the allocation-free variant on the device, from the
+// taps passed by value: entry i of an axis of length n is 1 / (sum of the taps w(d), |d| <= R,
+// with 0 <= i + d < n), summed in double over d = -R..R and rounded once to float, i.e. the
+// values inverse_norms() forms on the host.  (prm.wz holds w(R_z - j); the taps are symmetric,
+// so prm.wz[d + R_z] = w(d).)
+__global__ void k_noalloc_norms(float* __restrict__ tab, int nx, int ny, int nz, SmoothParams prm) {
+    const int total = nx + ny + nz;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const bool zax = t >= nx + ny;
+        const int i = t < nx ? t : (zax ? t - nx - ny : t - nx);
+        const int n = t < nx ? nx : (zax ? nz : ny);
+        const int R = zax ? prm.Rz : prm.Rxy;
+        double sum = 0.0;
+        for (int d = -R; d <= R; ++d)
+            if (i + d >= 0 && i + d < n) sum += (double)(zax ? prm.wz[d + R] : prm.wxy[d + R]);
+        tab[t] = (float)(1.0 / sum);
+    }
+}
+
 std::mutex g_noalloc_mu;
 float* g_noalloc_ptr[64] = {nullptr};
 
@@ -755,21 +774,23 @@ extern "C" int emfuse_smooth_z_noalloc(const void* in, int dt, float* out, int64
     EMF_TRY(noalloc_norms(&norms));
     const auto wxy = gaussian_taps(sigma_xy, Rxy);
     const auto wz = gaussian_taps(sigma_z, Rz);
-    std::vector<float> host = inverse_norms(wxy, (int)nx);
-    const auto iy = inverse_norms(wxy, (int)ny), iz = inverse_norms(wz, (int)nz);
-    host.insert(host.end(), iy.begin(), iy.end());
-    host.insert(host.end(), iz.begin(), iz.end());
-    // Stream-ordered after earlier work on `st`; a copy from pageable memory has read `host`
-    // by the time it returns.  Every entry of the table that the kernel reads is written here.
-    EMF_CUDA(cudaMemcpyAsync(norms, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-    const float* inv_x = norms;
-    const float* inv_y = inv_x + nx;
-    const float* inv_z = inv_y + ny;
     SmoothParams prm{};
     prm.Rxy = Rxy;
     prm.Rz = Rz;
     for (int d = 0; d < 2 * Rxy + 1; ++d) prm.wxy[d] = wxy[d];
     for (int j = 0; j < 2 * Rz + 1; ++j) prm.wz[j] = wz[2 * Rz - j];
+    // The normaliser tables are written on the device, stream-ordered before the smoothing
+    // kernel, from the taps in `prm` (no host buffer is involved).  Every entry the smoothing
+    // kernel reads is rewritten by each call.
+    {
+        const int total = (int)(nx + ny + nz);
+        KernelScope ks("smooth_noalloc_norms", st, 4.0 * total);
+        k_noalloc_norms<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(norms, (int)nx, (int)ny, (int)nz, prm);
+        EMF_CHECK_LAUNCH();
+    }
+    const float* inv_x = norms;
+    const float* inv_y = inv_x + nx;
+    const float* inv_z = inv_y + ny;
     const dim3 grid((unsigned)ceil_div(nx, kTX), (unsigned)ceil_div(ny, kTY));
     const int P = 2 * Rz + 1;
     const int64_t zin0 = std::max<int64_t>(0, z0 - Rz), zin1 = std::min<int64_t>(nz, z1 + Rz);

@@ -71,3 +71,35 @@ def test_full_ragged_batch_sampled_slices(dev):
         sl = lambda t: t[a:a + h * w].view(h, w).double().cpu().numpy()
         ref = O.solve_dct(sl(s), sl(o), alpha)
         assert maxdiff(sl(f), ref) <= SOLVE_TOL
+
+
+def _oracle_smooth_contiguous(x, sxy, sz):
+    """O.smooth_stack's x, y, z passes, each run by O.smooth_axis on a copy whose smoothed axis
+    is the outer one (contiguous rows: the oracle's per-index loop would otherwise gather with
+    a stride of a whole row at every step).  Only the memory layout changes, not the sums."""
+    a = np.ascontiguousarray(np.moveaxis(x, 2, 0))          # [nx][nz][ny]
+    a = O.smooth_axis(a, sxy, 0)
+    a = np.ascontiguousarray(np.moveaxis(a, 0, 2))          # back to [nz][ny][nx]
+    a = O.smooth_axis(a, sxy, 1)
+    return O.smooth_axis(a, sz, 0)
+
+
+@pytest.mark.parametrize("nz,ny", [(2, 2048), (1, 21504)])
+def test_paper_width_host_path_vs_oracle(dev, nz, ny):
+    """The slice width of the paper's largest stacks (21504 x 26624, Table t:kasthuri_cardona):
+    26624-wide rows take 238 wavefront strips per level-0 row (two edge strips, a different mix
+    from 2048-wide slices), uint8 input streamed from pinned host memory as in the streamed
+    configuration.  Every output element against the oracle's smoothing and DCT solve."""
+    nx, alpha = 26624, 1e-3
+    I0 = make_stack(nz, ny, nx, 4, device=dev, dtype=torch.float32, out_dtype=torch.uint8).cpu().pin_memory()
+    out = torch.empty((nz, ny, nx), dtype=torch.float32, pin_memory=True)
+    opts = api.default_opts(tol=1e-6, precision=api.PREC_MIXED)
+    _, stats = api.emfuse_correct_stack(I0, 1.0, 3.0, alpha, opts, out=out, return_stats=True)
+    assert max(st["rel_residual"] for st in stats) <= 1e-6
+    x = I0.numpy().astype(np.float64)
+    s = _oracle_smooth_contiguous(x, 1.0, 3.0)
+    for j in range(nz):
+        ref = O.solve_dct(s[j], x[j], alpha)
+        err = np.abs(out[j].numpy().astype(np.float64) - ref)
+        assert float(err.max()) <= SOLVE_TOL, (j, float(err.max()))
+        del ref, err

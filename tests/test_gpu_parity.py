@@ -108,6 +108,33 @@ def test_solve_odd_sizes(dev, shape, alpha):
     assert stats[0]["rel_residual"] <= 1e-10
 
 
+@pytest.mark.parametrize("case", ["plain_16x256", "mixed_2048_slices"])
+@pytest.mark.parametrize("precision", [api.PREC_MIXED, api.PREC_FP64])
+def test_reported_residual_matches_a_plain_fp64_recomputation(dev, case, precision):
+    """stats.rel_residual comes from the residual kernel, which (mixed) rounds A d to FP32 before
+    the subtraction and sums squares in FP32 per warp.  opts.verify_residual recomputes
+    ||b - A f|| / ||b|| on the same final FP64 iterate with a separate kernel in plain FP64 (b
+    formed from s and o, not the correction form).  The two agree to 1 % (the FP32 shortcuts
+    move the reported value by about 1e-5 of itself), so the reported convergence to 1e-6 holds."""
+    if case == "plain_16x256":
+        I0 = make_stack(16, 256, 256, seed=0).to(dev)
+        s, o, alpha = api.emfuse_smooth_z(I0, 1.0, 3.0), I0, 0.01
+    else:  # slices 30 and 31 of the 64 x 2048 x 2048 stack, smoothed within their neighbourhood
+        from paper_1506_02079_gb300.synthetic import evaluate_stack, stack_params
+        slab = evaluate_stack(stack_params(64, 2048, 2048, 1), 21, 41, device=dev, out_dtype=torch.float32)
+        s = api.emfuse_smooth_z(slab, 1.0, 3.0, z0=9, z1=11)
+        o, alpha = slab[9:11].contiguous(), 1e-3
+    opts = api.default_opts(tol=1e-6, precision=precision, verify_residual=1)
+    _, stats = api.emfuse_screened_poisson(s, o, alpha, opts, return_stats=True)
+    for st in stats:
+        assert st["rel_residual"] <= 1e-6
+        assert st["rel_residual_check"] > 0
+        assert abs(st["rel_residual"] - st["rel_residual_check"]) <= 0.01 * st["rel_residual_check"], st
+    off = api.emfuse_screened_poisson(s, o, alpha, api.default_opts(tol=1e-6, precision=precision),
+                                      return_stats=True)[1]
+    assert all(st["rel_residual_check"] == -1.0 for st in off)
+
+
 def test_solve_ragged_batch(dev):
     """One call on slices of mixed sizes (the batched configuration, scaled down)."""
     s, o, ny, nx, offs = make_ragged_batch(12, seed=2, side_lo=16, side_hi=300)
@@ -217,15 +244,21 @@ def corrupted_stack(nz, ny, nx, seed, dtype=torch.float32):
 
 
 def robust_compare(got, I0, sxy, sz, kappa):
-    """Element-wise against the oracle wherever no keep / drop decision of the window is within
-    a relative 1e-3 of a tie (FP32 and FP64 may decide ties differently; either is valid)."""
+    """Every voxel against the oracle.  Where no keep / drop decision of the window is within a
+    relative 1e-3 of its threshold, against the oracle's value; where one is (FP32 and FP64 may
+    decide it differently, and both decisions are valid), against the nearest of the window's
+    valid outcomes (every keep / drop choice of its near-tie samples)."""
     x = I0.double().numpy()
-    ref = O.robust_smooth_stack(x, sxy, sz, kappa)
-    margin = O.robust_margin(x, sxy, sz, kappa)
-    clear = margin > 1e-3
-    assert clear.mean() > 0.99
-    d = np.abs(np.asarray(got, np.float64) - ref)[clear]
-    assert d.max() <= SMOOTH_TOL
+    got = np.asarray(got, np.float64)
+    ref, alts = O.robust_outcomes(x, sxy, sz, kappa, tie=1e-3)
+    near = np.zeros(ref.size, bool)
+    near[list(alts)] = True
+    near = near.reshape(ref.shape)
+    assert near.mean() < 0.01
+    assert np.abs(got - ref)[~near].max() <= SMOOTH_TOL
+    flat = got.reshape(-1)
+    for idx, vals in alts.items():
+        assert np.min(np.abs(vals - flat[idx])) <= SMOOTH_TOL, (idx, flat[idx], vals)
 
 
 @pytest.mark.parametrize("shape,dtype", [((17, 64, 96), torch.float32), ((12, 40, 33), torch.uint8),

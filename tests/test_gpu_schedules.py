@@ -88,6 +88,15 @@ def test_integer_pipe_conversions_match_hardware(dev):
     assert api.emfuse_selftest_fpconv() == (0, 0)
 
 
+def test_device_code_is_sm103a_and_fp64_probe_runs(dev):
+    """The loaded device code is sm_103a (binary version 103, a runtime query instead of any
+    look into the binary); the FP64 rate probe returns a plausible GB300 rate (nominal 1.25
+    TFLOP/s at the maximum clock; well above 0.1 and below 3 at any clock)."""
+    assert api.emfuse_kernel_binary_version() == 103
+    r = api.emfuse_probe_fp64_fma_rate(dev)
+    assert 0.1 < r < 3.0, r
+
+
 def test_slices_met_at_initial_iterate_return_o(dev):
     """A slice with s = o has r = 0 at f = o and is never iterated; its output must still be
     written (f = o) while the other slices of the batch iterate, in every precision."""

@@ -362,6 +362,46 @@ def test_robust_uses_weighted_statistics_and_kappa_in_sigma_units():
     assert drop[1, 0, 0] == pytest.approx(10.0, abs=1e-12)
 
 
+# sigma_z with taps w(1) = 1/2 and w(2) = 1/16 exactly: exp(-1 / (2 sigma^2)) = 1/2
+SIGMA_HALF = math.sqrt(1.0 / (2.0 * math.log(2.0)))   # floor(3 sigma) = 2
+
+
+def test_robust_margin_on_hand_computed_windows():
+    """robust_margin = min over the window of |(v_d - mu)^2 - kappa^2 var| / (kappa^2 var + 1).
+    Stack -1, 0, 1 (one pixel per plane), kappa = 2, weights 1, 1/2, 1/16 at |d| = 0, 1, 2.
+    Middle plane: taps -1, 0, 1 with weights 1/2, 1, 1/2: mu = 0, var = 1/2, threshold 2,
+    squared deviations 1, 0, 1, margin |1 - 2| / 3 = 1/3.  First plane: taps 0, 1, 2 with
+    values -1, 0, 1 and weights 1, 1/2, 1/16 (W = 25/16): mu = -0.6, var = 0.5 / W = 0.32,
+    threshold 1.28, squared deviations 0.16, 0.36, 2.56, margin 0.92 / 2.28; the last plane
+    mirrors it.  A one-plane window (sigma_z with floor(3 sigma_z) = 0) is an exact tie at
+    every voxel (0 <= 0): margin 0."""
+    assert O.support_radius(SIGMA_HALF) == 2
+    I0 = np.array([-1.0, 0.0, 1.0]).reshape(3, 1, 1)
+    m = O.robust_margin(I0, 0.0, SIGMA_HALF, kappa=2.0)[:, 0, 0]
+    np.testing.assert_allclose(m, [0.92 / 2.28, 1.0 / 3.0, 0.92 / 2.28], rtol=0, atol=1e-12)
+    flat = np.random.default_rng(3).uniform(0, 255, size=(4, 3, 5))
+    np.testing.assert_allclose(O.robust_margin(flat, 1.0, 0.2), 0.0, rtol=0, atol=0)
+
+
+def test_robust_margin_zero_at_an_exact_tie_and_outcomes_list_both_decisions():
+    """Stack 0, 0, 4 with the same weights: at the middle plane W = 2, mu = 1, var = 3 and the
+    squared deviations are 1, 1, 9.  With kappa = sqrt(3) the sample 4 sits exactly on the
+    threshold 9: margin 0 (to the rounding of kappa^2), and both decisions are valid: keep it
+    (average 1) or drop it (average 0).  robust_outcomes lists exactly these two values there,
+    the oracle's own decision among them, and nothing at the clear first plane (samples 0, 0,
+    4 with weights 1, 1/2, 1/16: margins far from 0)."""
+    I0 = np.array([0.0, 0.0, 4.0]).reshape(3, 1, 1)
+    k = math.sqrt(3.0)
+    assert O.robust_margin(I0, 0.0, SIGMA_HALF, kappa=k)[1, 0, 0] == pytest.approx(0.0, abs=1e-12)
+    ref, alts = O.robust_outcomes(I0, 0.0, SIGMA_HALF, kappa=k, tie=1e-6)
+    assert sorted(alts) == [1]
+    np.testing.assert_allclose(np.sort(alts[1]), [0.0, 1.0], rtol=0, atol=1e-12)
+    assert np.min(np.abs(alts[1] - ref[1, 0, 0])) <= 1e-12
+    # away from the tie (kappa = 2: threshold 12 > 9) the sample is kept and nothing is listed
+    ref2, alts2 = O.robust_outcomes(I0, 0.0, SIGMA_HALF, kappa=2.0, tie=1e-6)
+    assert alts2 == {} and ref2[1, 0, 0] == pytest.approx(1.0, abs=1e-12)
+
+
 # ----------------------------------------------------------------------------- colour fusion
 def test_fuse_color_closed_forms():
     """Colour / monochrome fusion (Sec. 3): (1) a grey colour image (three equal channels)
