@@ -110,6 +110,35 @@ struct StencilTab {
     Coef<T> ci;   // interior stencil
 };
 
+// Per-lane diagonal of the interior body (see "ghost strips" in k_wave): 1 / D of cell 0, of
+// cells 1 and 2 and of cell 3 of the lane, and D of cells 0 and 3 (cells 1 and 2 always have the
+// interior D).  Interior lanes hold the interior values; lanes outside the level 1 / D = 0.
+template <class T>
+struct LaneDiag {
+    T iD0, iD12, iD3;
+    T D0, D3;
+};
+
+// gs_update with the reciprocal diagonal given separately (same operations, same order).
+template <class T>
+__device__ __forceinline__ T gs_update_iD(const Coef<T>& c, T iD, T b, T uw, T ue, T un, T us) {
+    T acc = fma_t(c.cw, uw, b);
+    acc = fma_t(c.ce, ue, acc);
+    acc = fma_t(c.cn, un, acc);
+    acc = fma_t(c.cs, us, acc);
+    return mul_t(acc, iD);
+}
+
+// residual_at with the diagonal given separately (same operations, same order).
+template <class T>
+__device__ __forceinline__ T residual_at_D(const Coef<T>& c, T D, T b, T u, T uw, T ue, T un, T us) {
+    T acc = fma_t(c.cw, uw, b);
+    acc = fma_t(c.ce, ue, acc);
+    acc = fma_t(c.cn, un, acc);
+    acc = fma_t(c.cs, us, acc);
+    return fma_t(-D, u, acc);
+}
+
 template <class T>
 __device__ __forceinline__ void make_stencil_tab(StencilTab<T>& tab, int k, T alpha, T sk) {
     AxisCoef<T> one;
@@ -162,15 +191,15 @@ __device__ __forceinline__ Coef<T> cached_coef(uint32_t cache, int i) {
 template <class T, bool FAST>
 __device__ __forceinline__ void sweep_row(T (&row)[4], const T (&brow)[4], const T (&nrow)[4], const T (&srow)[4],
                                           int f, T west, T east, bool fast, bool irow, uint32_t cache,
-                                          const StencilTab<T>& tab, int xlane, int r, int nx, int ny, int n0x,
-                                          int n0y, int k, T alpha, T sk) {
+                                          const StencilTab<T>& tab, const LaneDiag<T>& g, int xlane, int r, int nx,
+                                          int ny, int n0x, int n0y, int k, T alpha, T sk) {
     if (FAST || fast) {
         if (f == 0) {
-            row[0] = gs_update<T>(tab.ci, brow[0], west, row[1], nrow[0], srow[0]);
-            row[2] = gs_update<T>(tab.ci, brow[2], row[1], row[3], nrow[2], srow[2]);
+            row[0] = gs_update_iD<T>(tab.ci, g.iD0, brow[0], west, row[1], nrow[0], srow[0]);
+            row[2] = gs_update_iD<T>(tab.ci, g.iD12, brow[2], row[1], row[3], nrow[2], srow[2]);
         } else {
-            row[1] = gs_update<T>(tab.ci, brow[1], row[0], row[2], nrow[1], srow[1]);
-            row[3] = gs_update<T>(tab.ci, brow[3], row[2], east, nrow[3], srow[3]);
+            row[1] = gs_update_iD<T>(tab.ci, g.iD12, brow[1], row[0], row[2], nrow[1], srow[1]);
+            row[3] = gs_update_iD<T>(tab.ci, g.iD3, brow[3], row[2], east, nrow[3], srow[3]);
         }
     } else {
 #pragma unroll
@@ -189,16 +218,21 @@ __device__ __forceinline__ void sweep_row(T (&row)[4], const T (&brow)[4], const
 template <class T, bool FAST>
 __device__ __forceinline__ void residual_row(T (&res)[4], const T (&row)[4], const T (&brow)[4], const T (&nrow)[4],
                                              const T (&srow)[4], T west, T east, bool fast, bool irow,
-                                             uint32_t cache, const StencilTab<T>& tab, int xlane, int r, int nx,
-                                             int ny, int n0x, int n0y, int k, T alpha, T sk) {
+                                             uint32_t cache, const StencilTab<T>& tab, const LaneDiag<T>& g,
+                                             int xlane, int r, int nx, int ny, int n0x, int n0y, int k, T alpha,
+                                             T sk) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const T uw = i == 0 ? west : row[i - 1];
         const T ue = i == 3 ? east : row[i + 1];
-        const Coef<T> c = (FAST || fast) ? tab.ci
-                               : (irow ? cached_coef<T>(cache, i)
-                                       : edge_coef<T>(tab, xlane + i, r, nx, ny, n0x, n0y, k, alpha, sk));
-        res[i] = residual_at<T>(c, brow[i], row[i], uw, ue, nrow[i], srow[i]);
+        if (FAST || fast) {
+            const T D = i == 0 ? g.D0 : (i == 3 ? g.D3 : tab.ci.D);
+            res[i] = residual_at_D<T>(tab.ci, D, brow[i], row[i], uw, ue, nrow[i], srow[i]);
+        } else {
+            const Coef<T> c = irow ? cached_coef<T>(cache, i)
+                                   : edge_coef<T>(tab, xlane + i, r, nx, ny, n0x, n0y, k, alpha, sk);
+            res[i] = residual_at<T>(c, brow[i], row[i], uw, ue, nrow[i], srow[i]);
+        }
     }
 }
 
@@ -296,16 +330,43 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     const bool interior_lane = lane >= kWaveHalo / 4 && lane < 32 - kWaveHalo / 4;
     StencilTab<T> tab;
     make_stencil_tab<T>(tab, k, alpha, sk);
-    // xint: the lane can use the interior stencil: all 4 cells interior along x, or all 4
-    // outside the level (their values are never written back and in-level cells give them
-    // zero weight, so any finite update will do)
-    bool xint = xlane + 3 < 0 || xlane >= nx;
-    if (!xint) {
-        xint = true;
+
+    // Ghost strips.  A strip whose lanes are each wholly inside or wholly outside the level, and
+    // whose in-level cells are all interior along x except the level's first cell (cell 0 of a
+    // lane) and last cell (cell 3 of a lane) with their one-sided stencils (and for UP, there,
+    // the injection from the coarse cell), runs its interior rows with the interior body too.
+    // Cells outside the level are kept at exactly 0 there: their 1 / D is 0 and no coarse
+    // correction is added to them (weight pm = 0; TMA fills them with 0 on every load).  A
+    // boundary cell's missing neighbour then enters the interior stencil as 0, which adds
+    // nothing (fma(c, 0, acc) = acc), and only its diagonal differs from the interior one: the
+    // lane's iD0 / D0 or iD3 / D3 (LaneDiag), and its interpolation weight along x is 0 (wx0 /
+    // wx3).  The operations and their order are those of the per-cell stencils, so the results
+    // are the same bit for bit.  Every strip of a level whose width is a multiple of 4 and whose
+    // coarse cells are full qualifies; others take the general body.
+    const bool all_in = xlane >= 0 && xlane + 3 < nx;
+    const bool all_out = xlane + 3 < 0 || xlane >= nx;
+    bool ghost_ok = all_in || all_out;
+    LaneDiag<T> g;
+    g.iD0 = g.iD12 = g.iD3 = all_out ? T(0) : tab.ci.iD;
+    g.D0 = g.D3 = tab.ci.D;
+    T wx0 = T(0.25), wx3 = T(0.25);
+    const T pm = all_out ? T(0) : T(1);
+    if (all_in) {
+        AxisCoef<T> one;
+        one.w = T(1); one.gm = T(1); one.gp = T(1);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const AxisCoef<T> q = axis_coef<T>(xlane + i, nx, L.n0x, k);
-            xint = xint && q.w == T(1) && q.gm == T(1) && q.gp == T(1);
+            if (q.w == T(1) && q.gm == T(1) && q.gp == T(1)) continue;
+            const bool first = i == 0 && xlane == 0 && q.w == T(1) && q.gm == T(0) && q.gp == T(1);
+            const bool last = i == 3 && xlane + 3 == nx - 1 && q.w == T(1) && q.gm == T(1) && q.gp == T(0);
+            if (!(first || last)) {
+                ghost_ok = false;
+                continue;
+            }
+            const Coef<T> c = make_coef<T>(q, one, k, alpha, sk);
+            if (i == 0) { g.iD0 = c.iD; g.D0 = c.D; }
+            if (i == 3) { g.iD3 = c.iD; g.D3 = c.D; }
         }
     }
 
@@ -315,20 +376,24 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     bool std_lane = true;  // interior pattern: J = I-1, I+1, I-1, I+1 with weight 1/4
     const bool has_coarse = UP && L.uco != nullptr;
     if (UP) {
-        int oI[4], oJ[4];
-        T cwx[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             int I = 0, J = 0;
             T w = T(0);
             if (has_coarse && lane_in) interp_axis<T>(xlane + i, L.n0x, k, L.ncx, I, J, w);
-            oI[i] = I - cx0 + 1;
-            oJ[i] = J - cx0 + 1;
-            cwx[i] = w;
+            const int oI = I - cx0 + 1, oJ = J - cx0 + 1;
+            const int sI = i < 2 ? 1 : 2, sJ = (i == 0 || i == 2) ? sI - 1 : sI + 1;  // interior pattern
+            if (oI == sI && oJ == sJ && w == T(0.25)) continue;
+            std_lane = false;
+            // injection (J = I, weight 0) at the level's first / last cell keeps a ghost strip
+            const bool edge_cell = (i == 0 && xlane == 0) || (i == 3 && xlane + 3 == nx - 1);
+            if (has_coarse && all_in && edge_cell && oI == sI && J == I && w == T(0)) {
+                if (i == 0) wx0 = T(0);
+                if (i == 3) wx3 = T(0);
+            } else if (has_coarse && all_in) {
+                ghost_ok = false;
+            }
         }
-        std_lane = oI[0] == 1 && oJ[0] == 0 && oI[1] == 1 && oJ[1] == 2 && oI[2] == 2 && oJ[2] == 1 &&
-                   oI[3] == 2 && oJ[3] == 3 && cwx[0] == T(0.25) && cwx[1] == T(0.25) &&
-                   cwx[2] == T(0.25) && cwx[3] == T(0.25);
     }
 
     {  // cache this lane's stencils for interior rows (read when the row pair is not all-interior)
@@ -383,7 +448,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
     // interior stencil along x (and for UP the regular 1/4-3/4 prolongation pattern), run a
     // step body specialised to the interior stencil; the others the general one.  The choice
     // is warp-uniform, so each step executes exactly one of the two bodies.
-    const bool x_fast = __all_sync(0xffffffffu, xint && lane_in && (!UP || (std_lane && xlane + 3 < nx)));
+    const bool x_ghost = __all_sync(0xffffffffu, ghost_ok);
 
     auto step = [&](auto fast_tag, const int T_) {
         constexpr bool FAST = decltype(fast_tag)::value;
@@ -428,8 +493,14 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                     const T v1[4] = {a1[1], a1[2], a1[3], a1[4]};
                     if (!FAST && !lane_in) continue;
                     T(&row)[4] = w[NR - 1][h];
-                    if (FAST || (std_lane && xlane + 3 < nx)) {
-                        const T q4 = T(0.25);
+                    const T q4 = T(0.25);
+                    if (FAST) {
+                        // interior pattern, with the ghost-strip weights (fma(1, p, u) = u + p)
+                        row[0] = fma_t(pm, bilinear<T>(v0[1], v0[0], v1[1], v1[0], wx0, wy), row[0]);
+                        row[1] = fma_t(pm, bilinear<T>(v0[1], v0[2], v1[1], v1[2], q4, wy), row[1]);
+                        row[2] = fma_t(pm, bilinear<T>(v0[2], v0[1], v1[2], v1[1], q4, wy), row[2]);
+                        row[3] = fma_t(pm, bilinear<T>(v0[2], v0[3], v1[2], v1[3], wx3, wy), row[3]);
+                    } else if (std_lane && xlane + 3 < nx) {
                         row[0] = row[0] + bilinear<T>(v0[1], v0[0], v1[1], v1[0], q4, wy);
                         row[1] = row[1] + bilinear<T>(v0[1], v0[2], v1[1], v1[2], q4, wy);
                         row[2] = row[2] + bilinear<T>(v0[2], v0[1], v1[2], v1[1], q4, wy);
@@ -471,17 +542,17 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                 const bool ir0 = FAST || interior_row(r0, ny, k), ir1 = FAST || interior_row(r1, ny, k);
                 // warp-uniform: in a strip with edge lanes every lane reads its cached stencil
                 // (an interior lane's cached stencil is the interior one), so no lane diverges
-                const bool fast = FAST || (x_fast && ir0 && ir1);
-                sweep_row<T, FAST>(p0, b0, north, p1, f0, x0, x0, fast, ir0, coef_s, tab, xlane, r0, nx, ny, L.n0x,
-                                   L.n0y, k, alpha, sk);
+                const bool fast = FAST || (x_ghost && ir0 && ir1);
+                sweep_row<T, FAST>(p0, b0, north, p1, f0, x0, x0, fast, ir0, coef_s, tab, g, xlane, r0, nx, ny,
+                                   L.n0x, L.n0y, k, alpha, sk);
                 if (FAST || r1 < ny)
-                    sweep_row<T, FAST>(p1, b1, p0, south, f0 ^ 1, x1, x1, fast, ir1, coef_s, tab, xlane, r1, nx, ny,
-                                       L.n0x, L.n0y, k, alpha, sk);
+                    sweep_row<T, FAST>(p1, b1, p0, south, f0 ^ 1, x1, x1, fast, ir1, coef_s, tab, g, xlane, r1, nx,
+                                       ny, L.n0x, L.n0y, k, alpha, sk);
             }
             // output of the pair that completed all half-sweeps
             {
                 const int m = T_ - S;
-                if (interior_lane && (FAST || (m >= P0 && m < P1 && lane_in))) {
+                if (interior_lane && lane_in && (FAST || (m >= P0 && m < P1))) {
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int r = 2 * m + h;
@@ -515,14 +586,14 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                     load_b(bq, 0, b0);
                     load_b(bq, 1, b1);
                     const bool ir0 = FAST || interior_row(r0, ny, k), ir1 = FAST || interior_row(r1, ny, k);
-                    const bool fast = FAST || (x_fast && ir0 && ir1);
+                    const bool fast = FAST || (x_ghost && ir0 && ir1);
                     T res0[4], res1[4] = {T(0), T(0), T(0), T(0)};
-                    residual_row<T, FAST>(res0, q0, b0, w[0][1], q1, w0, e0, fast, ir0, coef_s, tab, xlane, r0, nx,
-                                          ny, L.n0x, L.n0y, k, alpha, sk);
+                    residual_row<T, FAST>(res0, q0, b0, w[0][1], q1, w0, e0, fast, ir0, coef_s, tab, g, xlane, r0,
+                                          nx, ny, L.n0x, L.n0y, k, alpha, sk);
                     const bool has_r1 = FAST || r1 < ny;
                     if (has_r1)
-                        residual_row<T, FAST>(res1, q1, b1, q0, w[2][0], w1, e1, fast, ir1, coef_s, tab, xlane, r1,
-                                              nx, ny, L.n0x, L.n0y, k, alpha, sk);
+                        residual_row<T, FAST>(res1, q1, b1, q0, w[2][0], w1, e1, fast, ir1, coef_s, tab, g, xlane,
+                                              r1, nx, ny, L.n0x, L.n0y, k, alpha, sk);
                     // same summation order as the reference restriction: (((0 + r00) + r01) + r10) + r11
                     T c0 = T(0), c1 = T(0);
                     if (FAST || xlane + 0 < nx) c0 = c0 + res0[0];
@@ -565,7 +636,7 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
         const int rlo = 2 * (T_ - S - (UP ? 0 : 1)), rhi = 2 * T_ - 1;
         const bool steady = T_ >= P0 + S + (UP ? 0 : 1) && 2 * (T_ - S) + 1 < Y1 && T_ - S < P1 &&
                             (!UP || 2 * T_ + 1 < ny);
-        if (x_fast && steady && interior_row(rlo, ny, k) && interior_row(rhi, ny, k))
+        if (x_ghost && steady && interior_row(rlo, ny, k) && interior_row(rhi, ny, k))
             step(std::true_type{}, T_);
         else
             step(std::false_type{}, T_);
