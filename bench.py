@@ -128,6 +128,31 @@ def cpu_oracle_sample(I0_cpu, alpha, planes=8):
                                       f"voxels/s = 1 / (smoothing s/voxel + solve s/voxel)")
 
 
+def oracle_slice_errors(out, I0, alpha, slices, s_oracle=None):
+    """max |f - f_oracle| and relative L2 error on sampled slices of a corrected stack, against
+    the CPU FP64 oracle (smoothing of the slice's floor(3 sigma_z) neighbourhood, then its DCT
+    solve); the worst over the slices.  s_oracle caches the oracle's smoothed slices."""
+    import numpy as np
+    from oracle import emfuse_oracle as O
+    nz = I0.shape[0]
+    worst_abs, worst_l2 = 0.0, 0.0
+    for j in slices:
+        if s_oracle is not None and j in s_oracle:
+            s, o = s_oracle[j]
+        else:
+            a, b = max(0, j - 9), min(nz, j + 10)
+            slab = I0[a:b].double().cpu().numpy()
+            s, o = O.smooth_stack(slab, 1.0, 3.0)[j - a], slab[j - a]
+            if s_oracle is not None:
+                s_oracle[j] = (s, o)
+        ref = O.solve_dct(s, o, alpha)
+        d = out[j].double().cpu().numpy() - ref
+        worst_abs = max(worst_abs, float(np.max(np.abs(d))))
+        worst_l2 = max(worst_l2, float(np.linalg.norm(d) / np.linalg.norm(ref)))
+    return {"slices": list(slices), "max_abs_err": worst_abs, "rel_to_255": worst_abs / 255.0,
+            "rel_l2_err": worst_l2}
+
+
 def make_input(device, nz=NZ):
     import torch
     from paper_1506_02079_gb300.synthetic import make_stack
@@ -190,6 +215,27 @@ def batched_extra(dev, alpha, steps=3):
         res[label] = {"value": px / (ms * 1e-3), "unit": "pixels/s", "ms": ms,
                       "vcycles": max(a["vcycles"] for a in st),
                       "max_rel_residual": max(a["rel_residual"] for a in st)}
+    # errors against the oracle on the smallest, the median and the largest slice, and the
+    # reported residual against its plain FP64 recomputation on every slice
+    import numpy as np
+    from oracle import emfuse_oracle as O
+    vopts = api.default_opts(tol=1e-6, autotune=1, verify_residual=1)
+    _, st = api.emfuse_screened_poisson(s, o, alpha, vopts, nx=nx, ny=ny, offsets=offs, out=f, return_stats=True)
+    order = np.argsort(ny * nx, kind="stable")
+    worst_abs, worst_l2 = 0.0, 0.0
+    for i in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        a, h, w = int(offs[i]), int(ny[i]), int(nx[i])
+        sl = lambda t: t[a:a + h * w].view(h, w).double().cpu().numpy()
+        ref = O.solve_dct(sl(s), sl(o), alpha)
+        d = sl(f) - ref
+        worst_abs = max(worst_abs, float(np.abs(d).max()))
+        worst_l2 = max(worst_l2, float(np.linalg.norm(d) / np.linalg.norm(ref)))
+    res["oracle_error"] = {"slices": "smallest, median, largest", "max_abs_err": worst_abs,
+                           "rel_to_255": worst_abs / 255.0, "rel_l2_err": worst_l2}
+    res["residual_check"] = {"max_rel_residual_fp64_recomputed": max(a["rel_residual_check"] for a in st),
+                             "max_rel_diff_reported_vs_recomputed":
+                                 max(abs(a["rel_residual"] - a["rel_residual_check"]) / a["rel_residual_check"]
+                                     for a in st if a["rel_residual_check"] > 0)}
     del s, o, f
     torch.cuda.empty_cache()
     return res
@@ -346,7 +392,19 @@ def run_gpu(args):
         # value above carries no instrumentation)
         prof = profile_steps(step, args.steps)
         extras["kernels"] = prof
-        roof = kernel_roofline(prof)
+        # the FP64 roofline denominator: FP64 FMA throughput measured on this GPU (CUDA events),
+        # with the clocks seen meanwhile
+        with ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0) as clk64:
+            rates = [api.emfuse_probe_fp64_fma_rate(dev) for _ in range(5)]
+        fp64_peak = statistics.median(rates)
+        roof = kernel_roofline(prof, fp64_peak)
+        roof["fp64_probe"] = {"tflops_median": fp64_peak, "tflops_all": rates, "clocks": clk64.summary()}
+        top = next((p for p in prof if p["name"] == roof["kernel"]), None)
+        if top and roof["bound"] == "alu":
+            # the same kernel against HBM at the survey's 40 B per cell and FP64 pass
+            cells = voxels
+            roof["hbm_frac_at_40B_per_cell"] = (cells * 40.0 / (top["ms_per_step"] / max(top["launches"], 1) * 1e-3)
+                                                / 1e9 / measured_hbm_peak()[0])
         extras["roofline_relaxation"] = relaxation_roofline(prof)
         # whole-step effective HBM fraction: voxels/s times the bytes per voxel the method must
         # move (input 4 + output 4 + first residual 12 + 16 per V-cycle + 40 per FP64 correction
@@ -397,9 +455,12 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1) / n64
+        s_cache = {}
+        sample = (args.nz // 2, args.nz - 1)
         extras["fp64_plain_solve"] = {"value": voxels / (ms64 * 1e-3), "unit": "voxels/s", "ms_per_step": ms64,
                                       "vcycles": max(s["vcycles"] for s in st64),
-                                      "max_rel_residual": max(s["rel_residual"] for s in st64)}
+                                      "max_rel_residual": max(s["rel_residual"] for s in st64),
+                                      "oracle_error": oracle_slice_errors(out, I0, args.alpha, sample, s_cache)}
         extras["mixed_over_fp64"] = (voxels / (ms * 1e-3)) / extras["fp64_plain_solve"]["value"]
         # the other screening weights of the configuration
         per_alpha = {}
@@ -412,7 +473,8 @@ def run_gpu(args):
             e1.record(stream)
             torch.cuda.synchronize()
             per_alpha[str(a)] = {"ms": e0.elapsed_time(e1), "vcycles": max(s["vcycles"] for s in sa),
-                                 "max_rel_residual": max(s["rel_residual"] for s in sa)}
+                                 "max_rel_residual": max(s["rel_residual"] for s in sa),
+                                 "oracle_error": oracle_slice_errors(out, I0, a, sample, s_cache)}
         extras["per_alpha"] = per_alpha
         extras["batched_512"] = batched_extra(dev, args.alpha)
         # the first "next" row: smoothing with robust averaging across slices, against the
@@ -500,15 +562,17 @@ def run_gpu(args):
         del outs
         api.emfuse_release_cache()
         torch.cuda.empty_cache()
-        # parity on a sampled slice of the timed output vs the CPU FP64 oracle
-        from oracle import emfuse_oracle as O
-        api.emfuse_correct_stack(I0, 1.0, 3.0, args.alpha, opts, out=out)
-        j = args.nz // 2
-        slab = I0[j - 9:j + 10].double().cpu().numpy()
-        s = O.smooth_stack(slab, 1.0, 3.0)
-        ref = O.solve_dct(s[9], slab[9], args.alpha)
-        err = float(np.max(np.abs(out[j].double().cpu().numpy() - ref)))
-        extras["parity_sampled_slice"] = {"slice": j, "max_abs_err": err, "rel_to_255": err / 255.0}
+        # parity of the timed configuration vs the CPU FP64 oracle on sampled slices (the middle
+        # of the stack and its last slice, whose z-window is cut by the stack end), and the
+        # reported residual against its plain FP64 recomputation on every slice
+        vopts = api.default_opts(tol=1e-6, precision=api.PREC_MIXED, verify_residual=1)
+        _, stv = api.emfuse_correct_stack(I0, 1.0, 3.0, args.alpha, vopts, out=out, return_stats=True)
+        extras["parity_sampled_slices"] = oracle_slice_errors(out, I0, args.alpha, sample, s_cache)
+        extras["residual_check"] = {
+            "max_rel_residual_reported": max(a["rel_residual"] for a in stv),
+            "max_rel_residual_fp64_recomputed": max(a["rel_residual_check"] for a in stv),
+            "max_rel_diff_reported_vs_recomputed": max(abs(a["rel_residual"] - a["rel_residual_check"])
+                                                       / a["rel_residual_check"] for a in stv)}
         cpu = None
         if not args.no_cpu_baseline:
             v, dt, sample = cpu_oracle_sample(I0.cpu(), args.alpha, planes=12)

@@ -28,9 +28,13 @@
  *   - Errors: every call returns an emfuse_status; it never aborts.  On error a message is
  *     available from emfuse_last_error() (per host thread).  Invalid arguments are
  *     detected before any work is queued.
- *   - Solves (screened_poisson, correct_stack, backward) block the calling host thread:
- *     the host reads per-slice residual norms between V-cycles to decide convergence.
- *     Outputs are complete when the call returns.
+ *   - Solves (screened_poisson, fuse_color, correct_stack, backward): the whole outer loop
+ *     of the solve (residual, convergence check, V-cycle, ...) runs on the device, as one
+ *     CUDA graph whose loop is a conditional WHILE node (a per-slice check kernel decides
+ *     after every residual pass).  By default the call then waits for the stream and returns
+ *     the outcome (EMFUSE_OK / EMFUSE_ENOCONV ...) with outputs and stats complete; with
+ *     opts.async_solve = 1 it returns at once and stats are valid after a stream
+ *     synchronisation (see emfuse_solve_opts).
  */
 #ifndef EMFUSE_H
 #define EMFUSE_H
@@ -104,6 +108,22 @@ typedef struct {
                             iterate and report it in stats.rel_residual_check: a check of
                             the reported rel_residual, whose kernel rounds A d to FP32 and
                             sums squares in FP32 per warp.  One extra pass.  Default 0.   */
+    int async_solve;     /* 1: the solve is only queued on `stream` and the call returns at
+                            once (emfuse_screened_poisson, emfuse_fuse_color,
+                            emfuse_correct_stack on device buffers; ignored by the host-
+                            buffer path and emfuse_backward, which complete): stats are
+                            written by a stream callback and valid once the stream has
+                            reached this point (after a stream or event synchronisation);
+                            the return value reports argument and launch errors only, the
+                            outcome is stats[j].converged (0 for a slice that missed tol or
+                            had a non-finite residual).  Needs the graph path (fused = 1,
+                            no_graphs = 0); otherwise, and while the library records
+                            per-launch events, the call completes before it returns, as
+                            with 0.  Default 0.                                           */
+    int host_chunk;      /* emfuse_correct_stack with host buffers: slices per chunk of the
+                            copy / compute pipeline; 0 = chosen (four chunks when the whole
+                            input fits on the device, else as many slices as memory allows,
+                            at most 64).  Default 0.                                      */
 } emfuse_solve_opts;
 
 /* Per-slice result of a solve. */
@@ -274,12 +294,15 @@ int emfuse_fuse_color(const float* s_rgb, const float* o_grey, float* f_rgb, int
  *   out       I2, float32, same shape.
  *   in_is_host  0: `in` and `out` are device pointers.
  *               1: `in` and `out` are HOST pointers (page-locked memory is strongly
- *                  recommended); copies overlap compute on side streams.  When the input and
- *                  its smoothed copy fit on the device, the input is copied whole, smoothed in
- *                  two z-chunks and solved in chunks whose results are copied back while the
- *                  next solves; otherwise the stack streams through in z-slabs with
- *                  floor(3 sigma_z) halo planes, so stacks larger than device memory are
- *                  supported (opts->host_pipeline chooses explicitly).
+ *                  recommended); copies overlap compute on side streams, and the call returns
+ *                  when `out` is written.  When the input and its smoothed copy fit on the
+ *                  device, the input arrives in pieces, and each chunk of slices (four chunks
+ *                  unless opts->host_chunk says otherwise) is smoothed and solved as soon as
+ *                  its planes are there, its solve queued without the host waiting, and its
+ *                  result copied back while the next chunks compute; otherwise the stack
+ *                  streams through in z-slabs with floor(3 sigma_z) halo planes, so stacks
+ *                  larger than device memory are supported (opts->host_pipeline chooses
+ *                  explicitly).  The result equals the device path's bit for bit.
  *   stats     NULL or a HOST array of nz entries.
  */
 int emfuse_correct_stack(const void* in, int dt, int in_is_host, float* out, int64_t nx,

@@ -23,7 +23,7 @@ __all__ = [
     "emfuse_autotune_result", "TuneEntry", "emfuse_fuse_color", "emfuse_screened_poisson_dct",
     "emfuse_smooth_gradient_domain", "emfuse_correct_stack",
     "emfuse_backward", "emfuse_version", "emfuse_release_cache", "emfuse_kernel_binary_version",
-    "emfuse_probe_fp64_fma_rate", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
+    "emfuse_probe_fp64_fma_rate", "PendingStats", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
     "PREC_FP64", "EXPORTED_SYMBOLS",
 ]
 
@@ -56,7 +56,7 @@ class SolveOpts(ctypes.Structure):
                 ("nu_post", ctypes.c_int), ("precision", ctypes.c_int), ("fused", ctypes.c_int),
                 ("first_vcycles", ctypes.c_int), ("tile_rows", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("no_graphs", ctypes.c_int), ("robust_kappa", ctypes.c_float), ("host_pipeline", ctypes.c_int),
-                ("verify_residual", ctypes.c_int)]
+                ("verify_residual", ctypes.c_int), ("async_solve", ctypes.c_int), ("host_chunk", ctypes.c_int)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -189,6 +189,27 @@ def _require_cuda(*ts):
             raise ValueError("expected a contiguous tensor")
 
 
+class PendingStats:
+    """Per-slice results of an asynchronous solve (opts.async_solve = 1).  The library writes
+    them from a stream callback; ``result()`` waits for the stream to pass the solve and returns
+    them.  Holds the array the callback writes into until then."""
+
+    def __init__(self, arr, stream_ptr: int, device: torch.device):
+        self._arr = arr
+        # an event recorded right after the call on the stream it was queued on (the current
+        # PyTorch stream, the default stream included) completes after the stream callback
+        self._done = torch.cuda.Event()
+        self._done.record(torch.cuda.current_stream(device))
+
+    def result(self) -> list[dict]:
+        self._done.synchronize()
+        return _stats_list(self._arr)
+
+
+def _is_async(opts) -> bool:
+    return opts is not None and bool(getattr(opts, "async_solve", 0))
+
+
 def _stats_list(arr) -> list[dict]:
     return [{"vcycles": s.vcycles, "converged": bool(s.converged), "rel_residual": s.rel_residual,
              "b_norm": s.b_norm, "rel_residual_check": s.rel_residual_check} for s in arr]
@@ -296,16 +317,22 @@ def emfuse_screened_poisson(s, o, alpha: float, opts: SolveOpts | None = None, *
     _require_cuda(f)
     n = len(nxs)
     stats = (SliceStats * n)()
+    asynchronous = _is_async(opts)
+    # an asynchronous solve writes stats later, from a stream callback: only when they are
+    # returned (PendingStats keeps the array alive until then)
+    want_stats = return_stats or not asynchronous
     code = lib().emfuse_screened_poisson(
         sp.data_ptr(), op.data_ptr(), f.data_ptr(), n, nxs.ctypes.data, nys.ctypes.data,
         offs.ctypes.data, float(alpha), ctypes.byref(opts) if opts is not None else None,
-        ctypes.addressof(stats), _stream_ptr(sp.device))
+        ctypes.addressof(stats) if want_stats else None, _stream_ptr(sp.device))
     _check(code, allow_noconv)
     if shapes not in (None, "packed"):
         f = [f[int(a):int(a) + h * w].view(h, w) for a, (h, w) in zip(offs, shapes)]
     elif isinstance(s, torch.Tensor) and s.dim() == 2 and nx is None:
         f = f[0]
-    return (f, _stats_list(stats)) if return_stats else f
+    if not return_stats:
+        return f
+    return (f, PendingStats(stats, _stream_ptr(sp.device), sp.device)) if asynchronous else (f, _stats_list(stats))
 
 
 def emfuse_screened_poisson_dct(s: torch.Tensor, o: torch.Tensor, alpha: float, precision: int = PREC_FP64,
@@ -359,11 +386,16 @@ def emfuse_fuse_color(s_rgb: torch.Tensor, o_grey: torch.Tensor, alpha: float, o
         raise TypeError("s_rgb and o_grey must be float32")
     f = torch.empty_like(s4)
     stats = (SliceStats * (3 * n))()
+    asynchronous = _is_async(opts)
+    want_stats = return_stats or not asynchronous
     _check(lib().emfuse_fuse_color(s4.data_ptr(), o3.data_ptr(), f.data_ptr(), n, nx, ny, float(alpha),
-                                   ctypes.byref(opts) if opts is not None else None, ctypes.addressof(stats),
+                                   ctypes.byref(opts) if opts is not None else None,
+                                   ctypes.addressof(stats) if want_stats else None,
                                    _stream_ptr(s4.device)), allow_noconv)
     f = f[0] if single else f
-    return (f, _stats_list(stats)) if return_stats else f
+    if not return_stats:
+        return f
+    return (f, PendingStats(stats, _stream_ptr(s4.device), s4.device)) if asynchronous else (f, _stats_list(stats))
 
 
 def emfuse_correct_stack(stack: torch.Tensor, sigma_xy: float = 1.0, sigma_z: float = 3.0,
@@ -384,12 +416,17 @@ def emfuse_correct_stack(stack: torch.Tensor, sigma_xy: float = 1.0, sigma_z: fl
         raise ValueError("out must live where the stack lives")
     dev = stack.device if stack.is_cuda else torch.device("cuda", torch.cuda.current_device() if device is None else device)
     stats = (SliceStats * nz)()
+    asynchronous = _is_async(opts) and not on_host  # host buffers: the call always completes
+    want_stats = return_stats or not asynchronous
     code = lib().emfuse_correct_stack(
         stack.data_ptr(), _dtype_code(stack), int(on_host), out.data_ptr(), nx, ny, nz,
         float(sigma_xy), float(sigma_z), float(alpha),
-        ctypes.byref(opts) if opts is not None else None, ctypes.addressof(stats), _stream_ptr(dev))
+        ctypes.byref(opts) if opts is not None else None, ctypes.addressof(stats) if want_stats else None,
+        _stream_ptr(dev))
     _check(code, allow_noconv)
-    return (out, _stats_list(stats)) if return_stats else out
+    if not return_stats:
+        return out
+    return (out, PendingStats(stats, _stream_ptr(dev), dev)) if asynchronous else (out, _stats_list(stats))
 
 
 def emfuse_backward(grad_f: torch.Tensor, f: torch.Tensor | None, s: torch.Tensor | None,

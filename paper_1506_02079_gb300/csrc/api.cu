@@ -40,6 +40,8 @@ static int resolve_opts(const emfuse_solve_opts* in, emfuse_solve_opts* out) {
     if (out->no_graphs != 0 && out->no_graphs != 1) return einval("opts.no_graphs must be 0 or 1");
     if (out->host_pipeline < 0 || out->host_pipeline > 2) return einval("opts.host_pipeline must be 0, 1 or 2");
     if (out->verify_residual != 0 && out->verify_residual != 1) return einval("opts.verify_residual must be 0 or 1");
+    if (out->async_solve != 0 && out->async_solve != 1) return einval("opts.async_solve must be 0 or 1");
+    if (out->host_chunk < 0) return einval("opts.host_chunk must be >= 0");
     if (!(out->robust_kappa == 0.f || (out->robust_kappa >= 1.f && std::isfinite(out->robust_kappa))))
         return einval("opts.robust_kappa must be 0 (plain averaging) or finite and >= 1");
     return EMFUSE_OK;
@@ -89,53 +91,62 @@ static int solve_stack(const float* s, const void* o, int dt, float* out, int64_
 
 
 // Host-resident stack whose input and smoothed copy fit on the device together with the
-// solver's chunk workspace.  The smoothing then runs in large z-chunks (two, or one) reading
-// the resident input, so the x/y blur of the floor(3 sigma_z) halo planes is redone only at the
-// one chunk boundary, while the solves run in chunks of C slices sized by memory:
+// solvers' chunk workspaces.  Everything is queued without waiting on the host, and the call
+// synchronises once at the end:
 //   copy-in  (side stream): the input in pieces, piece k ending at the last plane smoothing
-//            chunk k reads, each with an event (the first chunk starts before the rest arrives);
-//   compute  (the caller's stream): smoothing of a z-chunk once the input it reads has arrived,
-//            then the solves of the slices it covers, into output buffer i mod 2;
-//   copy-out (side stream): output buffer i mod 2 to the host.
+//            chunk k reads, each with an event;
+//   compute  (the caller's stream): smoothing of a chunk of C slices once its input has
+//            arrived (the first chunk's input is small, so compute starts early), and its solve,
+//            queued asynchronously (the solve's outer loop runs on the device, so the host never
+//            waits between chunks), into an output buffer of a ring of four;
+//   copy-out (side stream): each chunk's output to the host as soon as its solve is done.
+// A slice's result does not depend on the batch it is solved in, so the output equals the
+// device path's bit for bit.  The per-slice stats of the chunks give the outcome.
 static int correct_stack_resident(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
                                   float sigma_xy, float sigma_z, double alpha, const emfuse_solve_opts& o2,
                                   emfuse_slice_stats* stats, cudaStream_t st, int64_t C) {
     const int64_t R = support_radius(sigma_z);
     const int64_t plane = nx * ny;
     const size_t esz = dtype_size(dt);
-    const int64_t ns = nz >= 2 ? 2 : 1;       // smoothing chunks (and input pieces)
-    const int64_t Cs = (nz + ns - 1) / ns;
-    const int64_t nchunks = (nz + C - 1) / C;  // solve chunks
-    DeviceBuffer din, ds, dout[2];
+    const int64_t nchunks = (nz + C - 1) / C;            // solve chunks
+    const int64_t Cs = C;                                // smoothing chunks: one per solve chunk
+    const int64_t ns = (nz + Cs - 1) / Cs;
+    constexpr int kRing = 4;                             // chunk output buffers
+    const int nbuf = (int)std::min<int64_t>(kRing, nchunks);
+    emfuse_solve_opts o3 = o2;
+    o3.async_solve = 1;  // queued; the outcome is read from the stats after the final synchronisation
+    std::vector<emfuse_slice_stats> hst((size_t)nz);
+    DeviceBuffer din, ds, dout[kRing];
     EMF_TRY(din.alloc((size_t)(nz * plane) * esz, st));
     EMF_TRY(ds.alloc((size_t)(nz * plane) * sizeof(float), st));
-    for (int q = 0; q < 2; ++q) EMF_TRY(dout[q].alloc((size_t)(C * plane) * sizeof(float), st));
+    for (int q = 0; q < nbuf; ++q) EMF_TRY(dout[q].alloc((size_t)(C * plane) * sizeof(float), st));
     cudaStream_t s_in = nullptr, s_out = nullptr;
-    cudaEvent_t ev_alloc = nullptr, ev_piece[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
-                ev_out[2] = {nullptr, nullptr};
-    int rc_all = EMFUSE_OK;
+    cudaEvent_t ev_alloc = nullptr, ev_outq = nullptr;
+    std::vector<cudaEvent_t> ev_piece(ns, nullptr), ev_smooth(ns, nullptr), ev_comp(nchunks, nullptr),
+        ev_free(kRing, nullptr);
     auto cleanup = [&]() {
-        for (int q = 0; q < 2; ++q) {
-            if (ev_piece[q]) cudaEventDestroy(ev_piece[q]);
-            if (ev_comp[q]) cudaEventDestroy(ev_comp[q]);
-            if (ev_out[q]) cudaEventDestroy(ev_out[q]);
-        }
-        if (ev_alloc) cudaEventDestroy(ev_alloc);
+        for (auto* v : {&ev_piece, &ev_smooth, &ev_comp, &ev_free})
+            for (auto& e : *v)
+                if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : {ev_alloc, ev_outq})
+            if (e) cudaEventDestroy(e);
         if (s_in) cudaStreamDestroy(s_in);
         if (s_out) cudaStreamDestroy(s_out);
+    };
+    auto ev = [](cudaEvent_t& e) -> int {
+        EMF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        return EMFUSE_OK;
     };
     auto body = [&]() -> int {
         EMF_CUDA(cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking));
         EMF_CUDA(cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking));
-        EMF_CUDA(cudaEventCreateWithFlags(&ev_alloc, cudaEventDisableTiming));
-        for (int q = 0; q < 2; ++q) {
-            EMF_CUDA(cudaEventCreateWithFlags(&ev_piece[q], cudaEventDisableTiming));
-            EMF_CUDA(cudaEventCreateWithFlags(&ev_comp[q], cudaEventDisableTiming));
-            EMF_CUDA(cudaEventCreateWithFlags(&ev_out[q], cudaEventDisableTiming));
-        }
+        EMF_TRY(ev(ev_alloc));
+        EMF_TRY(ev(ev_outq));
+        for (auto* v : {&ev_piece, &ev_smooth, &ev_comp, &ev_free})
+            for (auto& e : *v) EMF_TRY(ev(e));
+        // the buffers come from the caller's stream's pool: valid for the other streams after this
         EMF_CUDA(cudaEventRecord(ev_alloc, st));
-        EMF_CUDA(cudaStreamWaitEvent(s_in, ev_alloc, 0));
-        EMF_CUDA(cudaStreamWaitEvent(s_out, ev_alloc, 0));
+        for (cudaStream_t x : {s_in, s_out}) EMF_CUDA(cudaStreamWaitEvent(x, ev_alloc, 0));
         for (int64_t k = 0, have = 0; k < ns; ++k) {
             const int64_t need = std::min(nz, std::min(nz, (k + 1) * Cs) + R);  // planes [0, need) read
             if (need > have)
@@ -145,49 +156,65 @@ static int correct_stack_resident(const void* in, int dt, float* out, int64_t nx
             have = std::max(have, need);
             EMF_CUDA(cudaEventRecord(ev_piece[k], s_in));
         }
-        int64_t smoothed = 0;  // output planes [0, smoothed) are queued for smoothing
+        std::vector<char> smoothed(ns, 0);
         for (int64_t i = 0; i < nchunks; ++i) {
-            const int q = int(i & 1);
+            const cudaStream_t c = st;
+            const int q = int(i % nbuf);
             const int64_t z0 = i * C, z1 = std::min(nz, z0 + C);
-            while (smoothed < z1) {
-                const int64_t k = smoothed / Cs;
+            const int64_t k = z0 / Cs;  // chunk boundaries are multiples of C, and Cs = C
+            if (!smoothed[k]) {
                 const int64_t a = k * Cs, b = std::min(nz, a + Cs);
-                EMF_CUDA(cudaStreamWaitEvent(st, ev_piece[k], 0));  // input planes [0, b + R) arrived
+                EMF_CUDA(cudaStreamWaitEvent(c, ev_piece[k], 0));  // input planes [0, b + R) arrived
                 EMF_TRY(smooth_stack(din.as<char>(), dt, ds.as<float>() + a * plane, nx, ny, nz, nx, a, b, sigma_xy,
-                                     sigma_z, st, 0, o2.robust_kappa));
-                smoothed = b;
+                                     sigma_z, c, 0, o2.robust_kappa));
+                EMF_CUDA(cudaEventRecord(ev_smooth[k], c));
+                smoothed[k] = 1;
+            } else {
+                EMF_CUDA(cudaStreamWaitEvent(c, ev_smooth[k], 0));
             }
-            if (i >= 2) EMF_CUDA(cudaStreamWaitEvent(st, ev_out[q], 0));  // dout[q] drained
+            if (i >= nbuf) EMF_CUDA(cudaStreamWaitEvent(c, ev_free[q], 0));  // dout[q] drained
             const int rc = solve_stack(ds.as<float>() + z0 * plane, din.as<char>() + (size_t)(z0 * plane) * esz, dt,
-                                       dout[q].as<float>(), nx, ny, z1 - z0, alpha, o2, stats ? stats + z0 : nullptr,
-                                       nullptr, st);
+                                       dout[q].as<float>(), nx, ny, z1 - z0, alpha, o3, hst.data() + z0, nullptr, c);
             if (rc != EMFUSE_OK && rc != EMFUSE_ENOCONV) return rc;
-            if (rc == EMFUSE_ENOCONV) rc_all = rc;
-            EMF_CUDA(cudaEventRecord(ev_comp[q], st));
-            EMF_CUDA(cudaStreamWaitEvent(s_out, ev_comp[q], 0));
+            EMF_CUDA(cudaEventRecord(ev_comp[i], c));
+            EMF_CUDA(cudaStreamWaitEvent(s_out, ev_comp[i], 0));
             EMF_CUDA(cudaMemcpyAsync(out + z0 * plane, dout[q].as<float>(), (size_t)((z1 - z0) * plane) * sizeof(float),
                                      cudaMemcpyDeviceToHost, s_out));
-            EMF_CUDA(cudaEventRecord(ev_out[q], s_out));
+            EMF_CUDA(cudaEventRecord(ev_free[q], s_out));
         }
-        for (int q = 0; q < 2; ++q) EMF_CUDA(cudaStreamWaitEvent(st, ev_out[q], 0));
+        // the caller's stream waits for the copy streams (the buffers go back to its pool)
+        EMF_CUDA(cudaEventRecord(ev_outq, s_out));
+        EMF_CUDA(cudaStreamWaitEvent(st, ev_outq, 0));
         EMF_CUDA(cudaStreamWaitEvent(st, ev_piece[ns - 1], 0));
         return EMFUSE_OK;
     };
-    const int rc = body();
-    if (rc != EMFUSE_OK) {
-        if (s_in) cudaStreamSynchronize(s_in);
-        if (s_out) cudaStreamSynchronize(s_out);
-        cudaStreamSynchronize(st);
-        cleanup();
-        return rc;
-    }
+    int rc = body();
+    // wait for everything queued (also after a failure part-way, before the buffers are released)
+    if (s_in) cudaStreamSynchronize(s_in);
+    if (s_out) cudaStreamSynchronize(s_out);
     const cudaError_t e = cudaStreamSynchronize(st);
     cleanup();
+    if (rc != EMFUSE_OK) return rc;
     if (e != cudaSuccess) {
         set_error(std::string("emfuse_correct_stack: ") + cudaGetErrorString(e));
         return EMFUSE_ECUDA;
     }
-    return rc_all;
+    EMF_TRY(solve_async_status(st, o2.precision));
+    if (stats) std::memcpy(stats, hst.data(), hst.size() * sizeof(emfuse_slice_stats));
+    bool nonfinite = false, converged = true;
+    for (const auto& x : hst) {
+        nonfinite |= !std::isfinite(x.rel_residual);
+        converged &= x.converged != 0;
+    }
+    if (nonfinite) {
+        set_error("non-finite residual (NaN or Inf in the inputs?)");
+        return EMFUSE_EINVAL;
+    }
+    if (!converged) {
+        set_error("tolerance not reached within max_vcycles");
+        return EMFUSE_ENOCONV;
+    }
+    return EMFUSE_OK;
 }
 
 // Host-resident stack, streamed through the device in z-chunks of C output slices.  Chunk i
@@ -225,17 +252,21 @@ static int correct_stack_host(const void* in, int dt, float* out, int64_t nx, in
     // chunk costs a solve's fixed, latency-bound coarse-level time, so no more than needed);
     // equal chunk sizes (but the last) keep the solver's cached plan valid from chunk to chunk
     cmax = std::min<int64_t>({cmax, 64, std::max<int64_t>(1, (nz + 1) / 2)});
+    if (o2.host_chunk > 0) cmax = std::min<int64_t>(cmax, o2.host_chunk);
     const int64_t nchunks = (nz + cmax - 1) / cmax;
     const int64_t C = (nz + nchunks - 1) / nchunks;
-    // the whole input and its smoothed copy on the device as well: smooth in large chunks
-    const double resident = (double)(nz * plane) * (esz + 4.0) + (double)(C * plane) * (8.0 + 32.0);
+    // the resident schedule: the whole input and its smoothed copy on the device, chunks of Cr
+    // slices (four chunks unless opts.host_chunk says otherwise), the solver plan (about 48 B per
+    // pixel: pyramids and FP64 iterates) and a ring of four chunk output buffers
+    const int64_t Cr = std::min<int64_t>(nz, o2.host_chunk > 0 ? o2.host_chunk : std::max<int64_t>(1, (nz + 3) / 4));
+    const double resident = (double)(nz * plane) * (esz + 4.0) + (double)(Cr * plane) * (4.0 * 4.0 + 48.0);
     const bool fits = resident <= 0.7 * (double)free_b;
     if (o2.host_pipeline == 2 && !fits) {
         set_error("emfuse_correct_stack: the whole input and its smoothed copy do not fit on the device");
         return EMFUSE_ENOMEM;
     }
     if (o2.host_pipeline == 2 || (o2.host_pipeline == 0 && fits))
-        return correct_stack_resident(in, dt, out, nx, ny, nz, sigma_xy, sigma_z, alpha, o2, stats, st, C);
+        return correct_stack_resident(in, dt, out, nx, ny, nz, sigma_xy, sigma_z, alpha, o2, stats, st, Cr);
     const int64_t slab_cap = std::min<int64_t>(nz, C + 2 * R);
 
     DeviceBuffer din[2], dout[2], ds;
@@ -531,6 +562,7 @@ int emfuse_correct_stack(const void* in, int dt, int in_is_host, float* out, int
                              o2.robust_kappa));
         return solve_stack(sbuf.as<float>(), in, dt, out, nx, ny, nz, alpha, o2, stats, nullptr, st);
     }
+    o2.async_solve = 0;  // host buffers: the call returns when out is written
     return correct_stack_host(in, dt, out, nx, ny, nz, sigma_xy, sigma_z, alpha, o2, stats, st);
 }
 
@@ -550,6 +582,7 @@ int emfuse_backward(const float* grad_f, const float* f, const float* s, const v
     EMF_TRY(check_sigma(sigma_xy, sigma_z));
     emfuse_solve_opts o2;
     EMF_TRY(resolve_opts(opts, &o2));
+    o2.async_solve = 0;  // the gradients below need the solve's outcome
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = nx * ny * nz;
     DeviceBuffer lam;

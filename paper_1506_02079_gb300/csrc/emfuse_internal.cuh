@@ -46,6 +46,10 @@ int solve_batch(const SolveRequest& req, cudaStream_t st);
 // candidates timed by the last autotuning solve on this host thread, the chosen one first
 const std::vector<emfuse_tune_entry>& last_autotune();
 void release_plans();
+// after a synchronisation of `st`: EMFUSE_ETIMEOUT (and the error word cleared) if a bounded wait
+// of the last solve of the plan of (current device, st, precision) expired, else EMFUSE_OK; for
+// asynchronous solves, whose return value cannot report it
+int solve_async_status(cudaStream_t st, int precision);
 // bytes of the pyramids and FP64 iterates held by the cached plan of (current device, stream,
 // precision): a later solve on that stream reuses them
 size_t cached_plan_bytes(cudaStream_t st, int precision);

@@ -149,6 +149,29 @@ struct AlphaDeg {
                     // take the FP64 pipe)
 };
 
+// Device-side state of the outer loop of one solve (one per plan).  The loop (residual pass,
+// convergence check, V-cycle, residual pass, ...) is decided on the device by k_check after
+// every residual pass, so that a solve is one CUDA graph whose loop is a conditional WHILE node
+// (without graphs the same kernels are launched by a host loop that reads `cont`).
+struct SolveState {
+    int it;         // index of the next residual pass (0 = the first residual)
+    int vdone;      // V-cycles applied so far to the slices still iterating
+    int cont;       // 1 while another V-cycle and residual pass follow
+    int nonfinite;  // some slice's residual was not finite
+    int timeout;    // a bounded wait of a V-cycle kernel expired
+    int pad[3];
+};
+
+// The caller's buffers of the current call, which the residual kernels read through this
+// struct (written by k_set_call before every solve), so a captured solve graph stays valid
+// when they change.
+struct CallPtrs {
+    const float* s;
+    const void* o;
+    const float* rhs;
+    float* out;
+};
+
 constexpr int kTopTX = 64;
 constexpr int kTopTY = 16;
 
@@ -164,12 +187,22 @@ constexpr int kTopTY = 16;
 template <class TF, class TV, class To, int MODE, bool EXACT>
 __global__ void __launch_bounds__(256)
 k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, int nslices,
-      const int* __restrict__ active, const float* __restrict__ s, const To* __restrict__ o,
-      const float* __restrict__ rhs, const TF* __restrict__ d_old, TF* __restrict__ d_new,
-      float* __restrict__ out, double alpha, AlphaDeg<TF> ad, double* __restrict__ norms) {
+      const int* __restrict__ active, const CallPtrs* __restrict__ call, const SolveState* __restrict__ state,
+      TF* __restrict__ dbuf0, TF* __restrict__ dbuf1, double alpha, AlphaDeg<TF> ad,
+      double* __restrict__ norms) {
     const int64_t t = blockIdx.x;
     const int j = find_item(tile_start, nslices, t);
     if (active && !active[j]) return;
+    // the caller's buffers, and the iterate buffers of this pass: pass `it` writes buffer it & 1
+    // and reads the other (they alternate, so that a tile can read d_old on its halo while its
+    // neighbours write d_new)
+    const float* __restrict__ s = call->s;
+    const To* __restrict__ o = static_cast<const To*>(call->o);
+    const float* __restrict__ rhs = call->rhs;
+    float* __restrict__ out = call->out;
+    const int it = state->it;
+    const TF* __restrict__ d_old = (it & 1) ? dbuf0 : dbuf1;
+    TF* __restrict__ d_new = (it & 1) ? dbuf1 : dbuf0;
     const TopSlice G = top[j];
     const int lt = int(t - tile_start[j]);
     const int tx0 = (lt % G.tiles_x) * kTopTX;
@@ -285,12 +318,12 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
 // per slice for the final iterate f = o + d, with every operation in FP64 (hardware
 // conversions), b = alpha s + L o formed directly (not the correction form of k_top) and the
 // squares summed in FP64 (per-block shuffle tree, one FP64 atomic per block and slice).
-// which[j] picks the iterate buffer of slice j: 0 = none (d = 0, never iterated), 1 or 2 = the
-// first or second FP64 buffer.  Neighbours are read from global memory (a one-off pass).
+// last_pass[j] is the residual pass that last wrote slice j's iterate (0: never iterated, d = 0).
+// Neighbours are read from global memory (a one-off pass).
 template <class TF, class To>
 __global__ void __launch_bounds__(256)
 k_verify(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, int nslices,
-         const int* __restrict__ which, const float* __restrict__ s, const To* __restrict__ o,
+         const int* __restrict__ last_pass, const float* __restrict__ s, const To* __restrict__ o,
          const float* __restrict__ rhs, const TF* __restrict__ d0, const TF* __restrict__ d1, double alpha,
          double* __restrict__ sums) {
     const int64_t t = blockIdx.x;
@@ -300,7 +333,9 @@ k_verify(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_star
     const int tx0 = (lt % G.tiles_x) * kTopTX;
     const int ty0 = (lt / G.tiles_x) * kTopTY;
     const int tid = threadIdx.x;
-    const TF* d = which[j] == 1 ? d0 : (which[j] == 2 ? d1 : nullptr);
+    // the iterate of slice j: written by its last residual pass p (buffer p & 1), none if p = 0
+    const int lp = last_pass[j];
+    const TF* d = lp == 0 ? nullptr : ((lp & 1) ? d1 : d0);
     auto fval = [&](int64_t q) -> double {  // f = o + d (rhs mode: f = d)
         const double dv = d ? (double)d[q] : 0.0;
         return rhs ? dv : (double)o[q] + dv;
@@ -350,12 +385,127 @@ k_verify(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_star
     }
 }
 
-// out = o (or 0 in the adjoint mode) on one slice that was never iterated (it met the
-// tolerance at the initial iterate f = o).
+// ---------------------------------------------------------------- device-side outer loop
+__global__ void k_set_call(CallPtrs* __restrict__ dst, CallPtrs v) { *dst = v; }
+
+// Start of a solve: every slice active, no V-cycle yet, norms and wavefront work counters zero.
+__global__ void k_init(SolveState* __restrict__ st, int n, int* __restrict__ done, int* __restrict__ active,
+                       int* __restrict__ vcycles, int* __restrict__ last_pass, double* __restrict__ norms,
+                       unsigned int* __restrict__ work) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        done[j] = 0;
+        active[j] = 1;
+        vcycles[j] = 0;
+        last_pass[j] = 0;
+        norms[2 * j] = 0.0;
+        norms[2 * j + 1] = 0.0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->it = 0;
+        st->vdone = 0;
+        st->cont = 0;
+        st->nonfinite = 0;
+        st->timeout = 0;
+        work[0] = 0u;
+        work[1] = 0u;
+    }
+}
+
+// Convergence check after residual pass st->it, one CTA: per slice, ||r|| / ||b|| from the
+// squared norms the pass accumulated (||b|| from pass 0); a slice at or below tol (or with a
+// non-finite residual) is done and leaves the active set.  Another V-cycle follows (cont) while
+// some slice is left, fewer than maxit V-cycles were applied and no bounded wait expired; it is
+// then counted (nv V-cycles) for the slices left.  The norms are cleared for the next pass.
+// With use_handle, the decision is also the condition of the solve graph's WHILE node: it is
+// set on every call, and cont is 0 once maxit V-cycles are done, so the loop ends.
+__global__ void __launch_bounds__(256)
+k_check(SolveState* __restrict__ st, int n, double* __restrict__ norms, double* __restrict__ bnorm,
+        double* __restrict__ rel, int* __restrict__ done, int* __restrict__ active, int* __restrict__ vcycles,
+        int* __restrict__ last_pass, double tol, int maxit, int nv, const int* __restrict__ err, int use_handle,
+        cudaGraphConditionalHandle h) {
+    __shared__ int s_left, s_nonfinite;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_left = 0;
+        s_nonfinite = 0;
+    }
+    __syncthreads();
+    const int it = st->it;
+    int left = 0, nonfinite = 0;
+    for (int j = tid; j < n; j += blockDim.x) {
+        if (done[j]) continue;
+        last_pass[j] = it;
+        if (it == 0) bnorm[j] = sqrt(norms[2 * j + 1]);
+        const double rn = sqrt(norms[2 * j]);
+        const double b = bnorm[j];
+        const double r = b > 0.0 ? rn / b : rn;
+        rel[j] = r;
+        if (r <= tol || !isfinite(r)) {
+            done[j] = 1;
+            active[j] = 0;
+            nonfinite += !isfinite(r);
+        } else {
+            ++left;
+        }
+    }
+    if (left) atomicAdd(&s_left, left);
+    if (nonfinite) atomicAdd(&s_nonfinite, nonfinite);
+    __syncthreads();
+    const int timeout = *err != 0;
+    const int cont = (s_left > 0 && st->vdone < maxit && !timeout && it <= maxit + 1) ? 1 : 0;
+    __syncthreads();  // every thread has read st before thread 0 updates it
+    for (int j = tid; j < n; j += blockDim.x) {
+        norms[2 * j] = 0.0;
+        norms[2 * j + 1] = 0.0;
+        if (cont && !done[j]) vcycles[j] += nv;
+    }
+    if (tid == 0) {
+        st->it = it + 1;
+        if (cont) st->vdone += nv;
+        st->cont = cont;
+        if (s_nonfinite) st->nonfinite = 1;
+        if (timeout) st->timeout = 1;
+        if (use_handle) cudaGraphSetConditional(h, cont ? 1u : 0u);
+    }
+}
+
+// out = o (or 0 in the adjoint mode) on the slices that were never iterated (they met the
+// tolerance at the initial iterate f = o): kFinishBlocks CTAs per slice, which return at once
+// for the slices that were iterated.
+constexpr int kFinishBlocks = 8;
 template <class To>
-__global__ void k_fill_initial(const To* __restrict__ o, float* __restrict__ out, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = o ? float(o[i]) : 0.f;
+__global__ void __launch_bounds__(256)
+k_finish(const TopSlice* __restrict__ top, const int* __restrict__ vcycles, const CallPtrs* __restrict__ call) {
+    const int j = blockIdx.x / kFinishBlocks;
+    if (vcycles[j] != 0) return;
+    const TopSlice G = top[j];
+    const To* o = static_cast<const To*>(call->o);
+    const bool zero = call->rhs != nullptr;
+    const int64_t cells = (int64_t)G.nx * G.ny;
+    for (int64_t q = (int64_t)(blockIdx.x % kFinishBlocks) * blockDim.x + threadIdx.x; q < cells;
+         q += (int64_t)kFinishBlocks * blockDim.x)
+        call->out[G.off + q] = zero ? 0.f : float(o[G.off + q]);
+}
+
+// Per-slice results of a solve in the layout of emfuse_slice_stats (vsums: the squared norms of
+// the verification pass, or null).
+__global__ void k_stats(int n, const int* __restrict__ vcycles, const double* __restrict__ rel,
+                        const double* __restrict__ bnorm, const double* __restrict__ vsums, double tol,
+                        emfuse_slice_stats* __restrict__ out) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        emfuse_slice_stats r;
+        r.vcycles = vcycles[j];
+        r.rel_residual = rel[j];
+        r.b_norm = bnorm[j];
+        r.converged = rel[j] <= tol ? 1 : 0;
+        if (vsums) {
+            const double rn = sqrt(vsums[2 * j]), bn = sqrt(vsums[2 * j + 1]);
+            r.rel_residual_check = bn > 0.0 ? rn / bn : rn;
+        } else {
+            r.rel_residual_check = -1.0;
+        }
+        out[j] = r;
+    }
 }
 
 // A workspace larger than the device's whole memory can never be allocated: such a request
@@ -420,13 +570,13 @@ struct Solver {
     const SolveRequest* rq = nullptr;  // the call being served
     cudaStream_t st;
     std::vector<LevelPlan<TV>> levels;
-    DeviceBuffer ws_levels, ws_desc, ws_f, ws_norms, ws_active;
+    DeviceBuffer ws_levels, ws_desc, ws_f, ws_norms, ws_active, ws_loop;
     std::vector<int> nlev, kc;
     int Kmax = 0, Kw = 0;       // levels, and levels with wavefront work
     TF* dbuf[2] = {nullptr, nullptr};  // FP64 iterates d, alternating between passes
     double* d_norms = nullptr;
     int* d_active = nullptr;
-    int* d_err = nullptr;
+    int* d_err = nullptr;            // this plan's error word (bounded waits of its V-cycle kernels)
     unsigned int* d_work = nullptr;  // wavefront work counters (reset by each launch's last warp)
     TopSlice* d_top = nullptr;
     int64_t* d_top_ts = nullptr;
@@ -436,23 +586,47 @@ struct Solver {
     double tail_cells = 0;
     bool fused = true;
 
-    // V-cycles replayed as CUDA graphs, one per starting mode (from zero / continuing),
-    // captured on a private stream for the alpha they were captured with
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    int64_t gnodes[2] = {0, 0};
-    double galpha[2] = {0.0, 0.0};
-    cudaStream_t cap_st = nullptr;
+    // device-side outer loop (ws_loop): state, the caller's buffers, per-slice arrays, results
+    SolveState* d_state = nullptr;
+    CallPtrs* d_call = nullptr;
+    int *d_done = nullptr, *d_vcyc = nullptr, *d_lastp = nullptr;
+    double *d_bnorm = nullptr, *d_rel = nullptr, *d_vsums = nullptr;
+    emfuse_slice_stats* d_stats = nullptr;
+    // page-locked host copies of the results (read after a synchronisation, or by the stream
+    // callback of an asynchronous solve)
+    emfuse_slice_stats* h_stats = nullptr;
+    SolveState* h_state = nullptr;
+    cudaEvent_t async_done = nullptr;  // recorded after the last asynchronous solve's callback
+
+    // The whole solve as one CUDA graph with a WHILE node (see solve_graph), captured on private
+    // streams and replayed on the caller's; rebuilt when one of the values it bakes in changes.
+    cudaGraphExec_t sexec = nullptr;
+    std::vector<double> skey;
+    int64_t s_pro_nodes = 0, s_body_nodes = 0;  // kernel nodes outside / inside the loop
+    int s_pro_passes = 0;                       // residual passes outside the loop
+    cudaStream_t cap_st = nullptr, cap_body = nullptr;
 
     explicit Solver(cudaStream_t s) : st(s) {}
     ~Solver() {
+        if (async_done) {  // the stream callback of an asynchronous solve reads h_stats / h_state
+            cudaEventSynchronize(async_done);
+            cudaEventDestroy(async_done);
+        }
         drop_graphs();
         if (cap_st) cudaStreamDestroy(cap_st);
+        if (cap_body) cudaStreamDestroy(cap_body);
+        free_host();
     }
     void drop_graphs() {
-        for (int q = 0; q < 2; ++q) {
-            if (gexec[q]) cudaGraphExecDestroy(gexec[q]);
-            gexec[q] = nullptr;
-        }
+        if (sexec) cudaGraphExecDestroy(sexec);
+        sexec = nullptr;
+        skey.clear();
+    }
+    void free_host() {
+        if (h_stats) cudaFreeHost(h_stats);
+        if (h_state) cudaFreeHost(h_state);
+        h_stats = nullptr;
+        h_state = nullptr;
     }
 
     // What the plan depends on: the slice geometry and the schedule options.
@@ -478,6 +652,9 @@ struct Solver {
         ws_desc.release();
         ws_norms.release();
         ws_active.release();
+        ws_loop.release();
+        if (async_done) cudaEventSynchronize(async_done);
+        free_host();
         nlev.clear();
         kc.clear();
         Kmax = Kw = 0;
@@ -659,10 +836,26 @@ struct Solver {
         d_active = ws_active.as<int>();
         d_work = reinterpret_cast<unsigned int*>(d_active + n);
         EMF_CUDA(cudaMemsetAsync(d_work, 0, 2 * sizeof(unsigned int), st));
-        d_err = device_error_flag();
-        if (!d_err) {
-            set_error("could not allocate the device error word");
-            return EMFUSE_ECUDA;
+        {
+            // loop state, call buffers and this plan's error word, then the per-slice arrays
+            const size_t head = 256, ints = round_up(n * sizeof(int), 256), dbls = round_up(n * sizeof(double), 256);
+            const size_t stats = round_up(n * sizeof(emfuse_slice_stats), 256);
+            EMF_TRY(ws_loop.alloc_persistent(head + 3 * ints + 4 * dbls + stats));
+            char* q = ws_loop.as<char>();
+            d_state = reinterpret_cast<SolveState*>(q);
+            d_call = reinterpret_cast<CallPtrs*>(q + 64);
+            d_err = reinterpret_cast<int*>(q + 128);
+            q += head;
+            d_done = reinterpret_cast<int*>(q); q += ints;
+            d_vcyc = reinterpret_cast<int*>(q); q += ints;
+            d_lastp = reinterpret_cast<int*>(q); q += ints;
+            d_bnorm = reinterpret_cast<double*>(q); q += dbls;
+            d_rel = reinterpret_cast<double*>(q); q += dbls;
+            d_vsums = reinterpret_cast<double*>(q); q += 2 * dbls;
+            d_stats = reinterpret_cast<emfuse_slice_stats*>(q);
+            EMF_CUDA(cudaMemsetAsync(ws_loop.as<char>(), 0, head, st));
+            EMF_CUDA(cudaMallocHost(&h_stats, std::max<size_t>(1, n) * sizeof(emfuse_slice_stats)));
+            EMF_CUDA(cudaMallocHost(&h_state, sizeof(SolveState)));
         }
         tail.table = reinterpret_cast<const LSlice<TV>*>(dbase + pos_table);
         tail.level_off = reinterpret_cast<const int*>(dbase + pos_loff);
@@ -778,58 +971,13 @@ struct Solver {
         return EMFUSE_OK;
     }
 
-    // One V-cycle.  The fused schedule is captured once per (plan, starting mode, alpha) as a
-    // CUDA graph and replayed; instrumented runs (per-launch events) and opts.no_graphs launch
-    // directly.
-    int vcycle(bool cont) {
-        if (!fused) return vcycle_reference(cont);
-        if (rq->opts.no_graphs || profiling_active()) return vcycle_fused(cont);
-        const int q = cont ? 1 : 0;
-        if (gexec[q] && galpha[q] != rq->alpha) {
-            cudaGraphExecDestroy(gexec[q]);
-            gexec[q] = nullptr;
-        }
-        if (!gexec[q]) {
-            if (!cap_st) EMF_CUDA(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
-            const uint64_t n0 = launch_count();
-            EMF_CUDA(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
-            cudaStream_t user = st;
-            st = cap_st;
-            const int rc = vcycle_fused(cont);
-            st = user;
-            cudaGraph_t g = nullptr;
-            const cudaError_t e = cudaStreamEndCapture(cap_st, &g);
-            const int64_t nodes = (int64_t)(launch_count() - n0);
-            add_launches(-nodes);  // captured, not run
-            if (rc != EMFUSE_OK) {
-                if (g) cudaGraphDestroy(g);
-                return rc;
-            }
-            if (e != cudaSuccess) {
-                set_error(std::string("V-cycle graph capture: ") + cudaGetErrorString(e));
-                return EMFUSE_ECUDA;
-            }
-            const cudaError_t ei = cudaGraphInstantiate(&gexec[q], g, 0);
-            cudaGraphDestroy(g);
-            if (ei != cudaSuccess) {
-                gexec[q] = nullptr;
-                set_error(std::string("V-cycle graph instantiation: ") + cudaGetErrorString(ei));
-                return EMFUSE_ECUDA;
-            }
-            gnodes[q] = nodes;
-            galpha[q] = rq->alpha;
-        }
-        EMF_CUDA(cudaGraphLaunch(gexec[q], st));
-        add_launches(gnodes[q]);
-        return EMFUSE_OK;
-    }
+    // One V-cycle (launched directly, or recorded while a solve graph is captured).
+    int vcycle(bool cont) { return fused ? vcycle_fused(cont) : vcycle_reference(cont); }
 
-    // Pass `it` of the outer loop: MODE 0 at it == 0, MODE 1 at it == 1, MODE 2 after that.
-    // The FP64 iterates alternate between the two halves of ws_f (written: it & 1).
+    // Residual pass MODE (0: first residual, 1: first correction, 2: later corrections) on the
+    // iterate buffers the device-side pass index selects.
     template <class To, int MODE>
-    int top_pass(const To* o, int it) {
-        const TF* d_old = dbuf[(it + 1) & 1];
-        TF* d_new = dbuf[it & 1];
+    int top_pass() {
         // algorithmic bytes: s and o (or rhs) read, r written; MODE >= 1 also reads e (and
         // d_old in MODE 2) and writes d_new and the output
         const double in_b = rq->rhs ? 4.0 : 4.0 + sizeof(To);
@@ -844,39 +992,194 @@ struct Solver {
         ad.alpha_f = float(rq->alpha);
         if (rq->opts.tol < 1e-7)
             k_top<TF, TV, To, MODE, true><<<(unsigned)top_tiles, 256, 0, st>>>(
-                d_top, d_top_ts, (int)rq->nslices, d_active, rq->s, o, rq->rhs, d_old, d_new, rq->out,
-                rq->alpha, ad, d_norms);
+                d_top, d_top_ts, (int)rq->nslices, d_active, d_call, d_state, dbuf[0], dbuf[1], rq->alpha, ad,
+                d_norms);
         else
             k_top<TF, TV, To, MODE, false><<<(unsigned)top_tiles, 256, 0, st>>>(
-                d_top, d_top_ts, (int)rq->nslices, d_active, rq->s, o, rq->rhs, d_old, d_new, rq->out,
-                rq->alpha, ad, d_norms);
+                d_top, d_top_ts, (int)rq->nslices, d_active, d_call, d_state, dbuf[0], dbuf[1], rq->alpha, ad,
+                d_norms);
         EMF_CHECK_LAUNCH();
         return EMFUSE_OK;
     }
 
-    // The plain FP64 recomputation of every slice's final relative residual (k_verify).
-    // last_pass[j]: the outer pass that last wrote slice j's iterate (0: never iterated).
-    template <class To>
-    int verify(const To* o, const std::vector<int>& last_pass, std::vector<double>& rel_out) {
-        const int64_t n = rq->nslices;
-        std::vector<int> which(n);
-        for (int64_t j = 0; j < n; ++j) which[j] = last_pass[j] == 0 ? 0 : 1 + (last_pass[j] & 1);
-        std::vector<double> sums(2 * n, 0.0);
-        EMF_CUDA(cudaMemcpyAsync(d_active, which.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
-        EMF_CUDA(cudaMemsetAsync(d_norms, 0, 2 * n * sizeof(double), st));
-        {
-            KernelScope ks("residual_verify", st, top_cells * (12.0 + sizeof(TF) + sizeof(To)));
-            k_verify<TF, To><<<(unsigned)top_tiles, 256, 0, st>>>(d_top, d_top_ts, (int)n, d_active, rq->s, o,
-                                                                    rq->rhs, dbuf[0], dbuf[1], rq->alpha, d_norms);
-            EMF_CHECK_LAUNCH();
-        }
-        EMF_CUDA(cudaMemcpyAsync(sums.data(), d_norms, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
-        EMF_CUDA(cudaStreamSynchronize(st));
-        for (int64_t j = 0; j < n; ++j) {
-            const double bn = std::sqrt(sums[2 * j + 1]), rn = std::sqrt(sums[2 * j]);
-            rel_out[j] = bn > 0 ? rn / bn : rn;
-        }
+    int launch_init() {
+        const int n = (int)rq->nslices;
+        KernelScope ks("solve_control", st, 0.0);
+        k_init<<<(unsigned)std::max<int64_t>(1, ceil_div(n, 256)), 256, 0, st>>>(d_state, n, d_done, d_active, d_vcyc,
+                                                                                 d_lastp, d_norms, d_work);
+        EMF_CHECK_LAUNCH();
         return EMFUSE_OK;
+    }
+
+    int launch_check(int nv, bool handle, cudaGraphConditionalHandle h) {
+        KernelScope ks("solve_control", st, 0.0);
+        k_check<<<1, 256, 0, st>>>(d_state, (int)rq->nslices, d_norms, d_bnorm, d_rel, d_done, d_active, d_vcyc,
+                                   d_lastp, rq->opts.tol, std::max(0, rq->opts.max_vcycles), nv, d_err,
+                                   handle ? 1 : 0, h);
+        EMF_CHECK_LAUNCH();
+        return EMFUSE_OK;
+    }
+
+    template <class To>
+    int launch_finish() {
+        KernelScope ks("store_initial", st, 0.0);
+        k_finish<To><<<(unsigned)(rq->nslices * kFinishBlocks), 256, 0, st>>>(d_top, d_vcyc, d_call);
+        EMF_CHECK_LAUNCH();
+        return EMFUSE_OK;
+    }
+
+    // V-cycles of the first outer iteration (the second continues from the first's correction)
+    int first_vcycles() const { return std::min(rq->opts.first_vcycles, std::max(0, rq->opts.max_vcycles)); }
+
+    // The outer loop, recorded on `st`:  first residual, check; then (when the first iteration
+    // has V-cycles) those V-cycles, the first correction pass and a check that sets the loop
+    // condition; the loop body is one V-cycle, a correction pass and a check.  Slices that are
+    // done are inactive, so the first iteration's kernels do nothing for them even when the
+    // first check finds every slice done.
+    template <class To>
+    int record_prologue(cudaGraphConditionalHandle h, bool handle) {
+        EMF_TRY(launch_init());
+        EMF_TRY((top_pass<To, 0>()));
+        const int nv = first_vcycles();
+        EMF_TRY(launch_check(nv, false, h));
+        if (nv == 0) return EMFUSE_OK;
+        for (int v = 0; v < nv; ++v) EMF_TRY(vcycle(v > 0));
+        EMF_TRY((top_pass<To, 1>()));
+        return launch_check(1, handle, h);
+    }
+    template <class To>
+    int record_body(cudaGraphConditionalHandle h, bool handle) {
+        EMF_TRY(vcycle(false));
+        EMF_TRY((top_pass<To, 2>()));
+        return launch_check(1, handle, h);
+    }
+
+    // The solve as one graph: the prologue, a conditional WHILE node whose condition k_check
+    // sets after every residual pass (the body captured into the node's child graph on a second
+    // private stream), and the store of the never-iterated slices.  Captured once per plan and
+    // per value baked into its kernels (alpha, tol, max_vcycles, first V-cycles, iterate and
+    // constraint types); the caller's buffers go through d_call.
+    template <class To>
+    int solve_graph() {
+        const std::vector<double> key = {rq->alpha, rq->opts.tol, (double)rq->opts.max_vcycles,
+                                         (double)first_vcycles(), rq->rhs ? 1.0 : 0.0, (double)sizeof(To)};
+        if (sexec && key == skey) return EMFUSE_OK;
+        drop_graphs();
+        if (!cap_st) EMF_CUDA(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
+        if (!cap_body) EMF_CUDA(cudaStreamCreateWithFlags(&cap_body, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        EMF_CUDA(cudaGraphCreate(&g, 0));
+        // the loop's condition handle (a graph without the loop node may hold no handle)
+        cudaGraphConditionalHandle h{};
+        cudaError_t e = first_vcycles() > 0 ? cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault)
+                                            : cudaSuccess;
+        int rc = EMFUSE_OK;
+        int64_t n_pro = 0, n_body = 0;
+        const cudaStream_t user = st;
+        if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cap_st, g, nullptr, nullptr, 0,
+                                                                cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const uint64_t c0 = launch_count();
+            st = cap_st;
+            rc = record_prologue<To>(h, first_vcycles() > 0);
+            if (rc == EMFUSE_OK && first_vcycles() > 0) {
+                cudaStreamCaptureStatus cs;
+                cudaGraph_t cg = nullptr;
+                const cudaGraphNode_t* deps = nullptr;
+                size_t ndeps = 0;
+                e = cudaStreamGetCaptureInfo(cap_st, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
+                cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+                cp.conditional.handle = h;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                cudaGraphNode_t loop = nullptr;
+                if (e == cudaSuccess) e = cudaGraphAddNode(&loop, cg, deps, nullptr, ndeps, &cp);
+                if (e == cudaSuccess)
+                    e = cudaStreamUpdateCaptureDependencies(cap_st, &loop, nullptr, 1, cudaStreamSetCaptureDependencies);
+                if (e == cudaSuccess)
+                    e = cudaStreamBeginCaptureToGraph(cap_body, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    const uint64_t b0 = launch_count();
+                    st = cap_body;
+                    rc = record_body<To>(h, true);
+                    n_body = (int64_t)(launch_count() - b0);
+                    cudaGraph_t body = nullptr;
+                    const cudaError_t eb = cudaStreamEndCapture(cap_body, &body);
+                    if (e == cudaSuccess) e = eb;
+                    st = cap_st;
+                }
+            }
+            if (rc == EMFUSE_OK && e == cudaSuccess) rc = launch_finish<To>();
+            n_pro = (int64_t)(launch_count() - c0) - n_body;
+            const cudaError_t ee = cudaStreamEndCapture(cap_st, &g);
+            if (e == cudaSuccess) e = ee;
+            add_launches(-(n_pro + n_body));  // recorded, not run
+        }
+        st = user;
+        if (rc == EMFUSE_OK && e == cudaSuccess) e = cudaGraphInstantiate(&sexec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (rc != EMFUSE_OK) {
+            sexec = nullptr;
+            return rc;
+        }
+        if (e != cudaSuccess) {
+            sexec = nullptr;
+            set_error(std::string("solve graph: ") + cudaGetErrorString(e));
+            return EMFUSE_ECUDA;
+        }
+        skey = key;
+        s_pro_nodes = n_pro;
+        s_body_nodes = n_body;
+        s_pro_passes = first_vcycles() > 0 ? 2 : 1;
+        return EMFUSE_OK;
+    }
+
+    // The same kernels launched directly, the host reading the loop decision after every check
+    // (per-launch profiling, opts.no_graphs, the reference schedule).
+    template <class To>
+    int solve_direct() {
+        auto cont = [&](int& c) -> int {
+            EMF_CUDA(cudaMemcpyAsync(h_state, d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+            EMF_CUDA(cudaStreamSynchronize(st));
+            c = h_state->cont;
+            return EMFUSE_OK;
+        };
+        cudaGraphConditionalHandle none{};
+        EMF_TRY(launch_init());
+        EMF_TRY((top_pass<To, 0>()));
+        const int nv = first_vcycles();
+        EMF_TRY(launch_check(nv, false, none));
+        int c = 0;
+        EMF_TRY(cont(c));
+        if (c && nv > 0) {
+            for (int v = 0; v < nv; ++v) EMF_TRY(vcycle(v > 0));
+            EMF_TRY((top_pass<To, 1>()));
+            EMF_TRY(launch_check(1, false, none));
+            EMF_TRY(cont(c));
+            while (c) {
+                EMF_TRY((record_body<To>(none, false)));
+                EMF_TRY(cont(c));
+            }
+        }
+        return launch_finish<To>();
+    }
+
+    // Stream callback of an asynchronous solve: copies the results to the caller's array and
+    // counts the kernels the graph ran (its loop ran a data-dependent number of times).
+    struct AsyncJob {
+        const emfuse_slice_stats* src;
+        emfuse_slice_stats* dst;
+        int64_t n;
+        const SolveState* state;
+        int64_t pro_nodes, body_nodes;
+        int pro_passes;
+    };
+    static void CUDART_CB async_done_cb(void* p) {
+        AsyncJob* j = static_cast<AsyncJob*>(p);
+        if (j->dst) std::memcpy(j->dst, j->src, (size_t)j->n * sizeof(emfuse_slice_stats));
+        add_launches(j->pro_nodes + j->body_nodes * std::max(0, j->state->it - j->pro_passes));
+        delete j;
     }
 
     template <class To>
@@ -890,87 +1193,72 @@ struct Solver {
             EMF_TRY(ws_f.alloc_persistent((size_t)(2 * half) * sizeof(TF)));
         dbuf[0] = ws_f.as<TF>();
         dbuf[1] = ws_f.as<TF>() + half;
-        std::vector<int> active(n, 1), vcycles(n, 0), last_pass(n, 0);
-        std::vector<double> norms(2 * n), rel(n, 0.0), bnorm(n, 0.0);
-        std::vector<char> done(n, 0);
-        EMF_CUDA(cudaMemcpyAsync(d_active, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
-        EMF_CUDA(cudaMemsetAsync(d_norms, 0, 2 * n * sizeof(double), st));
-        EMF_CUDA(cudaMemsetAsync(d_work, 0, 2 * sizeof(unsigned int), st));  // after an aborted launch
-        const int maxit = std::max(0, rq->opts.max_vcycles);
-        int vdone = 0;
-        bool all_done = false;
-        int rc = EMFUSE_OK;
-        for (int it = 0;; ++it) {
-            if (it > 0) EMF_CUDA(cudaMemsetAsync(d_norms, 0, n * 2 * sizeof(double), st));
-            if (it == 0) rc = top_pass<To, 0>(o, it);
-            else if (it == 1) rc = top_pass<To, 1>(o, it);
-            else rc = top_pass<To, 2>(o, it);
-            if (rc != EMFUSE_OK) return rc;
-            EMF_CUDA(cudaMemcpyAsync(norms.data(), d_norms, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
-            int err_flag = 0;
-            EMF_CUDA(cudaMemcpyAsync(&err_flag, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-            EMF_CUDA(cudaStreamSynchronize(st));
-            if (err_flag) {
-                cudaMemsetAsync(d_err, 0, sizeof(int), st);
-                cudaStreamSynchronize(st);
-                set_error("a bounded device-side wait (TMA staging) expired");
-                return EMFUSE_ETIMEOUT;
-            }
-            all_done = true;
-            for (int64_t j = 0; j < n; ++j) {
-                if (done[j]) continue;
-                last_pass[j] = it;  // this pass wrote the slice's iterate (it >= 1) and output
-                if (it == 0) bnorm[j] = std::sqrt(norms[2 * j + 1]);
-                const double rr = norms[2 * j];
-                rel[j] = bnorm[j] > 0 ? std::sqrt(rr) / bnorm[j] : std::sqrt(rr);
-                if (rel[j] <= rq->opts.tol || !std::isfinite(rel[j])) {
-                    done[j] = 1;
-                    active[j] = 0;
-                } else {
-                    all_done = false;
-                }
-            }
-            if (all_done || vdone >= maxit) break;
-            EMF_CUDA(cudaMemcpyAsync(d_active, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
-            // the first outer iteration runs first_vcycles V-cycles in FP32, each continuing
-            // from the previous one's correction, before the first FP64 residual
-            const int nv = it == 0 ? std::min(rq->opts.first_vcycles, maxit - vdone) : 1;
-            for (int v = 0; v < nv; ++v) {
-                EMF_TRY(vcycle(v > 0));
-                for (int64_t j = 0; j < n; ++j)
-                    if (active[j]) ++vcycles[j];
-            }
-            vdone += nv;
-        }
-        // Every residual pass after the first wrote the output of the slices it covered; slices
-        // that met the tolerance at the initial iterate get f = o here.
-        for (int64_t j = 0; j < n; ++j) {
-            if (vcycles[j] != 0) continue;
-            const int64_t cells = rq->nx[j] * rq->ny[j];
-            KernelScope ks("store_initial", st, (double)cells * ((rq->rhs ? 0 : sizeof(To)) + 4.0));
-            k_fill_initial<To><<<grid_for(cells, 256), 256, 0, st>>>(rq->rhs ? nullptr : o + rq->offsets[j],
-                                                                     rq->out + rq->offsets[j], cells);
+        // the graph path needs the fused schedule; instrumented runs time every launch directly
+        const bool graph = fused && !rq->opts.no_graphs && !profiling_active();
+        const bool async = graph && rq->opts.async_solve;
+        {
+            KernelScope ks("solve_control", st, 0.0);
+            k_set_call<<<1, 1, 0, st>>>(d_call, CallPtrs{rq->s, o, rq->rhs, rq->out});
             EMF_CHECK_LAUNCH();
         }
-        std::vector<double> check(n, -1.0);
-        if (rq->opts.verify_residual) EMF_TRY(verify<To>(o, last_pass, check));
-        bool nonfinite = false;
-        if (rq->stats) {
-            for (int64_t j = 0; j < n; ++j) {
-                rq->stats[j].vcycles = vcycles[j];
-                rq->stats[j].rel_residual = rel[j];
-                rq->stats[j].b_norm = bnorm[j];
-                rq->stats[j].converged = rel[j] <= rq->opts.tol ? 1 : 0;
-                rq->stats[j].rel_residual_check = check[j];
-            }
+        if (graph) {
+            EMF_TRY(solve_graph<To>());
+            EMF_CUDA(cudaGraphLaunch(sexec, st));
+        } else {
+            EMF_TRY(solve_direct<To>());
         }
-        for (int64_t j = 0; j < n; ++j) nonfinite |= !std::isfinite(rel[j]);
+        if (rq->opts.verify_residual) {
+            EMF_CUDA(cudaMemsetAsync(d_vsums, 0, 2 * n * sizeof(double), st));
+            KernelScope ks("residual_verify", st, top_cells * (12.0 + sizeof(TF) + sizeof(To)));
+            k_verify<TF, To><<<(unsigned)top_tiles, 256, 0, st>>>(d_top, d_top_ts, (int)n, d_lastp, rq->s, o, rq->rhs,
+                                                                    dbuf[0], dbuf[1], rq->alpha, d_vsums);
+            EMF_CHECK_LAUNCH();
+        }
+        {
+            KernelScope ks("solve_control", st, 0.0);
+            k_stats<<<(unsigned)std::max<int64_t>(1, ceil_div(n, 256)), 256, 0, st>>>(
+                (int)n, d_vcyc, d_rel, d_bnorm, rq->opts.verify_residual ? d_vsums : nullptr, rq->opts.tol, d_stats);
+            EMF_CHECK_LAUNCH();
+        }
+        EMF_CUDA(cudaMemcpyAsync(h_stats, d_stats, n * sizeof(emfuse_slice_stats), cudaMemcpyDeviceToHost, st));
+        EMF_CUDA(cudaMemcpyAsync(h_state, d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+        if (async) {
+            // results reach the caller's array from a stream callback: valid after the stream
+            // (or an event recorded after this call) has completed
+            AsyncJob* job = new AsyncJob{h_stats, rq->stats, n, h_state, s_pro_nodes, s_body_nodes, s_pro_passes};
+            const cudaError_t e = cudaLaunchHostFunc(st, async_done_cb, job);
+            if (e != cudaSuccess) {
+                delete job;
+                set_error(std::string("cudaLaunchHostFunc: ") + cudaGetErrorString(e));
+                return EMFUSE_ECUDA;
+            }
+            if (!async_done) EMF_CUDA(cudaEventCreateWithFlags(&async_done, cudaEventDisableTiming));
+            EMF_CUDA(cudaEventRecord(async_done, st));
+            return EMFUSE_OK;
+        }
+        int* dev_err = device_error_flag();  // bounded waits of other kernels (smoothing)
+        int dev_flag = 0;
+        if (dev_err) EMF_CUDA(cudaMemcpyAsync(&dev_flag, dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         EMF_CUDA(cudaStreamSynchronize(st));
+        if (graph) add_launches(s_pro_nodes + s_body_nodes * std::max(0, h_state->it - s_pro_passes));
+        if (rq->stats) std::memcpy(rq->stats, h_stats, (size_t)n * sizeof(emfuse_slice_stats));
+        if (h_state->timeout || dev_flag) {
+            cudaMemsetAsync(d_err, 0, sizeof(int), st);
+            if (dev_err) cudaMemsetAsync(dev_err, 0, sizeof(int), st);
+            cudaStreamSynchronize(st);
+            set_error("a bounded device-side wait (TMA staging) expired");
+            return EMFUSE_ETIMEOUT;
+        }
+        bool nonfinite = false, converged = true;
+        for (int64_t j = 0; j < n; ++j) {
+            nonfinite |= !std::isfinite(h_stats[j].rel_residual);
+            converged &= h_stats[j].rel_residual <= rq->opts.tol;
+        }
         if (nonfinite) {
             set_error("non-finite residual (NaN or Inf in the inputs?)");
             return EMFUSE_EINVAL;
         }
-        if (!all_done) {
+        if (!converged) {
             set_error("tolerance not reached within max_vcycles");
             return EMFUSE_ENOCONV;
         }
@@ -1154,6 +1442,7 @@ int solve_batch(const SolveRequest& req, cudaStream_t st) {
         SolveRequest c = r;
         c.stats = nullptr;
         c.opts.verify_residual = 0;
+        c.opts.async_solve = 0;
         c.opts.nu_pre = np;
         c.opts.nu_post = nq;
         c.opts.tile_rows = rows;
@@ -1195,6 +1484,39 @@ int solve_batch(const SolveRequest& req, cudaStream_t st) {
 }
 
 const std::vector<emfuse_tune_entry>& last_autotune() { return t_last_tune; }
+
+int solve_async_status(cudaStream_t st, int precision) {
+    int dev = 0;
+    EMF_CUDA(cudaGetDevice(&dev));
+    std::shared_ptr<void> solver;
+    std::shared_ptr<std::mutex> mu;
+    {
+        std::lock_guard<std::mutex> lk(g_plans_mu);
+        for (auto& e : g_plans)
+            if (e.dev == dev && e.st == st && e.prec == precision) {
+                solver = e.solver;
+                mu = e.mu;
+            }
+    }
+    if (!solver) return EMFUSE_OK;
+    std::lock_guard<std::mutex> lk(*mu);
+    auto status = [&](auto* sv) -> int {
+        if (!sv->h_state || !sv->d_err) return EMFUSE_OK;
+        int flag = 0;
+        EMF_CUDA(cudaMemcpyAsync(&flag, sv->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        EMF_CUDA(cudaStreamSynchronize(st));
+        if (!flag && !sv->h_state->timeout) return EMFUSE_OK;
+        cudaMemsetAsync(sv->d_err, 0, sizeof(int), st);
+        cudaStreamSynchronize(st);
+        set_error("a bounded device-side wait (TMA staging) expired");
+        return EMFUSE_ETIMEOUT;
+    };
+    switch (precision) {
+        case EMFUSE_PREC_FP32: return status(static_cast<Solver<float, float>*>(solver.get()));
+        case EMFUSE_PREC_MIXED: return status(static_cast<Solver<double, float>*>(solver.get()));
+        default: return status(static_cast<Solver<double, double>*>(solver.get()));
+    }
+}
 
 size_t cached_plan_bytes(cudaStream_t st, int precision) {
     int dev = 0;

@@ -117,14 +117,23 @@ def _hbm_roofline(p: dict) -> dict:
             "traffic": stored_traffic(p["name"])}
 
 
-def kernel_roofline(prof: list[dict]) -> dict:
+def kernel_roofline(prof: list[dict], fp64_measured_tflops: float | None = None) -> dict:
     """Roofline of the dominant kernel (largest share of the step): FP64-pipe bound ("alu")
-    when it does FP64 work, else HBM bound."""
+    when it does FP64 work, else HBM bound.  For the FP64 case the peak is the FP64 FMA rate
+    measured on this GPU (emfuse_probe_fp64_fma_rate) when given, with the peak derived from
+    the unit counts and clock beside it, and the kernel's HBM fraction at its algorithmic bytes."""
     top = max(prof, key=lambda p: p["share"])
     if top.get("fp64_flops_per_launch"):
+        peak = fp64_measured_tflops or FP64_PEAK_TFLOPS
+        hbm, kind = measured_hbm_peak()
         return {"kernel": top["name"], "bound": "alu", "achieved": top["fp64_tflops"],
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": top["fp64_tflops"] / FP64_PEAK_TFLOPS,
-                "peak_source": "FP64 derived from unit counts and clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "peak": peak, "unit": "TFLOP/s", "frac": top["fp64_tflops"] / peak,
+                "peak_source": ("FP64 FMA rate measured on this GPU by CUDA events (emfuse_probe_fp64_fma_rate)"
+                                if fp64_measured_tflops else
+                                "FP64 derived from unit counts and clock (152 SMs x 2 DFMA/clk x 2.07 GHz)"),
+                "peak_derived": FP64_PEAK_TFLOPS, "frac_of_derived": top["fp64_tflops"] / FP64_PEAK_TFLOPS,
+                "hbm_gbs": top["gbs"], "hbm_frac": top["gbs"] / hbm if top["gbs"] else None,
+                "hbm_peak_source": f"hbm_gbs of {kind}",
                 "share_of_step": top["share"], "flops_per_launch": top["fp64_flops_per_launch"],
                 "bytes_per_launch": top["bytes_per_launch"], "traffic": stored_traffic(top["name"])}
     return _hbm_roofline(top)

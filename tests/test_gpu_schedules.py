@@ -132,6 +132,35 @@ def test_graph_replay_and_tile_rows_are_bit_identical(dev, precision):
     assert torch.equal(g1, g2)
 
 
+@pytest.mark.parametrize("precision", [api.PREC_MIXED, api.PREC_FP64])
+def test_async_solve_returns_before_the_gpu_and_matches_the_blocking_call(dev, precision):
+    """opts.async_solve = 1: the whole solve (its outer loop a WHILE node of one CUDA graph) is
+    queued and the call returns while the GPU still works; after a stream synchronisation the
+    output is bit-identical to the blocking call's and the stats equal its stats.  A slice that
+    cannot reach tol is reported through stats.converged = 0 (no status code)."""
+    I0 = make_stack(16, 1024, 1024, seed=9).to(dev)
+    s = api.emfuse_smooth_z(I0, 1.0, 3.0)
+    ref, st_ref = api.emfuse_screened_poisson(s, I0, 1e-3, api.default_opts(precision=precision), return_stats=True)
+    stream = torch.cuda.current_stream(dev)
+    opts = api.default_opts(precision=precision, async_solve=1)
+    api.emfuse_screened_poisson(s, I0, 1e-3, opts)  # the first call of a geometry builds its plan and graph
+    torch.cuda.synchronize(dev)
+    out = torch.full_like(I0, float("nan"))
+    f, pending = api.emfuse_screened_poisson(s, I0, 1e-3, opts, out=out, return_stats=True)
+    ev = torch.cuda.Event()
+    ev.record(stream)
+    still_running = not ev.query()
+    st = pending.result()
+    assert still_running
+    assert torch.equal(f, ref)
+    assert st == st_ref
+    # non-convergence: no status code, converged = 0 in the stats
+    few = api.default_opts(precision=precision, async_solve=1, max_vcycles=1)
+    _, pend = api.emfuse_screened_poisson(s, I0, 1e-3, few, return_stats=True)
+    st1 = pend.result()
+    assert all(a["vcycles"] == 1 and not a["converged"] for a in st1)
+
+
 def test_autotune_picks_the_fastest_candidate(dev):
     s, o, ny, nx, offs = make_ragged_batch(10, seed=2, side_lo=64, side_hi=900)
     s, o = s.to(dev), o.to(dev)
