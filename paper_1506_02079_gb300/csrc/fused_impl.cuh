@@ -479,7 +479,13 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
                     if (!FAST && (r < 0 || r >= ny)) continue;
                     int Iy, Jy;
                     T wy;
-                    interp_axis<T>(r, L.n0y, k, L.ncy, Iy, Jy, wy);
+                    if (FAST) {  // interior pattern along y (the step's rows are >= 2 and below the last two coarse rows)
+                        Iy = T_;
+                        Jy = h ? T_ + 1 : T_ - 1;
+                        wy = T(0.25);
+                    } else {
+                        interp_axis<T>(r, L.n0y, k, L.ncy, Iy, Jy, wy);
+                    }
                     // coarse row q sits at box row q - (T - 1); columns cx0-1 .. cx0+2 at 2l+3 .. 2l+6
                     const uint32_t c0 = cb + ((Iy - T_ + 1) * kWaveCoarseW + 2 * lane + 2) * (uint32_t)sizeof(T);
                     const uint32_t c1 = cb + ((Jy - T_ + 1) * kWaveCoarseW + 2 * lane + 2) * (uint32_t)sizeof(T);
@@ -631,11 +637,13 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
         // The interior body also drops the range checks of a march step, so it is taken where
         // every stage has its pair (T - S >= first pair of the march), the output pair T - S
         // and the residual pair T - S - 1 (DOWN) lie in this chunk, the prolongation rows 2T,
-        // 2T + 1 (UP) in the level, and every row the step updates is an interior row
+        // 2T + 1 (UP) in the level with the interior interpolation pattern along y (coarse rows
+        // T - 1 .. T + 1 all full: T + 2 < the coarse level's rows), and every row the step
+        // updates is an interior row
         // (pairs T - S - 1 .. T - 1; interior rows form one contiguous range).
         const int rlo = 2 * (T_ - S - (UP ? 0 : 1)), rhi = 2 * T_ - 1;
         const bool steady = T_ >= P0 + S + (UP ? 0 : 1) && 2 * (T_ - S) + 1 < Y1 && T_ - S < P1 &&
-                            (!UP || 2 * T_ + 1 < ny);
+                            (!UP || (2 * T_ + 1 < ny && (!has_coarse || T_ + 2 < L.ncy)));
         if (x_ghost && steady && interior_row(rlo, ny, k) && interior_row(rhi, ny, k))
             step(std::true_type{}, T_);
         else
@@ -664,6 +672,12 @@ __global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(Wav
 }
 
 // ---------------------------------------------------------------- coarse tail
+// The levels of one slice from kc (the first with both sides <= kTailMax) down to 1 x 1 are run
+// by one CTA on copies in shared memory (dense rows): at most 64 x 64 + 32 x 32 + ... cells, u and
+// b each.  Only level kc touches global memory: its right-hand side (and, continuing at level 0,
+// its iterate) is read at the start and its final iterate written at the end, where the wavefront
+// UP kernel of level kc - 1 (or the residual kernel, at kc = 0) reads it.  The per-cell arithmetic
+// and its order are those of every other schedule.
 template <class T>
 __device__ void tail_relax(const LSlice<T>& L, int k, T alpha, T sk, int sweeps) {
     const int n = L.nx * L.ny;
@@ -684,26 +698,59 @@ __device__ void tail_relax(const LSlice<T>& L, int k, T alpha, T sk, int sweeps)
         }
 }
 
+constexpr int kTailMaxLevels = 16;
+
 template <class T>
 __global__ void __launch_bounds__(512) k_tail(TailArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char tail_smem[];
     const int j = blockIdx.x;
     if (a.active && !a.active[j]) return;
     const LSlice<T>* lv = a.table + a.level_off[j];
     const int kc = a.kc[j];
     const int K = a.nlev[j] - 1;
+    if (K - kc + 1 > kTailMaxLevels) return;  // never: a 64 x 64 level has 7 levels below it
+    // shared-memory copies of levels kc .. K: u then b, dense rows; their descriptors once per CTA
+    __shared__ LSlice<T> sl[kTailMaxLevels];
+    if (threadIdx.x == 0) {
+        T* q = reinterpret_cast<T*>(tail_smem);
+        for (int k = kc; k <= K; ++k) {
+            LSlice<T> L = lv[k];
+            L.pitch = L.nx;
+            L.u = q;
+            q += (size_t)L.nx * L.ny;
+            L.b = q;
+            q += (size_t)L.nx * L.ny;
+            sl[k - kc] = L;
+        }
+        for (int k = kc; k < K; ++k) {
+            sl[k - kc].uc = sl[k + 1 - kc].u;
+            sl[k - kc].bc = sl[k + 1 - kc].b;
+            sl[k - kc].pitchc = sl[k + 1 - kc].pitch;
+        }
+    }
+    __syncthreads();
+    {   // level kc from global memory: its rhs, and its iterate when continuing at level 0
+        const LSlice<T>& G = lv[kc];
+        const LSlice<T>& L = sl[0];
+        const bool cont = a.cont && kc == 0;
+        for (int p = threadIdx.x; p < L.nx * L.ny; p += blockDim.x) {
+            const int y = p / L.nx, x = p - y * L.nx;
+            const int64_t g = (int64_t)y * G.pitch + x;
+            L.b[p] = G.b[g];
+            L.u[p] = cont ? G.u[g] : T(0);  // coarse levels solve for a correction from zero
+        }
+        __syncthreads();
+    }
     for (int k = kc; k <= K; ++k) {
-        const LSlice<T> L = lv[k];
+        const LSlice<T>& L = sl[k - kc];
         const T sk = T(ldexp(1.0, -2 * k));
-        if (!(a.cont && k == 0)) {  // coarse levels solve for a correction from zero
-            for (int p = threadIdx.x; p < L.nx * L.ny; p += blockDim.x) {
-                const int y = p / L.nx, x = p - y * L.nx;
-                L.u[(int64_t)y * L.pitch + x] = T(0);
-            }
+        if (k > kc) {
+            for (int p = threadIdx.x; p < L.nx * L.ny; p += blockDim.x) L.u[p] = T(0);
             __syncthreads();
         }
         tail_relax<T>(L, k, a.alpha, sk, a.nu_pre);
         if (k < K) {
-            const LSlice<T> C = lv[k + 1];
+            const LSlice<T>& C = sl[k + 1 - kc];
             for (int p = threadIdx.x; p < C.nx * C.ny; p += blockDim.x) {
                 const int J = p / C.nx, I = p - J * C.nx;
                 T sum = T(0);
@@ -728,7 +775,7 @@ __global__ void __launch_bounds__(512) k_tail(TailArgs<T> a) {
         }
     }
     for (int k = K - 1; k >= kc; --k) {
-        const LSlice<T> L = lv[k];
+        const LSlice<T>& L = sl[k - kc];
         const T sk = T(ldexp(1.0, -2 * k));
         for (int p = threadIdx.x; p < L.nx * L.ny; p += blockDim.x) {
             const int y = p / L.nx, x = p - y * L.nx;
@@ -736,6 +783,14 @@ __global__ void __launch_bounds__(512) k_tail(TailArgs<T> a) {
         }
         __syncthreads();
         tail_relax<T>(L, k, a.alpha, sk, a.nu_post);
+    }
+    {   // the final iterate of level kc back to global memory
+        const LSlice<T>& G = lv[kc];
+        const LSlice<T>& L = sl[0];
+        for (int p = threadIdx.x; p < L.nx * L.ny; p += blockDim.x) {
+            const int y = p / L.nx, x = p - y * L.nx;
+            G.u[(int64_t)y * G.pitch + x] = L.u[p];
+        }
     }
 }
 

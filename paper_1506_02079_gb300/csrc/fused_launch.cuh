@@ -83,8 +83,20 @@ int launch_wave_impl(const WaveArgs<T>& a, int S, bool zero_init, bool up, cudaS
 template <class T>
 int launch_tail_impl(const TailArgs<T>& a, cudaStream_t st, double bytes) {
     if (a.nslices == 0) return EMFUSE_OK;
+    static std::mutex mu;
+    static int attr_set[64] = {0};  // the shared-memory limit set per device
+    int dev = 0;
+    EMF_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (attr_set[dev] < a.smem_bytes) {
+            EMF_CUDA(cudaFuncSetAttribute(fused_detail::k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          a.smem_bytes));
+            attr_set[dev] = a.smem_bytes;
+        }
+    }
     KernelScope ks("coarse_tail", st, bytes);
-    fused_detail::k_tail<T><<<(unsigned)a.nslices, 512, 0, st>>>(a);
+    fused_detail::k_tail<T><<<(unsigned)a.nslices, 512, (size_t)a.smem_bytes, st>>>(a);
     EMF_CHECK_LAUNCH();
     return EMFUSE_OK;
 }

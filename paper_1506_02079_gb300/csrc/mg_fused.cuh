@@ -215,6 +215,19 @@ __device__ __forceinline__ int find_item(const int64_t* __restrict__ ts, int n, 
     return lo;
 }
 
+// Shared-memory bytes of the coarse tail of a slice whose first tail level has nx x ny cells
+// (u and b of every level down to 1 x 1, dense rows).
+template <class T>
+__host__ __device__ inline size_t tail_smem_bytes(int nx, int ny) {
+    size_t cells = 0;
+    for (int k = 0;; ++k) {
+        const int lx = ((nx - 1) >> k) + 1, ly = ((ny - 1) >> k) + 1;
+        cells += (size_t)lx * ly;
+        if (lx == 1 && ly == 1) break;
+    }
+    return 2 * cells * sizeof(T);
+}
+
 // ---------------------------------------------------------------- fused schedule (fused.cu)
 constexpr int kWaveHalo = 8;                      // x halo of a strip (cells, multiple of 4)
 constexpr int kWaveWidth = 128;                   // strip width: 32 lanes x 4 cells
@@ -251,6 +264,7 @@ struct TailArgs {
     int nu_pre, nu_post;
     const int* active;
     int cont;                    // 1: a slice whose tail starts at level 0 continues from u
+    int smem_bytes;              // dynamic shared memory of the launch (the largest slice's tail)
 };
 
 template <class T>

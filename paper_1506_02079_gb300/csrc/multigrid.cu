@@ -867,6 +867,11 @@ struct Solver {
         tail.nu_post = rq->opts.nu_post;
         tail.active = d_active;
         tail.cont = 0;
+        tail.smem_bytes = 0;
+        for (int64_t j = 0; j < n; ++j)
+            if (kc[j] < nlev[j])
+                tail.smem_bytes = std::max<int>(tail.smem_bytes, (int)tail_smem_bytes<TV>(
+                    level_size((int)rq->nx[j], kc[j]), level_size((int)rq->ny[j], kc[j])));
         EMF_CUDA(cudaStreamSynchronize(st));  // the host staging blob goes out of scope
         built = true;
         return EMFUSE_OK;
