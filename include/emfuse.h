@@ -80,8 +80,10 @@ typedef struct {
                             alpha >= 0.01, but at alpha = 0.001 its rounding reaches the
                             smooth error modes amplified by ~1/alpha (about 4e-4 of the
                             range), and it cannot reach tol below ~1e-6.                   */
-    int fused;           /* 1: fused wavefront kernels on large levels; 0: one kernel per
-                            half-sweep (reference schedule).  Default 1.                   */
+    int fused;           /* 1: fused wavefront kernels on large levels (nu_pre in 1..3,
+                            nu_post in 1..4: the strips overlap by 8 cells; other counts run
+                            the reference schedule); 0: one kernel per half-sweep
+                            (reference schedule).  Default 1.                              */
     int first_vcycles;   /* V-cycles in the first outer iteration (the second continues from
                             the first's correction in FP32 before the first FP64 residual).
                             0 = default (2).                                               */
@@ -89,10 +91,11 @@ typedef struct {
                             on the finest level: 0 = chosen from the batch size, else a
                             power of two in [8, 256].                                      */
     int autotune;        /* 1: before solving, time complete solves of this batch for
-                            tile_rows in {32, 64, 128, 256} and (nu_pre, nu_post) in
-                            {1, 2}^2 (fused schedule), keep the fastest for this batch
-                            geometry, alpha, precision and tol, and solve with it (see
-                            emfuse_autotune_result).  Default 0.                           */
+                            tile_rows in {32, 64, 128, 256} (with nu = (2, 2)), then for
+                            (nu_pre, nu_post) in {(1,1), (1,2), (2,1), (2,3), (3,2), (3,3),
+                            (3,4)} with the best tile_rows (fused schedule), keep the
+                            fastest for this batch geometry, alpha, precision and tol, and
+                            solve with it (see emfuse_autotune_result).  Default 0.        */
     int no_graphs;       /* 1: launch every V-cycle kernel directly instead of replaying
                             the V-cycle as a captured CUDA graph.  Default 0.              */
     float robust_kappa;  /* emfuse_correct_stack only: > 0 smooths with robust averaging

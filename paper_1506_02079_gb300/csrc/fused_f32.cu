@@ -3,6 +3,11 @@
 #include "fused_launch.cuh"
 
 namespace emfuse {
+namespace fused_detail {
+// nu = 3, 4: instantiated in fused_f32_s68.cu
+extern template int launch_wave_s<float, 6>(const WaveArgs<float>&, bool, bool, cudaStream_t);
+extern template int launch_wave_s<float, 8>(const WaveArgs<float>&, bool, bool, cudaStream_t);
+}  // namespace fused_detail
 
 template <>
 int launch_wave<float>(const WaveArgs<float>& a, int S, bool zero_init, bool up, cudaStream_t st, double bytes) {

@@ -95,9 +95,10 @@ __device__ __forceinline__ T pick4(const T (&v)[4], int i) {
     return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3]));
 }
 
-// CTAs per SM the register budget is sized for (FP64 windows take twice the registers).
-template <class T>
-struct WaveOcc { static constexpr int value = sizeof(T) == 4 ? 4 : 2; };
+// CTAs per SM the register budget is sized for: the register window grows with the sweeps (S + 3
+// row pairs) and FP64 windows take twice the registers.
+template <class T, int S>
+struct WaveOcc { static constexpr int value = (sizeof(T) == 4 && S <= 4) ? 4 : 2; };
 
 // ---------------------------------------------------------------- per-cell stencils
 // Interior cells (full cells with full neighbours) all share one stencil.  Cells on a slice
@@ -273,7 +274,7 @@ template <class T, int S, bool ZERO, bool UP>
 constexpr int wave_smem_bytes() { return kWaveWarps * WaveRing<T, S, ZERO, UP>::kWarpBytes; }
 
 template <class T, int S, bool ZERO, bool UP>
-__global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T>::value) k_wave(WaveArgs<T> a) {
+__global__ void __launch_bounds__(kWaveWarps * 32, WaveOcc<T, S>::value) k_wave(WaveArgs<T> a) {
     using R = WaveRing<T, S, ZERO, UP>;
     constexpr int NB = R::kNB;
     constexpr int AHEAD = R::kAhead;

@@ -1,6 +1,7 @@
 // Host-side launchers of the fused multigrid schedule (kernels in fused_impl.cuh), one template
-// for both iterate types; fused_f32.cu and fused_f64.cu each instantiate it once (two
-// translation units, so that the kernel instantiations of the two types compile in parallel).
+// for both iterate types.  fused_f32.cu and fused_f64.cu instantiate it for their type with 2 and
+// 4 half-sweeps (nu = 1, 2); fused_f32_s68.cu and fused_f64_s68.cu the kernels with 6 and 8
+// (nu = 3, 4), so that the four sets compile in parallel.
 #pragma once
 #include <algorithm>
 #include <mutex>
@@ -56,8 +57,13 @@ int launch_wave_one(const WaveArgs<T>& a, cudaStream_t st) {
 template <class T, int S>
 int launch_wave_s(const WaveArgs<T>& a, bool zero_init, bool up, cudaStream_t st) {
     if (up) return launch_wave_one<T, S, false, true>(a, st);
-    if (zero_init) return launch_wave_one<T, S, true, false>(a, st);
-    return launch_wave_one<T, S, false, false>(a, st);
+    if constexpr (S + 1 > kWaveHalo) {  // the DOWN leg's residual needs S + 1 <= the strip halo
+        set_error("wavefront kernel: the DOWN leg supports at most 3 sweeps");
+        return EMFUSE_EINVAL;
+    } else {
+        if (zero_init) return launch_wave_one<T, S, true, false>(a, st);
+        return launch_wave_one<T, S, false, false>(a, st);
+    }
 }
 
 }  // namespace fused_detail
@@ -74,6 +80,8 @@ int launch_wave_impl(const WaveArgs<T>& a, int S, bool zero_init, bool up, cudaS
     switch (S) {
         case 2: EMF_TRY((fused_detail::launch_wave_s<T, 2>(a, zero_init, up, st))); break;
         case 4: EMF_TRY((fused_detail::launch_wave_s<T, 4>(a, zero_init, up, st))); break;
+        case 6: EMF_TRY((fused_detail::launch_wave_s<T, 6>(a, zero_init, up, st))); break;
+        case 8: EMF_TRY((fused_detail::launch_wave_s<T, 8>(a, zero_init, up, st))); break;
         default: set_error("wavefront kernel: unsupported sweep count"); return EMFUSE_EINVAL;
     }
     EMF_CHECK_LAUNCH();

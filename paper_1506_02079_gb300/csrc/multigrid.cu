@@ -642,7 +642,11 @@ struct Solver {
         return v;
     }
 
-    static bool wave_ok(int nu) { return nu == 1 || nu == 2; }
+    // The wavefront kernels' strips overlap by kWaveHalo = 8 cells, and every half-sweep carries
+    // the wrong values at a strip's outer edge one cell further in: the UP leg (S = 2 nu
+    // half-sweeps) needs S <= 8, the DOWN leg, whose residual reaches one cell further, S + 1 <= 8.
+    static bool wave_ok_pre(int nu) { return nu >= 1 && 2 * nu + 1 <= kWaveHalo; }
+    static bool wave_ok_post(int nu) { return nu >= 1 && 2 * nu <= kWaveHalo; }
 
     // Drops the plan but keeps the two large buffers (pyramids, FP64 iterates): their layout
     // is recomputed by build() and they are only reallocated when a batch needs more.
@@ -673,7 +677,7 @@ struct Solver {
         reset();
         sig = std::move(want);
         const int64_t n = rq->nslices;
-        fused = rq->opts.fused != 0 && wave_ok(rq->opts.nu_pre) && wave_ok(rq->opts.nu_post);
+        fused = rq->opts.fused != 0 && wave_ok_pre(rq->opts.nu_pre) && wave_ok_post(rq->opts.nu_post);
         nlev.resize(n);
         kc.resize(n);
         for (int64_t j = 0; j < n; ++j) {
@@ -1373,7 +1377,8 @@ static int solve_batch_once(const SolveRequest& req, cudaStream_t st) {
 // Schedules are compared by the time of a complete solve to the requested tolerance (a
 // schedule with fewer sweeps is cheaper per V-cycle but may need more V-cycles).  The search
 // is staged: rows per work item on the finest level in {32, 64, 128, 256} with nu = (2, 2),
-// then nu in {(1, 1), (1, 2), (2, 1)} with the best rows.  Each candidate runs twice (the
+// then (nu_pre, nu_post) in {(1, 1), (1, 2), (2, 1), (2, 3), (3, 2), (3, 3), (3, 4)} with the best
+// rows (one to four red-black sweeps per leg, all in the fused wavefront kernels).  Each candidate runs twice (the
 // first run builds its plan and captures its graphs) and the second run is timed.  The winner
 // is cached per batch geometry, alpha, precision and tol.
 namespace {
@@ -1469,7 +1474,8 @@ int solve_batch(const SolveRequest& req, cudaStream_t st) {
     for (int rows : {32, 64, 128, 256}) EMF_TRY(trial(2, 2, rows));
     int b = best_of();
     const int rows = b >= 0 ? table[b].tile_rows : 128;
-    for (auto nu : {std::pair<int, int>{1, 1}, {1, 2}, {2, 1}}) EMF_TRY(trial(nu.first, nu.second, rows));
+    for (auto nu : {std::pair<int, int>{1, 1}, {1, 2}, {2, 1}, {2, 3}, {3, 2}, {3, 3}, {3, 4}})
+        EMF_TRY(trial(nu.first, nu.second, rows));
     b = best_of();
     if (b < 0) {
         t_last_tune = table;

@@ -65,8 +65,10 @@ def measured_hbm_peak():
 # CUDA sources each instrumented kernel is built from (the others: every source)
 _KERNEL_SOURCES = {
     "residual": ("multigrid.cu", "fpconv.cuh", "mg_fused.cuh", "emfuse_common.cuh"),
-    "wave": ("fused_impl.cuh", "fused_f32.cu", "fused_f64.cu", "mg_fused.cuh", "tma.cuh", "emfuse_common.cuh"),
-    "coarse_tail": ("fused_impl.cuh", "fused_f32.cu", "fused_f64.cu", "mg_fused.cuh", "emfuse_common.cuh"),
+    "wave": ("fused_impl.cuh", "fused_launch.cuh", "fused_f32.cu", "fused_f64.cu", "fused_f32_s68.cu",
+             "fused_f64_s68.cu", "mg_fused.cuh", "tma.cuh", "emfuse_common.cuh"),
+    "coarse_tail": ("fused_impl.cuh", "fused_launch.cuh", "fused_f32.cu", "fused_f64.cu", "mg_fused.cuh",
+                    "emfuse_common.cuh"),
     "smooth": ("smooth.cu", "tma.cuh", "emfuse_common.cuh"),
 }
 
