@@ -4,11 +4,12 @@
 //
 // Three implementations:
 //   * smooth_tma_kernel (default): one HBM pass.  A CTA owns a 64x16 xy-tile and marches
-//     along z.  Input planes (tile plus xy halo) arrive by TMA bulk tensor copies into two
-//     shared-memory buffers, the next plane in flight while the current one is blurred; the
-//     hardware zero-fills the halo outside the stack.  x then y blur from shared memory with
-//     vector loads, then a 19-plane register ring along z (rotated, so the march stays a
-//     small rolled loop).  Needs rows whose byte pitch is a multiple of 16.
+//     along z.  Input planes (tile plus xy halo) arrive by TMA bulk tensor copies into a ring of
+//     shared-memory buffers, all but one in flight while a plane is blurred; the hardware
+//     zero-fills the halo outside the stack.  x blur in items of 8 outputs, one barrier per
+//     plane, y blur of 2 x 2 outputs per thread, then a 19-plane register ring along z (moved
+//     once per block of planes, so the march stays a small rolled loop).  Needs rows whose
+//     byte pitch is a multiple of 16.
 //   * smooth_fused_kernel: the same data flow with plain loads, for any pitch.
 //     Each input plane is staged in shared memory with its xy halo, blurred in x then y,
 //     and pushed into a per-thread ring of the last P planes held in registers; the z-blur of
@@ -188,31 +189,62 @@ smooth_fused_kernel(const Tin* __restrict__ in, float* __restrict__ out, int nx,
 }
 
 // ---------------------------------------------------------------- TMA-staged kernel
+// Shared-memory layout of the TMA kernel for input type Tin and xy radius R.
 template <class Tin, int R>
 struct SmTile {
-    static constexpr int HX = sizeof(Tin) == 1 ? 16 : 4;  // staged columns left of the tile
-    static constexpr int BX = kTX + 2 * HX;                // x-start stays 16-byte aligned
+    static constexpr int HX = sizeof(Tin) == 1 ? 16 : 4;   // staged columns left of the tile: the
+                                                          // copy's x-start stays 16-byte aligned
+    static constexpr int HXR = sizeof(Tin) == 1 ? 16 : 8;  // right: a float row of 76 words is
+                                                          // 304 B, so 8 consecutive rows start in
+                                                          // 8 different 16-B bank groups
+    static constexpr int BX = kTX + HX + HXR;
     static constexpr int BY = kTY + 2 * R;
     static constexpr int kPlaneBytes = BX * BY * (int)sizeof(Tin);
     static constexpr int kPlaneStride = (kPlaneBytes + 127) / 128 * 128;  // TMA destinations 128-B aligned
-    // plane buffers: NBUF - 1 copies in flight while one plane is blurred (enough bytes in
-    // flight per SM to cover the HBM latency with two CTAs per SM)
+    // plane buffers, all in flight except the one being blurred (about 64 KiB of copies in
+    // flight per SM with two CTAs per SM for float input)
     static constexpr int NBUF = sizeof(Tin) == 1 ? 8 : 5;
+    static constexpr int SXW = kTX + 4;                    // x-blurred row stride (words): 272 B,
+                                                          // 8 rows -> 8 different bank groups
+    static constexpr int kRowBlocks = (BY + 7) / 8;        // x-blur items: 8 rows x 8 groups each
+    static constexpr int kXItems = 64 * kRowBlocks;        // <= 256 for R <= 4
+    static constexpr int kSmemBytes = NBUF * kPlaneStride + 2 * BY * SXW * 4 + NBUF * 8;
 };
 
+// 16 consecutive staged values (as float) starting at p.
 template <class Tin>
-__device__ __forceinline__ void load_word(const Tin* p, float (&v)[4]);
+__device__ __forceinline__ void load16(const Tin* p, float (&s)[16]);
 template <>
-__device__ __forceinline__ void load_word<float>(const float* p, float (&v)[4]) {
-    const float4 q = *reinterpret_cast<const float4*>(p);
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+__device__ __forceinline__ void load16<float>(const float* p, float (&s)[16]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 q = reinterpret_cast<const float4*>(p)[k];
+        s[4 * k] = q.x; s[4 * k + 1] = q.y; s[4 * k + 2] = q.z; s[4 * k + 3] = q.w;
+    }
 }
 template <>
-__device__ __forceinline__ void load_word<uint8_t>(const uint8_t* p, float (&v)[4]) {
-    const uchar4 q = *reinterpret_cast<const uchar4*>(p);
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+__device__ __forceinline__ void load16<uint8_t>(const uint8_t* p, float (&s)[16]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uchar4 q = reinterpret_cast<const uchar4*>(p)[k];
+        s[4 * k] = q.x; s[4 * k + 1] = q.y; s[4 * k + 2] = q.z; s[4 * k + 3] = q.w;
+    }
 }
 
+// One HBM pass of the separable smoothing.  A CTA owns a 64 x 16 xy-tile and marches along z.
+// Per input plane (arriving by TMA into a ring of NBUF shared-memory buffers, zero-filled
+// outside the stack):
+//   x blur   items of 8 outputs on one staged row (rows tile + y halo), written to one of two
+//            x-blurred planes; 8 consecutive lanes take 8 rows, so the vector loads and
+//            stores of a quarter-warp fall in distinct banks;
+//   barrier  the only one per plane: the x-blurred plane is complete, the staged buffer is
+//            free and is refilled with the plane NBUF ahead;
+//   y blur   each thread 2 columns x 2 rows into a register ring of the last 19 planes;
+//   z blur   the plane Rz behind is emitted from the ring, scaled by the product of the three
+//            inverse normalisers.
+// The taps are kernel parameters with compile-time indices, i.e. constant-bank operands of the
+// FMAs.  The blurs sum in their own order and scale once at the end, so results agree with the
+// other implementations to rounding.
 template <class Tin, int R, bool ROB>
 __global__ void __launch_bounds__(kThreads, 2)
 smooth_tma_kernel(const __grid_constant__ CUtensorMap map, float* __restrict__ out, int nx, int ny, int nz,
@@ -222,10 +254,10 @@ smooth_tma_kernel(const __grid_constant__ CUtensorMap map, float* __restrict__ o
     using G = SmTile<Tin, R>;
     constexpr int P = 19;  // z taps: supports floor(3 sigma_z) <= 9
     constexpr int NB = G::NBUF;
-    constexpr int AHEAD = NB - 1;
-    __shared__ __align__(128) unsigned char s_raw[NB * G::kPlaneStride];
-    __shared__ __align__(16) float s_x[G::BY][kTX];
-    __shared__ __align__(8) uint64_t s_bar[NB];
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* s_raw = smem;
+    float* s_x = reinterpret_cast<float*>(smem + NB * G::kPlaneStride);  // [2][BY][SXW]
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + NB * G::kPlaneStride + 2 * G::BY * G::SXW * 4);
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int Rz = prm.Rz;
@@ -236,142 +268,184 @@ smooth_tma_kernel(const __grid_constant__ CUtensorMap map, float* __restrict__ o
         mbar_init_fence();
     }
     __syncthreads();
-    // thread 0: plane zi into buffer slot (slots advance with zi; a slot is refilled only after
-    // the __syncthreads that ended the iteration which last read it)
+    // thread 0: plane zi into buffer slot (zi - zin_lo) mod NB; a slot is refilled only after
+    // the barrier that ended the x blur of the plane it held
     auto issue = [&](int zi, int slot) {
         fence_proxy_async();
         mbar_expect_tx(bar0 + 8 * slot, G::kPlaneBytes);
         tma_load_3d(smem_addr(s_raw + slot * G::kPlaneStride), &map, x0 - G::HX, y0 - R, zi, bar0 + 8 * slot);
     };
     if (tid == 0)
-        for (int q = 0; q < AHEAD && zin_lo + q < zin_hi; ++q) issue(zin_lo + q, q);
+        for (int q = 0; q < NB && zin_lo + q < zin_hi; ++q) issue(zin_lo + q, q);
 
-    float w[2 * R + 1];
-#pragma unroll
-    for (int d = 0; d < 2 * R + 1; ++d) w[d] = prm.wxy[d];
-    const int tx = tid % 16, ty = tid / 16;
-    const int gy = y0 + ty;
-    const float iny = inv_ny[min(gy, ny - 1)];
-    // x-blur items of this thread all have the same column group (kThreads is a multiple of 16)
-    float inx[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) inx[i] = inv_nx[min(x0 + 4 * (tid & 15) + i, nx - 1)];
+    // x-blur item of this thread (warp-uniform participation: kXItems is a multiple of 64)
+    const bool xw = tid < G::kXItems;
+    const int xr = (tid >> 6) * 8 + (tid & 7);  // staged row
+    const int xg = (tid >> 3) & 7;              // group of 8 output columns
+    const bool xitem = xw && xr < G::BY;
+    const Tin* const s_in0 = reinterpret_cast<const Tin*>(s_raw) + xr * G::BX + 8 * xg + G::HX - 4;
+    float* const sx_item = s_x + xr * G::SXW + 8 * xg;
+    // y/z outputs of this thread: columns 2 lane, 2 lane + 1 of rows 2 warp, 2 warp + 1
+    const int lane = tid & 31, wrp = tid >> 5;
+    const int gx = x0 + 2 * lane;
+    const int gy0 = y0 + 2 * wrp, gy1 = gy0 + 1;
+    const float* const sy_col = s_x + (2 * wrp) * G::SXW + 2 * lane;
+    float sxy[4];  // inv_x * inv_y of the 4 outputs (row 0 x, row 0 x+1, row 1 x, row 1 x+1)
+    {
+        const float ix0 = inv_nx[min(gx, nx - 1)], ix1 = inv_nx[min(gx + 1, nx - 1)];
+        const float iy0 = inv_ny[min(gy0, ny - 1)], iy1 = inv_ny[min(gy1, ny - 1)];
+        sxy[0] = ix0 * iy0; sxy[1] = ix1 * iy0; sxy[2] = ix0 * iy1; sxy[3] = ix1 * iy1;
+    }
+    const bool st0 = gy0 < ny, st1 = gy1 < ny;
+    const bool vec2 = (pitch & 1) == 0 && (reinterpret_cast<uintptr_t>(out) & 7) == 0 && gx + 1 < nx;
+    float* const dst0 = out + (int64_t)min(gy0, ny - 1) * pitch + gx;
+    float* const dst1 = out + (int64_t)min(gy1, ny - 1) * pitch + gx;
+
     // z ring: slots 0 .. P-2 hold the P-1 planes before the current block of U planes, slots
     // P-1 .. P-2+U the block; the ring moves by U slots once per block (the loop over a block is
     // unrolled, so every slot index is a constant)
-    constexpr int U = 4;
+    constexpr int U = ROB ? 2 : 4;  // the robust window needs more registers of its own
     float ring[P - 1 + U][4];
 #pragma unroll
     for (int q = 0; q < P - 1 + U; ++q)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) ring[q][i] = 0.f;
+        for (int c = 0; c < 4; ++c) ring[q][c] = 0.f;
     const int64_t plane = pitch * (int64_t)ny;
 
     int slot = 0;        // buffer slot of plane zi
     uint32_t phase = 0;  // barrier parity of the current lap over the slots
+    int buf = 0;         // x-blurred plane buffer (0 or 1)
 #pragma unroll 1
     for (int zb = zin_lo; zb < zi_end; zb += U) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int zi = zb + u;
             float v[4] = {0.f, 0.f, 0.f, 0.f};
-            if (zi < zin_hi) {
-                if (tid == 0 && zi + AHEAD < zin_hi) issue(zi + AHEAD, slot == 0 ? NB - 1 : slot - 1);
-                bool ok = false;
-                for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(bar0 + 8 * slot, phase);
+            if (zi < zin_hi) {  // uniform across the CTA
+                bool ok = true;
+                const int boff = buf * (G::BY * G::SXW);
+                if (xw) {
+                    ok = mbar_wait_warp(bar0 + 8 * slot, phase);
+                    if (ok && xitem) {
+                        float s[16];
+                        load16<Tin>(s_in0 + slot * (G::kPlaneStride / (int)sizeof(Tin)), s);
+                        // output i sits at s[4 + i]
+                        float o[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            float acc = prm.wxy[0] * s[4 + i - R];
+#pragma unroll
+                            for (int d = -R + 1; d <= R; ++d) acc = fmaf(prm.wxy[d + R], s[4 + i + d], acc);
+                            o[i] = acc;
+                        }
+                        float4* dst = reinterpret_cast<float4*>(sx_item + boff);
+                        dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+                        dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+                    }
+                }
                 if (!__syncthreads_and(ok)) {
                     // give up: flag the host, let the copies in flight land, leave
                     if (tid == 0) {
                         atomicExch(err, 1);
-                        int s2 = slot;
-                        uint32_t ph2 = phase;
-                        for (int zz = zi + 1; zz < zin_hi && zz <= zi + AHEAD; ++zz) {
-                            if (++s2 == NB) { s2 = 0; ph2 ^= 1u; }
+                        for (int zz = zi; zz < zin_hi && zz < zi + NB; ++zz) {
+                            const int k = zz - zin_lo;
+                            const uint32_t b = bar0 + 8 * (k % NB), ph = (uint32_t)((k / NB) & 1);
                             for (int it = 0; it < kWaitLimit; ++it)
-                                if (mbar_try_wait(bar0 + 8 * s2, ph2)) break;
+                                if (mbar_try_wait(b, ph)) break;
                         }
                     }
                     __syncthreads();
                     return;
                 }
-                // x blur: (row, group of 4 columns) items; the span of a group is 3 aligned words
-                const Tin(*s_in)[G::BX] = reinterpret_cast<const Tin(*)[G::BX]>(s_raw + slot * G::kPlaneStride);
-                for (int item = tid; item < G::BY * 16; item += kThreads) {
-                    const int r = item >> 4, g = item & 15;
-                    float s0[4], s1[4], s2[4];
-                    load_word<Tin>(&s_in[r][4 * g + G::HX - 4], s0);
-                    load_word<Tin>(&s_in[r][4 * g + G::HX], s1);
-                    load_word<Tin>(&s_in[r][4 * g + G::HX + 4], s2);
-                    const float s[12] = {s0[0], s0[1], s0[2], s0[3], s1[0], s1[1], s1[2], s1[3],
-                                         s2[0], s2[1], s2[2], s2[3]};
-                    float o[4];
+                if (tid == 0 && zi + NB < zin_hi) issue(zi + NB, slot);
+                // y blur of rows 2 warp, 2 warp + 1 (x-blurred rows 2 warp .. 2 warp + 2R + 1)
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        float acc = 0.f;
-#pragma unroll
-                        for (int d = -R; d <= R; ++d) acc = fmaf(w[d + R], s[4 + i + d], acc);
-                        o[i] = acc * inx[i];
+                for (int t = 0; t <= 2 * R + 1; ++t) {
+                    const float2 q = *reinterpret_cast<const float2*>(sy_col + boff + t * G::SXW);
+                    if (t == 0) {
+                        v[0] = prm.wxy[0] * q.x;
+                        v[1] = prm.wxy[0] * q.y;
+                    } else if (t <= 2 * R) {
+                        v[0] = fmaf(prm.wxy[t], q.x, v[0]);
+                        v[1] = fmaf(prm.wxy[t], q.y, v[1]);
                     }
-                    *reinterpret_cast<float4*>(&s_x[r][4 * g]) = make_float4(o[0], o[1], o[2], o[3]);
+                    if (t == 1) {
+                        v[2] = prm.wxy[0] * q.x;
+                        v[3] = prm.wxy[0] * q.y;
+                    } else if (t >= 2) {
+                        v[2] = fmaf(prm.wxy[t - 1], q.x, v[2]);
+                        v[3] = fmaf(prm.wxy[t - 1], q.y, v[3]);
+                    }
                 }
-                __syncthreads();
-                // y blur of this thread's 4 columns on row ty
-#pragma unroll
-                for (int d = -R; d <= R; ++d) {
-                    const float4 q = *reinterpret_cast<const float4*>(&s_x[ty + R + d][4 * tx]);
-                    v[0] = fmaf(w[d + R], q.x, v[0]);
-                    v[1] = fmaf(w[d + R], q.y, v[1]);
-                    v[2] = fmaf(w[d + R], q.z, v[2]);
-                    v[3] = fmaf(w[d + R], q.w, v[3]);
+                if (R == 0) {  // 2R + 1 = 1 row per output
+                    const float2 q = *reinterpret_cast<const float2*>(sy_col + boff + G::SXW);
+                    v[2] = prm.wxy[0] * q.x;
+                    v[3] = prm.wxy[0] * q.y;
                 }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) v[i] *= iny;
                 if (++slot == NB) { slot = 0; phase ^= 1u; }
+                buf ^= 1;
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) ring[P - 1 + u][i] = v[i];
+            for (int c = 0; c < 4; ++c) ring[P - 1 + u][c] = v[c];
             // emit plane zi - Rz from ring slots u .. u + P - 1 (slot u + P - 1 = plane zi)
             const int zo = zi - Rz;
-            if (zo >= z0 && zo < z1 && gy < ny) {
-                float o4[4] = {0.f, 0.f, 0.f, 0.f};
-                float inz = 1.f;
+            if (zo >= z0 && zo < z1) {  // uniform across the CTA
+                float o[4];
                 if constexpr (ROB) {
                     float wv[P];
 #pragma unroll
                     for (int jj = 0; jj < P; ++jj) wv[jj] = (zi - jj >= 0 && zi - jj < nz) ? prm.wz[jj] : 0.f;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int c = 0; c < 4; ++c) {
                         float vv[P];
 #pragma unroll
-                        for (int jj = 0; jj < P; ++jj) vv[jj] = ring[u + P - 1 - jj][i];
-                        o4[i] = robust_window<P>(vv, wv, prm.kappa2);
+                        for (int jj = 0; jj < P; ++jj) vv[jj] = ring[u + P - 1 - jj][c];
+                        o[c] = robust_window<P>(vv, wv, prm.kappa2) * sxy[c];
                     }
                 } else {
+                    const float inz = inv_nz[zo];
 #pragma unroll
-                    for (int jj = 0; jj < P; ++jj) {
-                        const float wz = prm.wz[jj];
+                    for (int c = 0; c < 4; ++c) {
+                        float acc = prm.wz[0] * ring[u + P - 1][c];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) o4[i] = fmaf(wz, ring[u + P - 1 - jj][i], o4[i]);
+                        for (int jj = 1; jj < P; ++jj) acc = fmaf(prm.wz[jj], ring[u + P - 1 - jj][c], acc);
+                        o[c] = acc * (sxy[c] * inz);
                     }
-                    inz = inv_nz[zo];
                 }
-                float* dst = out + (int64_t)(zo - z0) * plane + (int64_t)gy * pitch + x0 + 4 * tx;
-                const int gx = x0 + 4 * tx;
-                if (gx + 3 < nx && (pitch & 3) == 0) {
-                    *reinterpret_cast<float4*>(dst) = make_float4(o4[0] * inz, o4[1] * inz, o4[2] * inz, o4[3] * inz);
+                const int64_t zoff = (int64_t)(zo - z0) * plane;
+                if (vec2) {
+                    if (st0) *reinterpret_cast<float2*>(dst0 + zoff) = make_float2(o[0], o[1]);
+                    if (st1) *reinterpret_cast<float2*>(dst1 + zoff) = make_float2(o[2], o[3]);
                 } else {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        if (gx + i < nx) dst[i] = o4[i] * inz;
+                    if (st0 && gx < nx) dst0[zoff] = o[0];
+                    if (st0 && gx + 1 < nx) dst0[zoff + 1] = o[1];
+                    if (st1 && gx < nx) dst1[zoff] = o[2];
+                    if (st1 && gx + 1 < nx) dst1[zoff + 1] = o[3];
                 }
             }
-            __syncthreads();  // s_x and the input buffer of plane zi are reused
         }
 #pragma unroll
         for (int q = 0; q < P - 1; ++q)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) ring[q][i] = ring[q + U][i];
+            for (int c = 0; c < 4; ++c) ring[q][c] = ring[q + U][c];
     }
+}
+
+// Opt in to the TMA kernel's dynamic shared memory once per instantiation and device.
+template <class Tin, int R, bool ROB>
+int smooth_tma_prepare() {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    EMF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return EMFUSE_OK;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        EMF_CUDA(cudaFuncSetAttribute(smooth_tma_kernel<Tin, R, ROB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      SmTile<Tin, R>::kSmemBytes));
+        done[dev] = true;
+    }
+    return EMFUSE_OK;
 }
 
 struct AxisParams {
@@ -505,8 +579,8 @@ int smooth_stack(const void* in, int dt, float* out, int64_t nx, int64_t ny, int
         for (int j = 0; j < 2 * Rz + 1; ++j) prm.wz[j] = wz[2 * Rz - j];
         prm.kappa2 = kappa * kappa;
         CUtensorMap map;
-        const int hx = dt == EMFUSE_U8 ? 16 : 4;
-        EMF_TRY(encode_tensor_map_3d(&map, in, (int)esz, nx, ny, nz, pitch, kTX + 2 * hx, kTY + 2 * Rxy));
+        const int hx = dt == EMFUSE_U8 ? 16 : 4, hxr = dt == EMFUSE_U8 ? 16 : 8;
+        EMF_TRY(encode_tensor_map_3d(&map, in, (int)esz, nx, ny, nz, pitch, kTX + hx + hxr, kTY + 2 * Rxy));
         int* err = device_error_flag();
         if (!err) {
             set_error("could not allocate the device error word");
@@ -517,14 +591,16 @@ int smooth_stack(const void* in, int dt, float* out, int64_t nx, int64_t ny, int
         {
             KernelScope ks(rob ? "smooth_tma_robust" : "smooth_tma", st,
                            (double)nx * ny * ((zin1 - zin0) * (double)esz + (z1 - z0) * 4.0));
+#define EMF_SMOOTH_TMA2(TT, RR, RB)                                                                \
+    do {                                                                                           \
+        EMF_TRY((smooth_tma_prepare<TT, RR, RB>()));                                               \
+        smooth_tma_kernel<TT, RR, RB><<<grid, kThreads, SmTile<TT, RR>::kSmemBytes, st>>>(          \
+            map, out, (int)nx, (int)ny, (int)nz, pitch, (int)z0, (int)z1, inv_x, inv_y, inv_z, prm, err);       \
+    } while (0)
 #define EMF_SMOOTH_TMA1(RR, RB)                                                                    \
     do {                                                                                           \
-        if (dt == EMFUSE_U8)                                                                       \
-            smooth_tma_kernel<uint8_t, RR, RB><<<grid, kThreads, 0, st>>>(map, out, (int)nx, (int)ny, (int)nz, \
-                pitch, (int)z0, (int)z1, inv_x, inv_y, inv_z, prm, err);              \
-        else                                                                                       \
-            smooth_tma_kernel<float, RR, RB><<<grid, kThreads, 0, st>>>(map, out, (int)nx, (int)ny, (int)nz, \
-                pitch, (int)z0, (int)z1, inv_x, inv_y, inv_z, prm, err);              \
+        if (dt == EMFUSE_U8) EMF_SMOOTH_TMA2(uint8_t, RR, RB);                                     \
+        else EMF_SMOOTH_TMA2(float, RR, RB);                                                       \
     } while (0)
 #define EMF_SMOOTH_TMA(RR)                                                                         \
     do {                                                                                           \
@@ -540,6 +616,7 @@ int smooth_stack(const void* in, int dt, float* out, int64_t nx, int64_t ny, int
             }
 #undef EMF_SMOOTH_TMA
 #undef EMF_SMOOTH_TMA1
+#undef EMF_SMOOTH_TMA2
             EMF_CHECK_LAUNCH();
         }
         // a timed-out wait is reported by the next call that synchronises (the solves)
