@@ -768,10 +768,13 @@ struct Solver {
                 }
             }
             // rows per work item: tall chunks amortise the halo rows (about 2 nu + 3 pairs per
-            // chunk); shorter ones only while the level would otherwise leave SMs idle
-            // (down to 8 rows on small levels, where a march's latency, not its work, is the cost)
-            L.ch = 128;
-            while (L.ch > 8 && want / L.ch < (int64_t)kNumSMs * 16) L.ch /= 2;  // about one item per resident warp
+            // chunk) and the per-item set-up; 256 rows only where every resident warp still gets
+            // several items (the last ones would otherwise leave SMs idle), shorter ones while the
+            // level would leave SMs idle (down to 8 rows on small levels, where a march's latency,
+            // not its work, is the cost)
+            const int64_t resident = (int64_t)kNumSMs * 16;  // resident wavefront warps, about
+            L.ch = want / 256 >= 4 * resident ? 256 : 128;
+            while (L.ch > 8 && want / L.ch < resident) L.ch /= 2;  // about one item per resident warp
             if (k == 0 && rq->opts.tile_rows > 0) L.ch = rq->opts.tile_rows;
             for (const auto& S : L.wsl) {
                 L.item_start.push_back(L.item_start.back() + (int64_t)S.fstrips * ceil_div(S.ny, L.ch));

@@ -28,8 +28,8 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-__all__ = ["StackParams", "stack_params", "evaluate_stack", "make_stack", "make_ragged_batch",
-           "CONFIG_SEEDS"]
+__all__ = ["StackParams", "stack_params", "evaluate_stack", "evaluate_stack_tiled", "make_stack",
+           "make_ragged_batch", "CONFIG_SEEDS"]
 
 # Seeds of the five workload configurations (plain 16x256^2, 64x2048^2, ragged batch,
 # differentiation 32x512^2, paper-scale 64x21504x26624).
@@ -107,6 +107,64 @@ def evaluate_stack(p: StackParams, z0: int = 0, z1: int | None = None, device="c
             out[z - z0] = torch.round(V).to(torch.uint8)
         else:
             out[z - z0] = V.to(out_dtype)
+    return out
+
+
+def evaluate_stack_tiled(p: StackParams, z0: int = 0, z1: int | None = None, device="cpu",
+                         dtype=torch.float32, out_dtype=torch.uint8, tile: int = 2048, out=None):
+    """The same stack as evaluate_stack, evaluated tile by tile so that slices of any size fit:
+    each blob adds its profile product only inside its 3 s footprint, so a tile sums just the
+    blobs whose footprint meets it (a small matrix product per tile).  ``out`` may be given
+    (any device, e.g. pinned host memory); slices are written to it one at a time."""
+    nz, ny, nx = p.shape
+    z1 = nz if z1 is None else z1
+    if out is None:
+        out = torch.empty((z1 - z0, ny, nx), device=device, dtype=out_dtype)
+    cen = torch.as_tensor(p.centres, device=device, dtype=torch.float64)
+    sig = torch.as_tensor(p.sigmas, device=device, dtype=torch.float64)
+    amp = torch.as_tensor(p.amps, device=device, dtype=torch.float64)
+    # integer coordinates with a nonzero profile: ceil(c - 3 s) .. floor(c + 3 s)
+    lo = torch.ceil(cen[:, 1:] - 3.0 * sig[:, None])
+    hi = torch.floor(cen[:, 1:] + 3.0 * sig[:, None])
+    nty, ntx = (ny + tile - 1) // tile, (nx + tile - 1) // tile
+    t_lo = torch.clamp(torch.div(lo, tile, rounding_mode="floor"), min=0).to(torch.int64)
+    t_hi = torch.minimum(torch.div(hi, tile, rounding_mode="floor").to(torch.int64),
+                         torch.tensor([nty - 1, ntx - 1], device=device))
+    for z in range(z0, z1):
+        dz = z - cen[:, 0]
+        live = dz.abs() <= 3.0 * sig
+        wz_all = torch.where(live, amp * torch.exp(-(dz * dz) / (2.0 * sig * sig)), torch.zeros_like(amp))
+        V = torch.empty((ny, nx), device=device, dtype=dtype)
+        for ty in range(nty):
+            ya, yb = ty * tile, min(ny, (ty + 1) * tile)
+            in_y = live & (t_lo[:, 0] <= ty) & (t_hi[:, 0] >= ty)
+            for tx in range(ntx):
+                xa, xb = tx * tile, min(nx, (tx + 1) * tile)
+                idx = torch.nonzero(in_y & (t_lo[:, 1] <= tx) & (t_hi[:, 1] >= tx)).flatten()
+                Vt = torch.full((yb - ya, xb - xa), 128.0, device=device, dtype=dtype)
+                if idx.numel():
+                    def prof(c, n0, n1):
+                        x = torch.arange(n0, n1, device=device, dtype=dtype)[None, :]
+                        d = x - c.to(dtype)[:, None]
+                        s = sig[idx].to(dtype)[:, None]
+                        g = torch.exp(-(d * d) / (2.0 * s * s))
+                        return torch.where(d.abs() <= 3.0 * s, g, torch.zeros_like(g))
+                    gy = prof(cen[idx, 1], ya, yb)
+                    gx = prof(cen[idx, 2], xa, xb)
+                    Vt += (gy.t() * wz_all[idx].to(dtype)[None, :]) @ gx
+                ys = torch.arange(ya, yb, device=device, dtype=dtype)[:, None]
+                xs = torch.arange(xa, xb, device=device, dtype=dtype)[None, :]
+                for k in range(len(p.steps)):
+                    n = p.normals[k]; q = p.points[k]
+                    h = n[1] * (ys - q[1]) + n[2] * (xs - q[2]) + n[0] * (z - q[0])
+                    Vt += float(p.steps[k]) * torch.sign(h)
+                V[ya:yb, xa:xb] = Vt
+        V.clamp_(0.0, 255.0)
+        V = (float(p.gains[z]) * V + float(p.offsets[z])).clamp_(0.0, 255.0)
+        if out_dtype == torch.uint8:
+            out[z - z0].copy_(torch.round(V).to(torch.uint8))
+        else:
+            out[z - z0].copy_(V.to(out_dtype))
     return out
 
 
