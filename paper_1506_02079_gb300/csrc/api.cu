@@ -96,7 +96,9 @@ static int solve_stack(const float* s, const void* o, int dt, float* out, int64_
 //   copy-in  (side stream): the input in pieces, piece k ending at the last plane smoothing
 //            chunk k reads, each with an event;
 //   compute  (the caller's stream): smoothing of a chunk of C slices once its input has
-//            arrived (the first chunk's input is small, so compute starts early), and its solve,
+//            arrived (the first chunk's input is small, so compute starts early; on a stack so
+//            short that it is half the stack already, the whole stack in one launch), and the
+//            chunk's solve,
 //            queued asynchronously (the solve's outer loop runs on the device, so the host never
 //            waits between chunks), into an output buffer of a ring of four;
 //   copy-out (side stream): each chunk's output to the host as soon as its solve is done.
@@ -109,7 +111,10 @@ static int correct_stack_resident(const void* in, int dt, float* out, int64_t nx
     const int64_t plane = nx * ny;
     const size_t esz = dtype_size(dt);
     const int64_t nchunks = (nz + C - 1) / C;            // solve chunks
-    const int64_t Cs = C;                                // smoothing chunks: one per solve chunk
+    // smoothing chunks: one per solve chunk, unless the first chunk's input (its planes and R
+    // more) is already half the stack; then one launch smooths the whole stack, instead of
+    // each chunk marching through R halo planes on either side again
+    const int64_t Cs = C + R >= (nz + 1) / 2 ? nchunks * C : C;
     const int64_t ns = (nz + Cs - 1) / Cs;
     constexpr int kRing = 4;                             // chunk output buffers
     const int nbuf = (int)std::min<int64_t>(kRing, nchunks);
@@ -161,7 +166,7 @@ static int correct_stack_resident(const void* in, int dt, float* out, int64_t nx
             const cudaStream_t c = st;
             const int q = int(i % nbuf);
             const int64_t z0 = i * C, z1 = std::min(nz, z0 + C);
-            const int64_t k = z0 / Cs;  // chunk boundaries are multiples of C, and Cs = C
+            const int64_t k = z0 / Cs;  // chunk boundaries are multiples of C, and Cs of C
             if (!smoothed[k]) {
                 const int64_t a = k * Cs, b = std::min(nz, a + Cs);
                 EMF_CUDA(cudaStreamWaitEvent(c, ev_piece[k], 0));  // input planes [0, b + R) arrived
