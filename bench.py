@@ -40,6 +40,9 @@ def parse():
     p.add_argument("--impl", default="emfuse", choices=["emfuse", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--tile-rows", type=int, default=0,
+                   help="rows per work item of the finest level's wavefront kernels (0 = chosen; "
+                        "for profiling smaller stacks with the 64-slice step's items)")
     p.add_argument("--no-graphs", action="store_true",
                    help="launch every solver kernel directly instead of replaying CUDA graphs (for "
                         "profilers that do not look inside graphs with conditional nodes)")
@@ -353,7 +356,8 @@ def run_gpu(args):
     L = api.lib()
     I0 = make_input(dev, args.nz)
     out = torch.empty_like(I0)
-    opts = api.default_opts(tol=1e-6, precision=api.PREC_MIXED, no_graphs=int(args.no_graphs))
+    opts = api.default_opts(tol=1e-6, precision=api.PREC_MIXED, no_graphs=int(args.no_graphs),
+                            tile_rows=args.tile_rows)
     step = lambda: api.emfuse_correct_stack(I0, 1.0, 3.0, args.alpha, opts, out=out, return_stats=True)
 
     for _ in range(max(3, args.warmup)):
@@ -584,7 +588,8 @@ def run_gpu(args):
                            "alpha": args.alpha, "nz": args.nz, "ny": NY, "nx": NX,
                            "seed": SEED, "l2": "inputs (1.07 GB) larger than L2 (129 MB)",
                            "parallelism": f"replicas x{world}",
-                           "launch": "direct kernel launches" if args.no_graphs else "CUDA graphs"},
+                           "launch": "direct kernel launches" if args.no_graphs else "CUDA graphs",
+                           "tile_rows": args.tile_rows or "chosen"},
                 "gpu_launches": int(launches), "vcycles": max(vcycles), "max_rel_residual": worst_res,
                 "clocks": clk.summary()}
         if extras:
