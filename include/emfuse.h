@@ -93,9 +93,11 @@ typedef struct {
     int autotune;        /* 1: before solving, time complete solves of this batch for
                             tile_rows in {32, 64, 128, 256} (with nu = (2, 2)), then for
                             (nu_pre, nu_post) in {(1,1), (1,2), (2,1), (2,3), (3,2), (3,3),
-                            (3,4)} with the best tile_rows (fused schedule), keep the
-                            fastest for this batch geometry, alpha, precision and tol, and
-                            solve with it (see emfuse_autotune_result).  Default 0.        */
+                            (3,4), (4,4)} with each of the two fastest tile_rows (fused
+                            schedule; nu_pre = 4 runs its DOWN leg in the reference
+                            schedule), keep the fastest for this batch geometry, alpha,
+                            precision and tol, and solve with it (20 candidates, see
+                            emfuse_autotune_result).  Default 0.                           */
     int no_graphs;       /* 1: launch every V-cycle kernel directly instead of replaying
                             the V-cycle as a captured CUDA graph.  Default 0.              */
     float robust_kappa;  /* emfuse_correct_stack only: > 0 smooths with robust averaging

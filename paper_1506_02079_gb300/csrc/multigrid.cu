@@ -1474,12 +1474,17 @@ int solve_batch(const SolveRequest& req, cudaStream_t st) {
             if (table[i].ms >= 0 && (b < 0 || table[i].ms < table[b].ms)) b = i;
         return b;
     };
+    // rows per work item (the tile height of a 128-column strip) at nu = (2, 2), then every
+    // other sweep count with the two fastest tile heights
     for (int rows : {32, 64, 128, 256}) EMF_TRY(trial(2, 2, rows));
+    std::vector<emfuse_tune_entry> by_rows(table);
+    std::stable_sort(by_rows.begin(), by_rows.end(), [](const emfuse_tune_entry& x, const emfuse_tune_entry& y) {
+        const double a = x.ms < 0 ? 1e300 : x.ms, c = y.ms < 0 ? 1e300 : y.ms;
+        return a < c;
+    });
+    for (auto nu : {std::pair<int, int>{1, 1}, {1, 2}, {2, 1}, {2, 3}, {3, 2}, {3, 3}, {3, 4}, {4, 4}})
+        for (int q = 0; q < 2; ++q) EMF_TRY(trial(nu.first, nu.second, by_rows[q].tile_rows));
     int b = best_of();
-    const int rows = b >= 0 ? table[b].tile_rows : 128;
-    for (auto nu : {std::pair<int, int>{1, 1}, {1, 2}, {2, 1}, {2, 3}, {3, 2}, {3, 3}, {3, 4}})
-        EMF_TRY(trial(nu.first, nu.second, rows));
-    b = best_of();
     if (b < 0) {
         t_last_tune = table;
         set_error("autotune: no candidate schedule reached the tolerance");

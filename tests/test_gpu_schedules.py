@@ -167,9 +167,12 @@ def test_autotune_picks_the_fastest_candidate(dev):
     f, st = api.emfuse_screened_poisson(s, o, 1e-3, api.default_opts(autotune=1), nx=nx, ny=ny, offsets=offs,
                                         return_stats=True)
     table = api.emfuse_autotune_result()
-    assert len(table) == 11
-    # one to four sweeps per leg, all in the fused kernels
-    assert {(e["nu_pre"], e["nu_post"]) for e in table} >= {(1, 1), (2, 2), (3, 3), (3, 4), (2, 3), (3, 2)}
+    assert len(table) == 20
+    # one to four sweeps per leg, each sweep count with two tile heights (rows per work item)
+    pairs = {(e["nu_pre"], e["nu_post"]) for e in table}
+    assert pairs >= {(1, 1), (2, 2), (3, 3), (3, 4), (2, 3), (3, 2), (4, 4)}
+    for nu in pairs:
+        assert len({e["tile_rows"] for e in table if (e["nu_pre"], e["nu_post"]) == nu}) >= 2, nu
     best = table[0]
     assert best["ms"] == min(e["ms"] for e in table if e["ms"] >= 0)
     ref = api.emfuse_screened_poisson(s, o, 1e-3, api.default_opts(nu_pre=best["nu_pre"], nu_post=best["nu_post"],
