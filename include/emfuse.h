@@ -278,6 +278,32 @@ int emfuse_smooth_gradient_domain(const void* in, int dt, float* out, int64_t nx
                                   double alpha, int precision, void* stream);
 
 /*
+ * The same problem as emfuse_smooth_gradient_domain, solved by multigrid on the stack, as the
+ * paper's earlier method did (Sec. 3 "Alternate Solutions"), instead of by transforms:
+ * correction form out = in + d with (alpha I + L) d = -L_z in; V-cycles in FP32 on the 3-D
+ * grid (cell-centred coarsening to 1 x 1 x 1, finite-volume operators on the true cells,
+ * restriction by child sum / 8, trilinear prolongation, red-black Gauss-Seidel with
+ * opts->nu_pre / nu_post sweeps; opts->first_vcycles FP32 cycles before the first FP64 pass);
+ * after every V-cycle an FP64 pass forms d += e and r = -L_z in - A d (A d in FP64, rounded
+ * once to FP32 before the subtraction from the FP32-formed -L_z in; everything in FP64 when
+ * opts->tol < 1e-7) and writes out = in + d, until ||r|| / ||alpha in + L_xy in|| <= opts->tol
+ * or opts->max_vcycles V-cycles.  The host reads the residual norm after every pass (the call
+ * returns when out is final).  Other opts fields are ignored.
+ *   in      device, nz x ny x nx dense [z][y][x], uint8 (dt = EMFUSE_U8) or float32.
+ *   out     device float32, same shape; must not alias in.
+ *   alpha   > 0 (finite).
+ *   opts    NULL = defaults.
+ *   stats   NULL or ONE host entry for the whole stack (vcycles, converged, rel_residual,
+ *           b_norm; rel_residual_check = -1).
+ * Temporaries (from the library's pool): the level pyramid (u and b, about 9 B per cell) and
+ * the FP64 correction (8 B per cell).  Errors: EMFUSE_EINVAL (arguments; a NaN or Inf in `in`),
+ * EMFUSE_ENOMEM, EMFUSE_ENOCONV (tol not reached; out holds the last iterate).
+ */
+int emfuse_smooth_gradient_domain_mg(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                                     double alpha, const emfuse_solve_opts* opts, emfuse_slice_stats* stats,
+                                     void* stream);
+
+/*
  * Fusion of low-frequency colour images with high-frequency monochrome ones (Sec. 3, the
  * colour example): for every image i and colour channel c, Eq. (1) with the colour channel as
  * the value constraint and the grey image as the gradient constraint,

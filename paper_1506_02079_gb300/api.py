@@ -21,7 +21,7 @@ __all__ = [
     "default_opts", "emfuse_smooth_z", "emfuse_smooth_z_robust", "emfuse_smooth_z_noalloc",
     "emfuse_screened_poisson",
     "emfuse_autotune_result", "TuneEntry", "emfuse_fuse_color", "emfuse_screened_poisson_dct",
-    "emfuse_smooth_gradient_domain", "emfuse_correct_stack",
+    "emfuse_smooth_gradient_domain", "emfuse_smooth_gradient_domain_mg", "emfuse_correct_stack",
     "emfuse_backward", "emfuse_version", "emfuse_release_cache", "emfuse_kernel_binary_version",
     "emfuse_probe_fp64_fma_rate", "PendingStats", "EMFUSE_U8", "EMFUSE_F32", "PREC_FP32", "PREC_MIXED",
     "PREC_FP64", "EXPORTED_SYMBOLS",
@@ -37,6 +37,7 @@ EXPORTED_SYMBOLS = ["emfuse_default_opts", "emfuse_smooth_z", "emfuse_screened_p
                     "emfuse_profile_end", "emfuse_release_cache", "emfuse_smooth_z_noalloc",
                     "emfuse_selftest_fpconv", "emfuse_autotune_result", "emfuse_smooth_z_robust",
                     "emfuse_fuse_color", "emfuse_screened_poisson_dct", "emfuse_smooth_gradient_domain",
+                    "emfuse_smooth_gradient_domain_mg",
                     "emfuse_selftest_wait_timeout", "emfuse_kernel_binary_version",
                     "emfuse_probe_fp64_fma_rate"]
 
@@ -96,6 +97,8 @@ def lib() -> ctypes.CDLL:
             L.emfuse_fuse_color.argtypes = [vp, vp, vp, i64, i64, i64, db, ctypes.POINTER(SolveOpts), vp, vp]
             L.emfuse_screened_poisson_dct.argtypes = [vp, vp, vp, i64, i64, i64, db, ci, vp]
             L.emfuse_smooth_gradient_domain.argtypes = [vp, ci, vp, i64, i64, i64, db, ci, vp]
+            L.emfuse_smooth_gradient_domain_mg.argtypes = [vp, ci, vp, i64, i64, i64, db,
+                                                           ctypes.POINTER(SolveOpts), vp, vp]
             L.emfuse_selftest_wait_timeout.argtypes = [ci, vp]
             L.emfuse_selftest_wait_timeout.restype = ci
             L.emfuse_smooth_z_noalloc.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, fl, fl, vp]
@@ -368,6 +371,29 @@ def emfuse_smooth_gradient_domain(stack: torch.Tensor, alpha: float, precision: 
     _check(lib().emfuse_smooth_gradient_domain(stack.data_ptr(), _dtype_code(stack), out.data_ptr(), nx, ny, nz,
                                                float(alpha), int(precision), _stream_ptr(stack.device)))
     return out
+
+
+def emfuse_smooth_gradient_domain_mg(stack: torch.Tensor, alpha: float, opts: SolveOpts | None = None,
+                                     out: torch.Tensor | None = None, return_stats: bool = False,
+                                     allow_noconv: bool = False):
+    """The 3-D gradient-domain smoothing by multigrid on the stack (Sec. 3 "Alternate Solutions"):
+    FP32 V-cycles on the 7-point operator with FP64 defect correction to opts.tol.  ``stack``
+    CUDA uint8 or float32 [z][y][x].  Returns float32 of the same shape (and with return_stats
+    one dict for the whole stack)."""
+    _require_cuda(stack)
+    if stack.dim() != 3 or not stack.is_contiguous():
+        raise ValueError("stack must be a contiguous [z][y][x] tensor")
+    nz, ny, nx = stack.shape
+    if out is None:
+        out = torch.empty((nz, ny, nx), device=stack.device, dtype=torch.float32)
+    _require_cuda(out)
+    opts = opts if opts is not None else default_opts()
+    stats = (SliceStats * 1)()
+    code = lib().emfuse_smooth_gradient_domain_mg(stack.data_ptr(), _dtype_code(stack), out.data_ptr(), nx, ny, nz,
+                                                  float(alpha), ctypes.byref(opts), ctypes.addressof(stats),
+                                                  _stream_ptr(stack.device))
+    _check(code, allow_noconv)
+    return (out, _stats_list(stats)[0]) if return_stats else out
 
 
 def emfuse_fuse_color(s_rgb: torch.Tensor, o_grey: torch.Tensor, alpha: float, opts: SolveOpts | None = None,

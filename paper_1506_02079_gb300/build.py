@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(PKG, "libemfuse.so")
 SOURCES = ["api.cu", "smooth.cu", "multigrid.cu", "fused_f32.cu", "fused_f64.cu", "fused_f32_s68.cu",
-           "fused_f64_s68.cu", "runtime.cu", "dct_solve.cu"]
+           "fused_f64_s68.cu", "runtime.cu", "dct_solve.cu", "mg3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -508,6 +508,24 @@ int emfuse_smooth_gradient_domain(const void* in, int dt, float* out, int64_t nx
     return smooth_gradient_domain(in, dt, out, nx, ny, nz, alpha, precision, (cudaStream_t)stream);
 }
 
+int emfuse_smooth_gradient_domain_mg(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
+                                     double alpha, const emfuse_solve_opts* opts, emfuse_slice_stats* stats,
+                                     void* stream) {
+    set_error("");
+    if (!in || !out) return einval("emfuse_smooth_gradient_domain_mg: null pointer");
+    if (dt != EMFUSE_U8 && dt != EMFUSE_F32)
+        return einval("emfuse_smooth_gradient_domain_mg: dt must be EMFUSE_U8 or EMFUSE_F32");
+    if (nx < 1 || ny < 1 || nz < 1 || nx > kMaxSide || ny > kMaxSide || nz > kMaxSide)
+        return einval("emfuse_smooth_gradient_domain_mg: need sizes in [1, 2^29]");
+    if ((double)nx * (double)ny * (double)nz > 1099511627776.0)
+        return einval("emfuse_smooth_gradient_domain_mg: more than 2^40 cells");
+    if ((const void*)out == in) return einval("emfuse_smooth_gradient_domain_mg: out must not alias in");
+    EMF_TRY(check_alpha(alpha));
+    emfuse_solve_opts o2;
+    EMF_TRY(resolve_opts(opts, &o2));
+    return gd_multigrid(in, dt, out, nx, ny, nz, alpha, o2, stats, (cudaStream_t)stream);
+}
+
 int emfuse_fuse_color(const float* s_rgb, const float* o_grey, float* f_rgb, int64_t nimages, int64_t nx,
                       int64_t ny, double alpha, const emfuse_solve_opts* opts, emfuse_slice_stats* stats,
                       void* stream) {

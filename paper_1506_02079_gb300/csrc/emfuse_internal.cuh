@@ -64,6 +64,9 @@ int solve_dct_batch(const float* s, const float* o, float* f, int64_t n, int64_t
 // (dt EMFUSE_U8) or float, transforms in `precision`
 int smooth_gradient_domain(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz, double alpha,
                            int precision, cudaStream_t st);
+// mg3d.cu
+int gd_multigrid(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz, double alpha,
+                 const emfuse_solve_opts& opts, emfuse_slice_stats* stats, cudaStream_t st);
 void release_fft_plans();  // and the cuBLAS handles
 
 // elementwise helpers used by the adjoint (multigrid.cu)

@@ -75,6 +75,15 @@ def test_host_side_calls_without_gpu(libpath):
     assert L.emfuse_smooth_gradient_domain(fake, 1, ctypes.c_void_p(32), 1 << 20, 1 << 20, 4, 1e-3,
                                            api.PREC_FP32, None) == 1
     assert L.emfuse_smooth_gradient_domain(fake, 3, ctypes.c_void_p(32), 4, 4, 4, 1e-3, api.PREC_FP32, None) == 1
+    # 3-D gradient-domain multigrid: aliasing, dtype, alpha, size and option checks
+    mg = L.emfuse_smooth_gradient_domain_mg
+    assert mg(fake, 1, fake, 4, 4, 4, 1e-3, None, None, None) == 1
+    assert b"alias" in L.emfuse_last_error()
+    assert mg(fake, 3, ctypes.c_void_p(32), 4, 4, 4, 1e-3, None, None, None) == 1
+    assert mg(fake, 1, ctypes.c_void_p(32), 4, 4, 4, -1.0, None, None, None) == 1
+    assert mg(fake, 1, ctypes.c_void_p(32), 0, 4, 4, 1e-3, None, None, None) == 1
+    assert mg(fake, 1, ctypes.c_void_p(32), 1 << 20, 1 << 20, 4, 1e-3, None, None, None) == 1
+    assert mg(fake, 1, ctypes.c_void_p(32), 4, 4, 4, 1e-3, ctypes.byref(bad), None, None) == 1
     # the bounded-wait self-test validates its limit before any CUDA call
     assert L.emfuse_selftest_wait_timeout(0, None) == 1
     assert L.emfuse_selftest_wait_timeout((1 << 20) + 1, None) == 1
