@@ -402,7 +402,8 @@ def run_gpu(args):
         roof["fp64_probe"] = {"tflops_median": fp64_peak, "tflops_all": rates, "clocks": clk64.summary()}
         top = next((p for p in prof if p["name"] == roof["kernel"]), None)
         if top and roof["bound"] == "alu":
-            # the same kernel against HBM at the survey's 40 B per cell and FP64 pass
+            # the same kernel against HBM at a round 40 B per cell and FP64 pass (s, o, e, r, out in
+            # FP32 and the FP64 iterate read and written: 36 B, plus slack for the halo)
             cells = voxels
             roof["hbm_frac_at_40B_per_cell"] = (cells * 40.0 / (top["ms_per_step"] / max(top["launches"], 1) * 1e-3)
                                                 / 1e9 / measured_hbm_peak()[0])
