@@ -513,6 +513,17 @@ def run_gpu(args):
             sol[label] = {"ms": e0.elapsed_time(e1) / 2, "value": voxels / (e0.elapsed_time(e1) / 2 * 1e-3),
                           "unit": "voxels/s"}
             sol[label + "_out"] = res
+        # the solves alone against the oracle's DCT solve of the same smoothed slices
+        from oracle import emfuse_oracle as O
+        for label in ("multigrid_mixed", "fft_fp32", "fft_fp64"):
+            worst_abs, worst_l2 = 0.0, 0.0
+            for j in sample:
+                ref = O.solve_dct(s_c2[j].double().cpu().numpy(), I0[j].double().cpu().numpy(), args.alpha)
+                dj = sol[label + "_out"][j].double().cpu().numpy() - ref
+                worst_abs = max(worst_abs, float(np.max(np.abs(dj))))
+                worst_l2 = max(worst_l2, float(np.linalg.norm(dj) / np.linalg.norm(ref)))
+            sol[label]["oracle_error"] = {"slices": list(sample), "max_abs_err": worst_abs,
+                                          "rel_to_255": worst_abs / 255.0, "rel_l2_err": worst_l2}
         sol["max_abs_diff_multigrid_vs_fft_fp64"] = float((sol.pop("multigrid_mixed_out") - sol["fft_fp64_out"]).abs().max())
         sol["max_abs_diff_fft_fp32_vs_fft_fp64"] = float((sol.pop("fft_fp32_out") - sol.pop("fft_fp64_out")).abs().max())
         extras["solve_multigrid_vs_fft"] = sol
@@ -530,14 +541,21 @@ def run_gpu(args):
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(3):
-            _, stc = api.emfuse_fuse_color(s_rgb, base, args.alpha, return_stats=True)
+            f_rgb, stc = api.emfuse_fuse_color(s_rgb, base, args.alpha, return_stats=True)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_c = e0.elapsed_time(e1) / 3
+        # the first image's three channels against the oracle
+        ref_c = O.fuse_color(s_rgb[0].double().cpu().numpy(), base[0].double().cpu().numpy(), args.alpha)
+        dc = f_rgb[0].double().cpu().numpy() - ref_c
         extras["color_fusion"] = {"images": 4, "ny": 4096, "nx": 4096, "channels": 3, "ms": ms_c,
                                   "value": s_rgb.numel() / (ms_c * 1e-3), "unit": "pixels/s",
                                   "vcycles": max(a["vcycles"] for a in stc),
-                                  "max_rel_residual": max(a["rel_residual"] for a in stc)}
+                                  "max_rel_residual": max(a["rel_residual"] for a in stc),
+                                  "oracle_error": {"image": 0, "max_abs_err": float(np.max(np.abs(dc))),
+                                                   "rel_to_255": float(np.max(np.abs(dc))) / 255.0,
+                                                   "rel_l2_err": float(np.linalg.norm(dc) / np.linalg.norm(ref_c))}}
+        del f_rgb, ref_c, dc
         del base, s_rgb
         torch.cuda.empty_cache()
         # the fourth next row: phase 1 as the 3-D gradient-domain problem of the earlier method
@@ -564,9 +582,14 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_g = e0.elapsed_time(e1) / 2
+        mg_prof = profile_steps(lambda: api.emfuse_smooth_gradient_domain_mg(
+            I0, 0.1, api.default_opts(tol=1e-6), out=mg_out), 1)
         gd["multigrid"] = {"ms": ms_g, "value": voxels / (ms_g * 1e-3), "unit": "voxels/s",
                            "vcycles": mg_st["vcycles"], "rel_residual": mg_st["rel_residual"],
-                           "max_abs_diff_vs_fft_fp64": float((mg_out - outs["fp64"]).abs().max())}
+                           "max_abs_diff_vs_fft_fp64": float((mg_out - outs["fp64"]).abs().max()),
+                           "kernels": [{"name": q["name"], "launches": q["launches"],
+                                        "ms": round(q["ms_per_step"], 3), "gbs": round(q["gbs"] or 0.0, 1)}
+                                       for q in mg_prof[:8]]}
         del mg_out
         tot_in = float(I0.double().sum())
         gd.update({"alpha": 0.1, "gaussian_smoothing_ms": sm["plain"]["ms"],
