@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_prolong_add(LevelArgs<T> a) {
 struct TopSlice {
     int64_t off;   // element offset of the slice in the packed s / o / d / out buffers
     int nx, ny;
-    int tiles_x;   // 64 x 16 tiles of the residual kernel
+    int tiles_x;   // 64 x 32 tiles of the residual kernel
     int pitch0;    // level-0 row pitch
     void* u0;      // level-0 iterate of the V-cycle (the correction e)
     void* b0;      // level-0 right-hand side (the residual r)
@@ -173,7 +173,7 @@ struct CallPtrs {
 };
 
 constexpr int kTopTX = 64;
-constexpr int kTopTY = 16;
+constexpr int kTopTY = 32;  // two rows of 4 cells per thread; the one-cell halo of d is 9 % extra
 
 // MODE 0: d = 0, r = alpha (s - o)          (first residual; also accumulates ||b||^2)
 // MODE 1: d_new = e                          (first correction)
@@ -225,14 +225,14 @@ k_top(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_start, 
         __syncthreads();
     }
     const float af = ad.alpha_f;
-    // squared norms: FP32 partial sums over a warp's 128 cells, FP64 from there on (per-block
+    // squared norms: FP32 partial sums over a warp's 256 cells, FP64 from there on (per-block
     // sums, per-slice atomics); this keeps the FP64 pipe for the residual itself
     float rrf = 0.f, bbf = 0.f;
-    const int ly = tid / 16;
-    const int y = ty0 + ly;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int lx = (tid % 16) + 16 * i;  // consecutive threads, consecutive cells
+    for (int i = 0; i < 8; ++i) {
+        const int ly = tid / 16 + 16 * (i >> 2);  // rows tid / 16 and tid / 16 + 16
+        const int y = ty0 + ly;
+        const int lx = (tid % 16) + 16 * (i & 3);  // consecutive threads, consecutive cells
         const int x = tx0 + lx;
         if (x >= G.nx || y >= G.ny) continue;
         const int64_t p = G.off + (int64_t)y * G.nx + x;
@@ -341,10 +341,10 @@ k_verify(const TopSlice* __restrict__ top, const int64_t* __restrict__ tile_star
         return rhs ? dv : (double)o[q] + dv;
     };
     double rr = 0.0, bb = 0.0;
-    const int y = ty0 + tid / 16;
 #pragma unroll 1
-    for (int i = 0; i < 4; ++i) {
-        const int x = tx0 + (tid % 16) + 16 * i;
+    for (int i = 0; i < 8; ++i) {
+        const int y = ty0 + tid / 16 + 16 * (i >> 2);
+        const int x = tx0 + (tid % 16) + 16 * (i & 3);
         if (x >= G.nx || y >= G.ny) continue;
         const int64_t p = G.off + (int64_t)y * G.nx + x;
         const bool hw = x > 0, he = x + 1 < G.nx, hn = y > 0, hs = y + 1 < G.ny;
