@@ -104,6 +104,42 @@ static int solve_stack(const float* s, const void* o, int dt, float* out, int64_
 //   copy-out (side stream): each chunk's output to the host as soon as its solve is done.
 // A slice's result does not depend on the batch it is solved in, so the output equals the
 // device path's bit for bit.  The per-slice stats of the chunks give the outcome.
+// Copy streams and events of the host-buffer pipeline, kept per host thread and device for the
+// life of the process (creating and destroying streams on every call costs the driver
+// occasional stalls of tens of milliseconds).  Every event is complete when a call returns.
+struct PipeResources {
+    int dev = -1;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    std::vector<cudaEvent_t> events;
+    size_t next = 0;
+};
+static thread_local PipeResources* t_pipe = nullptr;
+
+static int pipe_resources(PipeResources** out) {
+    int dev = 0;
+    EMF_CUDA(cudaGetDevice(&dev));
+    if (!t_pipe) t_pipe = new PipeResources();
+    if (t_pipe->dev != dev) {  // first use on this thread, or another device: fresh resources
+        t_pipe = new PipeResources();  // the old device's streams stay valid for that device
+        EMF_CUDA(cudaStreamCreateWithFlags(&t_pipe->s_in, cudaStreamNonBlocking));
+        EMF_CUDA(cudaStreamCreateWithFlags(&t_pipe->s_out, cudaStreamNonBlocking));
+        t_pipe->dev = dev;
+    }
+    t_pipe->next = 0;
+    *out = t_pipe;
+    return EMFUSE_OK;
+}
+
+static int pipe_event(PipeResources* r, cudaEvent_t* e) {
+    if (r->next == r->events.size()) {
+        cudaEvent_t x = nullptr;
+        EMF_CUDA(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+        r->events.push_back(x);
+    }
+    *e = r->events[r->next++];
+    return EMFUSE_OK;
+}
+
 static int correct_stack_resident(const void* in, int dt, float* out, int64_t nx, int64_t ny, int64_t nz,
                                   float sigma_xy, float sigma_z, double alpha, const emfuse_solve_opts& o2,
                                   emfuse_slice_stats* stats, cudaStream_t st, int64_t C) {
@@ -125,26 +161,15 @@ static int correct_stack_resident(const void* in, int dt, float* out, int64_t nx
     EMF_TRY(din.alloc((size_t)(nz * plane) * esz, st));
     EMF_TRY(ds.alloc((size_t)(nz * plane) * sizeof(float), st));
     for (int q = 0; q < nbuf; ++q) EMF_TRY(dout[q].alloc((size_t)(C * plane) * sizeof(float), st));
-    cudaStream_t s_in = nullptr, s_out = nullptr;
+    PipeResources* pr = nullptr;
+    EMF_TRY(pipe_resources(&pr));
+    cudaStream_t s_in = pr->s_in, s_out = pr->s_out;
     cudaEvent_t ev_alloc = nullptr, ev_outq = nullptr;
     std::vector<cudaEvent_t> ev_piece(ns, nullptr), ev_smooth(ns, nullptr), ev_comp(nchunks, nullptr),
         ev_free(kRing, nullptr);
-    auto cleanup = [&]() {
-        for (auto* v : {&ev_piece, &ev_smooth, &ev_comp, &ev_free})
-            for (auto& e : *v)
-                if (e) cudaEventDestroy(e);
-        for (cudaEvent_t e : {ev_alloc, ev_outq})
-            if (e) cudaEventDestroy(e);
-        if (s_in) cudaStreamDestroy(s_in);
-        if (s_out) cudaStreamDestroy(s_out);
-    };
-    auto ev = [](cudaEvent_t& e) -> int {
-        EMF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        return EMFUSE_OK;
-    };
+    auto cleanup = [&]() {};  // streams and events are kept for the next call
+    auto ev = [&](cudaEvent_t& e) -> int { return pipe_event(pr, &e); };
     auto body = [&]() -> int {
-        EMF_CUDA(cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking));
-        EMF_CUDA(cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking));
         EMF_TRY(ev(ev_alloc));
         EMF_TRY(ev(ev_outq));
         for (auto* v : {&ev_piece, &ev_smooth, &ev_comp, &ev_free})
@@ -194,10 +219,21 @@ static int correct_stack_resident(const void* in, int dt, float* out, int64_t nx
         return EMFUSE_OK;
     };
     int rc = body();
-    // wait for everything queued (also after a failure part-way, before the buffers are released)
+    // wait for everything queued (also after a failure part-way, before the buffers are released);
+    // on success the caller's stream already waits for both copy streams, and the host thread
+    // sleeps on a blocking-sync event instead of spinning for the whole pipeline
+    cudaError_t e = cudaSuccess;
+    if (rc == EMFUSE_OK) {
+        cudaEvent_t done = nullptr;
+        e = cudaEventCreateWithFlags(&done, cudaEventBlockingSync | cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(done, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(done);
+        if (done) cudaEventDestroy(done);
+    }
     if (s_in) cudaStreamSynchronize(s_in);
     if (s_out) cudaStreamSynchronize(s_out);
-    const cudaError_t e = cudaStreamSynchronize(st);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e2;
     cleanup();
     if (rc != EMFUSE_OK) return rc;
     if (e != cudaSuccess) {
